@@ -1,0 +1,726 @@
+/*
+ * FP64 CPU oracle of the accelerated-Lambda-iteration hot path of
+ * De Ceuster et al., "Magritte I" (arXiv:1912.08445).
+ *
+ * TEST INFRASTRUCTURE ONLY. This file is the slow, plain reference that the CUDA
+ * path is checked against. Only the tests, the smoke check and the bench's CPU
+ * baseline may load it. It shares no code, header or table with the CUDA library.
+ *
+ * Build: gcc -O2 -ffp-contract=off -fopenmp -shared -fPIC (no FMA contraction, so that
+ * the ray tracer's floating-point decisions are reproducible bit for bit).
+ *
+ * Every function follows the paper's section or equation named in its comment.
+ * Readings where the paper is silent or ambiguous are marked "Reading:".
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* Physical constants (CODATA 2018). The paper lists none; its printed line widths
+ * (Sec. 4.1.1, 4.1.2) are reproduced with these values. */
+static const double H_PLANCK = 6.62607015e-34;
+static const double K_BOLTZ = 1.380649e-23;
+static const double C_LIGHT = 299792458.0;
+static const double SQRT_PI = 1.7724538509055160273;
+
+/* Model, species, discretisation and options, all host arrays owned by the caller. */
+typedef struct {
+    int64_t n;
+    int32_t geometry;          /* 0: 3D point cloud, 1: spherically symmetric shells on +z */
+    int32_t pad0;
+    const double *pos;         /* [n][3] */
+    const double *vel;         /* [n][3] */
+    const int64_t *nbr_off;    /* [n+1] */
+    const int32_t *nbr_idx;
+    const uint8_t *is_bdy;     /* [n] */
+    const double *n_coll;      /* [n] collision partner density */
+    const double *T;           /* [n] */
+    const double *v_turb;      /* [n] */
+    const double *n_spec;      /* [n] */
+    int32_t n_lev;
+    int32_t n_lines;
+    const double *E;           /* [n_lev] */
+    const double *g;           /* [n_lev] */
+    double mass;
+    const int32_t *up;         /* [n_lines] */
+    const int32_t *lo;
+    const double *A;
+    int32_t n_T;
+    int32_t pad1;
+    const double *T_grid;      /* [n_T] */
+    const double *K_down;      /* [n_lev(n_lev-1)/2][n_T] pair order (1,0),(2,0),(2,1),... */
+    int32_t R;                 /* number of ray directions */
+    int32_t Q;                 /* frequency bins per line */
+    const double *dirs;        /* [R][3] */
+    const int32_t *antipode;   /* [R] */
+    const double *roots;       /* [Q] */
+    const double *weights;     /* [Q] */
+    double dshift_frac;        /* velocity step as a fraction of the local width */
+    double chi_min;            /* opacity floor, m^-1 */
+    double dtau_min;           /* optical-depth increment floor */
+    double T_cmb;              /* boundary black-body temperature */
+    int64_t max_steps;         /* per half-ray cap on traced cells */
+} or_model;
+
+/* ------------------------------------------------------------------ line data */
+
+/* Line-centre frequency nu_ij = (E_i - E_j)/h. */
+static double line_nu(const or_model *m, int l) {
+    return (m->E[m->up[l]] - m->E[m->lo[l]]) / H_PLANCK;
+}
+
+/* Einstein B coefficients from A (textbook relations; the paper takes A from LAMDA):
+ * B_ul = A_ul c^2 / (2 h nu^3), B_lu = (g_u/g_l) B_ul. */
+static void einstein_b(const or_model *m, int l, double *Bul, double *Blu) {
+    double nu = line_nu(m, l);
+    *Bul = m->A[l] * C_LIGHT * C_LIGHT / (2.0 * H_PLANCK * nu * nu * nu);
+    *Blu = m->g[m->up[l]] / m->g[m->lo[l]] * (*Bul);
+}
+
+/* Velocity width b = sqrt(v_thermal^2 + v_turb^2), v_thermal = sqrt(2 k T / m_spec)
+ * (Sec. 2.2.1, characteristic line width delta_nu = nu/c * b). Operation order is
+ * fixed because the ray tracer compares velocity steps against it bit for bit. */
+double or_width(const or_model *m, int64_t c) {
+    double vth2 = 2.0 * K_BOLTZ * m->T[c] / m->mass;
+    return sqrt(vth2 + m->v_turb[c] * m->v_turb[c]);
+}
+
+/* Emissivity and opacity line integrals without the profile (eq. 'lines'):
+ * eta_int = h nu/4pi n_u A_ul, chi_int = h nu/4pi (n_l B_lu - n_u B_ul). */
+static void line_integrals(const or_model *m, const double *pops, int64_t c, int l,
+                           double *eta_int, double *chi_int) {
+    double nu = line_nu(m, l), Bul, Blu;
+    einstein_b(m, l, &Bul, &Blu);
+    double nu_ = pops[c * m->n_lev + m->up[l]];
+    double nl_ = pops[c * m->n_lev + m->lo[l]];
+    double pre = H_PLANCK * nu / (4.0 * M_PI);
+    *eta_int = pre * nu_ * m->A[l];
+    *chi_int = pre * (nl_ * Blu - nu_ * Bul);
+}
+
+/* Planck function B_nu(T). */
+static double planck(double nu, double T) {
+    return 2.0 * H_PLANCK * nu * nu * nu / (C_LIGHT * C_LIGHT) / (exp(H_PLANCK * nu / (K_BOLTZ * T)) - 1.0);
+}
+
+/* LTE (Boltzmann) populations: n_i = n g_i exp(-E_i/kT) / sum_j g_j exp(-E_j/kT). */
+int or_lte(const or_model *m, double *pops) {
+    for (int64_t c = 0; c < m->n; c++) {
+        double Z = 0.0;
+        for (int i = 0; i < m->n_lev; i++) Z += m->g[i] * exp(-m->E[i] / (K_BOLTZ * m->T[c]));
+        for (int i = 0; i < m->n_lev; i++)
+            pops[c * m->n_lev + i] = m->n_spec[c] * m->g[i] * exp(-m->E[i] / (K_BOLTZ * m->T[c])) / Z;
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------ ray tracing */
+
+/* Half-ray from origin o along direction r (Sec. 3.2, Fig. 'ray_tracing'):
+ * from the current cell, take the neighbour whose projection on the ray lies strictly
+ * farther than the current cell's and which lies closest to the ray; stop after a
+ * boundary cell.
+ * Readings: ties go to the smaller squared distance, then the smaller projection, then
+ * the smaller index; a cell with no farther neighbour ends the ray as a dead end; the
+ * origin itself never stops the walk.
+ * Outputs per element e (the origin is not an element): cell index, the number of
+ * points inserted before it by the velocity-step rule, the path length from the
+ * previous point, and the line-of-sight velocity n.(v_e - v_o). */
+static int trace_3d(const or_model *m, int64_t o, int r, int64_t cap, int32_t *cells,
+                    double *ds, double *vpar, int64_t *len, int *dead_end) {
+    const double *n = &m->dirs[3 * r];
+    const double *xo = &m->pos[3 * o];
+    int64_t cur = o;
+    double s_cur = 0.0;
+    *len = 0;
+    *dead_end = 0;
+    for (;;) {
+        int64_t best = -1;
+        double bs = 0.0, bd2 = 0.0;
+        for (int64_t e = m->nbr_off[cur]; e < m->nbr_off[cur + 1]; e++) {
+            int64_t c = m->nbr_idx[e];
+            double dx = m->pos[3 * c + 0] - xo[0];
+            double dy = m->pos[3 * c + 1] - xo[1];
+            double dz = m->pos[3 * c + 2] - xo[2];
+            double s = dx * n[0] + dy * n[1] + dz * n[2];
+            if (!(s > s_cur)) continue;
+            double px = dx - s * n[0], py = dy - s * n[1], pz = dz - s * n[2];
+            double d2 = px * px + py * py + pz * pz;
+            int better = (best < 0) || (d2 < bd2) || (d2 == bd2 && s < bs) ||
+                         (d2 == bd2 && s == bs && c < best);
+            if (better) { best = c; bs = s; bd2 = d2; }
+        }
+        if (best < 0) { *dead_end = 1; break; }
+        if (*len >= cap) return -1;
+        const double *vb = &m->vel[3 * best], *vo = &m->vel[3 * o];
+        cells[*len] = (int32_t)best;
+        ds[*len] = bs - s_cur;
+        vpar[*len] = n[0] * (vb[0] - vo[0]) + n[1] * (vb[1] - vo[1]) + n[2] * (vb[2] - vo[2]);
+        (*len)++;
+        s_cur = bs;
+        cur = best;
+        if (m->is_bdy[best]) break;
+    }
+    return 0;
+}
+
+/* Spherically symmetric model (points on the +z axis at increasing radii r_j): a ray
+ * from r_o with mu = n.z crosses sphere j where s = -r_o mu +- sqrt(r_j^2 - r_o^2(1-mu^2));
+ * the elements are the crossings in increasing s. Reading: radii below the innermost
+ * point form an empty core; the chord across it carries no optical depth (path length 0),
+ * as in the paper's power-law model with an empty core (Sec. 4.1.2). A centre point
+ * (r_0 = 0) is a single point, not a sphere. */
+static int trace_sph1d(const or_model *m, int64_t o, int r, int64_t cap, int32_t *cells,
+                       double *ds, double *vpar, int64_t *len) {
+    const double *n = &m->dirs[3 * r];
+    double mu = n[2];
+    double ro = m->pos[3 * o + 2];
+    double p2 = ro * ro * (1.0 - mu * mu);   /* squared impact parameter */
+    double vro = m->vel[3 * o + 2];
+    int64_t N = m->n;
+    *len = 0;
+    double s_prev = 0.0;
+    /* inward leg: shells o-1 .. jmin on the near side (only when mu < 0) */
+    int64_t j = o;
+    int through_core = 0;
+    if (mu < 0.0 && ro > 0.0) {
+        for (j = o - 1; j >= 0; j--) {
+            double rj = m->pos[3 * j + 2];
+            double q = rj * rj - p2;
+            if (rj == 0.0 && p2 == 0.0) {
+                /* a radial ray passes through the centre point itself */
+                double s = -ro * mu;
+                if (*len >= cap) return -1;
+                cells[*len] = (int32_t)j;
+                ds[*len] = s - s_prev;
+                vpar[*len] = -vro * mu;
+                (*len)++;
+                s_prev = s;
+                j--;
+                break;
+            }
+            if (!(q > 0.0) || rj == 0.0) break;
+            double s = -ro * mu - sqrt(q);
+            if (*len >= cap) return -1;
+            cells[*len] = (int32_t)j;
+            ds[*len] = s - s_prev;
+            vpar[*len] = m->vel[3 * j + 2] * (ro * mu + s) / rj - vro * mu;
+            (*len)++;
+            s_prev = s;
+        }
+        if (j < 0 && m->pos[2] > 0.0) through_core = 1;
+        j = j + 1;   /* innermost shell crossed on the near side (or o itself) */
+        if (j == 0 && m->pos[2] == 0.0) j = 1;   /* the centre point has no far side */
+    }
+    /* outward leg: far-side crossings of shells j .. N-1 (plus shell o when going in) */
+    int64_t jstart;
+    if (mu < 0.0 && ro > 0.0) jstart = j;           /* turning shell and outwards */
+    else jstart = o + 1;                              /* straight out */
+    for (int64_t k = jstart; k < N; k++) {
+        double rk = m->pos[3 * k + 2];
+        double q = rk * rk - p2;
+        if (q < 0.0) continue;
+        double s = -ro * mu + sqrt(q);
+        if (!(s > s_prev) && !(through_core && k == jstart)) continue;
+        if (*len >= cap) return -1;
+        cells[*len] = (int32_t)k;
+        if (through_core && k == jstart) { ds[*len] = 0.0; }
+        else ds[*len] = s - s_prev;
+        vpar[*len] = (rk > 0.0 ? m->vel[3 * k + 2] * (ro * mu + s) / rk : 0.0) - vro * mu;
+        (*len)++;
+        s_prev = s;
+    }
+    return 0;
+}
+
+/* Velocity-step rule (Sec. 3.1.1 and 3.2): when the line-of-sight velocity changes by
+ * more than a fraction f of the local width between consecutive points, insert
+ * ceil(dv/(f*min(b_a,b_b))) - 1 interpolated points. The previous point of element 0
+ * is the origin (line-of-sight velocity 0). */
+static void velocity_steps(const or_model *m, int64_t o, int64_t len, const int32_t *cells,
+                           const double *vpar, int32_t *nsub) {
+    double va = 0.0, ba = or_width(m, o);
+    for (int64_t e = 0; e < len; e++) {
+        double vb = vpar[e], bb = or_width(m, cells[e]);
+        double dv = fabs(vb - va);
+        double wmin = ba < bb ? ba : bb;
+        double lim = m->dshift_frac * wmin;
+        nsub[e] = 0;
+        if (dv > lim) nsub[e] = (int32_t)ceil(dv / lim) - 1;
+        va = vb; ba = bb;
+    }
+}
+
+int or_trace(const or_model *m, int64_t o, int r, int64_t cap, int32_t *cells, int32_t *nsub,
+             double *ds, double *vpar, int64_t *len, int *dead_end) {
+    int rc;
+    *dead_end = 0;
+    if (m->geometry == 1) rc = trace_sph1d(m, o, r, cap, cells, ds, vpar, len);
+    else rc = trace_3d(m, o, r, cap, cells, ds, vpar, len, dead_end);
+    if (rc) return rc;
+    velocity_steps(m, o, *len, cells, vpar, nsub);
+    return 0;
+}
+
+/* ------------------------------------------------------------------ Feautrier solve */
+
+/* Second-order transfer equation d^2u/dtau^2 = u - S on one ray pair (eq. 'GFE' with no
+ * scattering), discretised on K points with increments dtau[0..K-2]:
+ *   interior:  -A_k u_{k-1} + (1 + A_k + C_k) u_k - C_k u_{k+1} = S_k,
+ *              A_k = 2/((dtau_{k-1}+dtau_k) dtau_{k-1}), C_k = 2/((dtau_{k-1}+dtau_k) dtau_k);
+ *   ends (Auer 1967 second-order boundary condition with incoming intensity I):
+ *              (1 + 2/dtau + 2/dtau^2) u_0 - (2/dtau^2) u_1 = S_0 + (2/dtau) I_0, mirrored.
+ * Solved with the Rybicki & Hummer (1991) elimination, which carries the row excess
+ * H_k = B_k - A_k - C_k separately (1 in the interior, 1 + 2/dtau at the ends):
+ *   F_k = (H_k + A_k F_{k-1}/(1+F_{k-1})) / C_k,  z_k = (R_k + A_k z_{k-1}) / (C_k (1+F_k)),
+ *   u_k = z_k + u_{k+1}/(1+F_k);
+ * the diagonal of the inverse (the local approximate Lambda operator) follows from the
+ * forward F and the backward G recursions:
+ *   (T^-1)_kk = 1 / (H_k + A_k F_{k-1}/(1+F_{k-1}) + C_k G_{k+1}/(1+G_{k+1})).
+ * Returns u at index ko and (T^-1)_{ko,ko}. Work arrays: 5*K doubles. */
+int or_feautrier(int64_t K, int64_t ko, const double *dtau, const double *S, double I0,
+                 double IK, double *u_o, double *lam_o, double *work) {
+    if (K == 1) { *u_o = 0.5 * (I0 + IK); *lam_o = 0.0; return 0; }
+    double *A = work, *C = work + K, *H = work + 2 * K, *F = work + 3 * K, *z = work + 4 * K;
+    for (int64_t k = 0; k < K; k++) {
+        if (k == 0) {
+            A[k] = 0.0; C[k] = 2.0 / (dtau[0] * dtau[0]); H[k] = 1.0 + 2.0 / dtau[0];
+        } else if (k == K - 1) {
+            A[k] = 2.0 / (dtau[k - 1] * dtau[k - 1]); C[k] = 0.0; H[k] = 1.0 + 2.0 / dtau[k - 1];
+        } else {
+            A[k] = 2.0 / ((dtau[k - 1] + dtau[k]) * dtau[k - 1]);
+            C[k] = 2.0 / ((dtau[k - 1] + dtau[k]) * dtau[k]);
+            H[k] = 1.0;
+        }
+    }
+    /* right-hand side */
+    #define RHS(k) ((k) == 0 ? S[0] + 2.0 / dtau[0] * I0 : \
+                    ((k) == K - 1 ? S[K - 1] + 2.0 / dtau[K - 2] * IK : S[k]))
+    /* forward elimination */
+    F[0] = H[0] / C[0];
+    z[0] = RHS(0) / (H[0] + C[0]);
+    for (int64_t k = 1; k < K - 1; k++) {
+        F[k] = (H[k] + A[k] * F[k - 1] / (1.0 + F[k - 1])) / C[k];
+        z[k] = (RHS(k) + A[k] * z[k - 1]) / (C[k] * (1.0 + F[k]));
+    }
+    /* last row and back substitution down to ko */
+    double u = (RHS(K - 1) + A[K - 1] * z[K - 2]) / (H[K - 1] + A[K - 1] * F[K - 2] / (1.0 + F[K - 2]));
+    for (int64_t k = K - 2; k >= ko; k--) u = z[k] + u / (1.0 + F[k]);
+    *u_o = u;
+    #undef RHS
+    /* backward recursion G from the far end down to ko+1 */
+    double Gn = 0.0;   /* G_{ko+1} */
+    int have_G = 0;
+    if (ko < K - 1) {
+        double G = H[K - 1] / A[K - 1];
+        for (int64_t k = K - 2; k > ko; k--) G = (H[k] + C[k] * G / (1.0 + G)) / A[k];
+        Gn = G; have_G = 1;
+    }
+    double diag = H[ko];
+    if (ko > 0) diag += A[ko] * F[ko - 1] / (1.0 + F[ko - 1]);
+    if (have_G) diag += C[ko] * Gn / (1.0 + Gn);
+    *lam_o = 1.0 / diag;
+    return 0;
+}
+
+/* One expanded point of a ray pair: position and per-line data (interpolated for the
+ * points inserted by the velocity-step rule). */
+typedef struct {
+    int64_t K, ko, cap;
+    double *dsk;      /* [K-1] path length between points k and k+1 */
+    double *vpar;     /* [K] line-of-sight velocity relative to the origin (half-ray sign) */
+    double *b;        /* [K] velocity width */
+    double *eta;      /* [n_lines][K] eta_int */
+    double *chi;      /* [n_lines][K] chi_int */
+} pair_pts;
+
+static int pair_alloc(pair_pts *p, int64_t cap, int nl) {
+    p->cap = cap;
+    p->dsk = malloc(sizeof(double) * cap);
+    p->vpar = malloc(sizeof(double) * cap);
+    p->b = malloc(sizeof(double) * cap);
+    p->eta = malloc(sizeof(double) * cap * nl);
+    p->chi = malloc(sizeof(double) * cap * nl);
+    return (p->dsk && p->vpar && p->b && p->eta && p->chi) ? 0 : -1;
+}
+static void pair_free(pair_pts *p) {
+    free(p->dsk); free(p->vpar); free(p->b); free(p->eta); free(p->chi);
+}
+
+/* Per-cell line integrals for all cells (eq. 'lines' without the profile). */
+static void all_line_integrals(const or_model *m, const double *pops, double *eta_c, double *chi_c) {
+    for (int64_t c = 0; c < m->n; c++)
+        for (int l = 0; l < m->n_lines; l++)
+            line_integrals(m, pops, c, l, &eta_c[l * m->n + c], &chi_c[l * m->n + c]);
+}
+
+/* Points of one half-ray in order of increasing distance from the origin, each
+ * original element preceded by its inserted points (linear interpolation with weight
+ * j/(nsub+1) between the previous point and the element). Calls emit() per point. */
+static int64_t expand_half(const or_model *m, int64_t o, int64_t len, const int32_t *cells,
+                           const int32_t *nsub, const double *ds, const double *vpar,
+                           const double *eta_c, const double *chi_c,
+                           double *o_ds, double *o_v, double *o_b, double *o_eta, double *o_chi,
+                           int64_t stride, int64_t cap) {
+    int nl = m->n_lines;
+    int64_t cnt = 0;
+    int64_t prev = o;
+    double pv = 0.0;
+    for (int64_t e = 0; e < len; e++) {
+        int64_t c = cells[e];
+        int ns = nsub[e];
+        for (int j = 1; j <= ns + 1; j++) {
+            double w = (double)j / (double)(ns + 1);
+            if (cnt >= cap) return -1;
+            o_ds[cnt] = ds[e] / (double)(ns + 1);
+            o_v[cnt] = (1.0 - w) * pv + w * vpar[e];
+            o_b[cnt] = (1.0 - w) * or_width(m, prev) + w * or_width(m, c);
+            for (int l = 0; l < nl; l++) {
+                o_eta[l * stride + cnt] = (1.0 - w) * eta_c[l * m->n + prev] + w * eta_c[l * m->n + c];
+                o_chi[l * stride + cnt] = (1.0 - w) * chi_c[l * m->n + prev] + w * chi_c[l * m->n + c];
+            }
+            cnt++;
+        }
+        prev = c;
+        pv = vpar[e];
+    }
+    return cnt;
+}
+
+/* Formal solution at a list of origin points (Sec. 3.3 and 3.4):
+ * for each ray pair p and each line l and Gauss-Hermite bin q, the frequency at the
+ * origin is nu = nu_l + r_q delta_nu_l(o); at every point along the pair the opacity and
+ * emissivity sum the Gaussian profiles of all lines at the Doppler-shifted frequency;
+ * dtau = (chi_k + chi_{k+1})/2 * ds; the pair is solved for u and the diagonal ALO.
+ * Outputs per origin and line (Sec. 3.4, eq. 'L_operator', 'ALO', 'ourJeff'):
+ *   J    = (1/P) sum_p sum_q w_q u,
+ *   L    = (1/P) sum_p sum_q w_q Lambda*_oo chi_l/chi,
+ *   Jeff = (1/P) sum_p sum_q w_q (u - Lambda*_oo eta_l/chi),
+ * with P = R/2 ray pairs. Reading: the 1/2 in eq. 'L_operator' turns the average over
+ * all rays into the average over ray pairs, since u(n) = u(-n).
+ * The Doppler-shifted profile argument x = (nu s - nu_l')/delta_nu_l'(k), with comoving
+ * factor s = 1 - v_par/c (the paper's Hubble-Lemaitre formula, eq. 'optical_depth'), is
+ * evaluated in velocity units, x = (c (nu_l-nu_l')/nu_l' + (nu_l/nu_l')(r_q b_o (1 - v/c) - v)) / b_k,
+ * which is the same expression without the cancellation of nu s - nu_l'.
+ * Jnu (optional, [n_orig][n_lines][Q]) = (1/P) sum_p u per bin. */
+int or_formal_solve(const or_model *m, const double *pops, int64_t n_orig, const int64_t *origins,
+                    double *J, double *L, double *Jeff, double *Jnu, int nthreads) {
+    int nl = m->n_lines, Q = m->Q, R = m->R;
+    int64_t N = m->n;
+    double *eta_c = malloc(sizeof(double) * N * nl), *chi_c = malloc(sizeof(double) * N * nl);
+    if (!eta_c || !chi_c) return -2;
+    all_line_integrals(m, pops, eta_c, chi_c);
+    int npairs = 0;
+    int32_t *pf = malloc(sizeof(int32_t) * R), *pb = malloc(sizeof(int32_t) * R);
+    for (int r = 0; r < R; r++) if (r < m->antipode[r]) { pf[npairs] = r; pb[npairs] = m->antipode[r]; npairs++; }
+    int err = 0;
+    int64_t cap = m->max_steps;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+    #pragma omp parallel for schedule(dynamic, 1) reduction(|:err)
+#endif
+    for (int64_t io = 0; io < n_orig; io++) {
+        int64_t o = origins[io];
+        int32_t *cf = malloc(sizeof(int32_t) * cap), *cb = malloc(sizeof(int32_t) * cap);
+        int32_t *nf = malloc(sizeof(int32_t) * cap), *nb = malloc(sizeof(int32_t) * cap);
+        double *dsf = malloc(sizeof(double) * cap), *dsb = malloc(sizeof(double) * cap);
+        double *vf = malloc(sizeof(double) * cap), *vb = malloc(sizeof(double) * cap);
+        int64_t ecap = 0;
+        double *hds = NULL, *hv = NULL, *hb = NULL, *heta = NULL, *hchi = NULL;
+        double *chi = NULL, *eta = NULL, *S = NULL, *dtau = NULL, *work = NULL;
+        pair_pts P; P.cap = 0; P.dsk = P.vpar = P.b = P.eta = P.chi = NULL;
+        double *accJ = calloc(nl, sizeof(double)), *accL = calloc(nl, sizeof(double)), *accE = calloc(nl, sizeof(double));
+        double *accN = calloc((size_t)nl * Q, sizeof(double));
+        if (!cf || !cb || !nf || !nb || !dsf || !dsb || !vf || !vb || !accN) { err |= 1; continue; }
+        double bo = or_width(m, o);
+        for (int p = 0; p < npairs; p++) {
+            int64_t lf, lb; int de;
+            if (or_trace(m, o, pf[p], cap, cf, nf, dsf, vf, &lf, &de)) { err |= 2; break; }
+            if (or_trace(m, o, pb[p], cap, cb, nb, dsb, vb, &lb, &de)) { err |= 2; break; }
+            int64_t need = 1;
+            for (int64_t e = 0; e < lf; e++) need += nf[e] + 1;
+            for (int64_t e = 0; e < lb; e++) need += nb[e] + 1;
+            if (need > ecap) {
+                ecap = 2 * need;
+                free(hds); free(hv); free(hb); free(heta); free(hchi); pair_free(&P);
+                free(chi); free(eta); free(S); free(dtau); free(work);
+                hds = malloc(sizeof(double) * ecap); hv = malloc(sizeof(double) * ecap); hb = malloc(sizeof(double) * ecap);
+                heta = malloc(sizeof(double) * ecap * nl); hchi = malloc(sizeof(double) * ecap * nl);
+                chi = malloc(sizeof(double) * ecap); eta = malloc(sizeof(double) * ecap);
+                S = malloc(sizeof(double) * ecap); dtau = malloc(sizeof(double) * ecap);
+                work = malloc(sizeof(double) * 5 * ecap);
+                if (pair_alloc(&P, ecap, nl) || !hds || !hv || !hb || !heta || !hchi || !chi || !eta || !S || !dtau || !work) { err |= 1; break; }
+            }
+            /* backward half expanded, then reversed into pair order */
+            int64_t eb = expand_half(m, o, lb, cb, nb, dsb, vb, eta_c, chi_c, hds, hv, hb, heta, hchi, ecap, ecap);
+            if (eb < 0) { err |= 4; break; }
+            int64_t K = 0;
+            for (int64_t k = eb - 1; k >= 0; k--) {
+                P.vpar[K] = hv[k]; P.b[K] = hb[k];
+                for (int l = 0; l < nl; l++) { P.eta[l * P.cap + K] = heta[l * ecap + k]; P.chi[l * P.cap + K] = hchi[l * ecap + k]; }
+                P.dsk[K] = hds[k];  /* distance from this point to the next one towards the origin */
+                K++;
+            }
+            P.ko = K;
+            P.vpar[K] = 0.0; P.b[K] = bo;
+            for (int l = 0; l < nl; l++) { P.eta[l * P.cap + K] = eta_c[l * N + o]; P.chi[l * P.cap + K] = chi_c[l * N + o]; }
+            K++;
+            int64_t ef = expand_half(m, o, lf, cf, nf, dsf, vf, eta_c, chi_c, hds, hv, hb, heta, hchi, ecap, ecap);
+            if (ef < 0) { err |= 4; break; }
+            for (int64_t k = 0; k < ef; k++) {
+                P.dsk[K - 1] = hds[k];
+                P.vpar[K] = hv[k]; P.b[K] = hb[k];
+                for (int l = 0; l < nl; l++) { P.eta[l * P.cap + K] = heta[l * ecap + k]; P.chi[l * P.cap + K] = hchi[l * ecap + k]; }
+                K++;
+            }
+            P.K = K;
+            for (int l = 0; l < nl; l++) {
+                double nu_l = line_nu(m, l);
+                for (int q = 0; q < Q; q++) {
+                    double aq = m->roots[q] * bo;        /* r_q b_o */
+                    double chi_lo = 0.0, eta_lo = 0.0;   /* line l's own share at the origin */
+                    for (int64_t k = 0; k < K; k++) {
+                        double v = P.vpar[k], bk = P.b[k];
+                        double ch = 0.0, et = 0.0;
+                        for (int l2 = 0; l2 < nl; l2++) {
+                            double nu2 = line_nu(m, l2);
+                            double x = (C_LIGHT * (nu_l - nu2) / nu2 + (nu_l / nu2) * (aq * (1.0 - v / C_LIGHT) - v)) / bk;
+                            double dnu = nu2 * bk / C_LIGHT;
+                            double phi = exp(-x * x) / (dnu * SQRT_PI);
+                            ch += P.chi[l2 * P.cap + k] * phi;
+                            et += P.eta[l2 * P.cap + k] * phi;
+                            if (k == P.ko && l2 == l) {
+                                chi_lo = P.chi[l2 * P.cap + k] * phi;
+                                eta_lo = P.eta[l2 * P.cap + k] * phi;
+                            }
+                        }
+                        if (ch < m->chi_min) ch = m->chi_min;
+                        chi[k] = ch; eta[k] = et; S[k] = et / ch;
+                    }
+                    for (int64_t k = 0; k + 1 < K; k++) {
+                        double dt = 0.5 * (chi[k] + chi[k + 1]) * P.dsk[k];
+                        dtau[k] = dt < m->dtau_min ? m->dtau_min : dt;
+                    }
+                    /* incoming CMB at both ends, at the comoving frequency there */
+                    double nu_o = nu_l * (1.0 + aq / C_LIGHT);
+                    double I0 = planck(nu_o * (1.0 - P.vpar[0] / C_LIGHT), m->T_cmb);
+                    double IK = planck(nu_o * (1.0 - P.vpar[K - 1] / C_LIGHT), m->T_cmb);
+                    double u, lam;
+                    or_feautrier(K, P.ko, dtau, S, I0, IK, &u, &lam, work);
+                    double w = m->weights[q];
+                    accJ[l] += w * u;
+                    accL[l] += w * lam * chi_lo / chi[P.ko];
+                    accE[l] += w * (u - lam * eta_lo / chi[P.ko]);
+                    accN[l * Q + q] += u;
+                }
+            }
+        }
+        for (int l = 0; l < nl; l++) {
+            J[io * nl + l] = accJ[l] / npairs;
+            L[io * nl + l] = accL[l] / npairs;
+            Jeff[io * nl + l] = accE[l] / npairs;
+            if (Jnu) for (int q = 0; q < Q; q++) Jnu[(io * nl + l) * Q + q] = accN[l * Q + q] / npairs;
+        }
+        free(cf); free(cb); free(nf); free(nb); free(dsf); free(dsb); free(vf); free(vb);
+        free(hds); free(hv); free(hb); free(heta); free(hchi); pair_free(&P);
+        free(chi); free(eta); free(S); free(dtau); free(work); free(accJ); free(accL); free(accE); free(accN);
+    }
+    free(eta_c); free(chi_c); free(pf); free(pb);
+    return err ? -3 : 0;
+}
+
+/* ------------------------------------------------------------------ statistical equilibrium */
+
+/* Collisional de-excitation coefficient of pair (i>j) at temperature T: linear
+ * interpolation in T on the tabulated grid, constant beyond its ends (Reading). */
+static double k_down(const or_model *m, int i, int j, double T) {
+    int pair = i * (i - 1) / 2 + j;
+    const double *k = &m->K_down[pair * m->n_T];
+    const double *Tg = m->T_grid;
+    if (m->n_T == 1 || T <= Tg[0]) return k[0];
+    if (T >= Tg[m->n_T - 1]) return k[m->n_T - 1];
+    int a = 0;
+    while (Tg[a + 1] < T) a++;
+    double t = (T - Tg[a]) / (Tg[a + 1] - Tg[a]);
+    return k[a] + t * (k[a + 1] - k[a]);
+}
+
+/* Dense solve with LU decomposition and partial pivoting (in place). */
+static int lu_solve(int n, double *M, double *b) {
+    for (int c = 0; c < n; c++) {
+        int piv = c;
+        for (int r = c + 1; r < n; r++) if (fabs(M[r * n + c]) > fabs(M[piv * n + c])) piv = r;
+        if (M[piv * n + c] == 0.0) return -1;
+        if (piv != c) {
+            for (int k = 0; k < n; k++) { double t = M[c * n + k]; M[c * n + k] = M[piv * n + k]; M[piv * n + k] = t; }
+            double t = b[c]; b[c] = b[piv]; b[piv] = t;
+        }
+        for (int r = c + 1; r < n; r++) {
+            double f = M[r * n + c] / M[c * n + c];
+            for (int k = c; k < n; k++) M[r * n + k] -= f * M[c * n + k];
+            b[r] -= f * b[c];
+        }
+    }
+    for (int r = n - 1; r >= 0; r--) {
+        double s = b[r];
+        for (int k = r + 1; k < n; k++) s -= M[r * n + k] * b[k];
+        b[r] = s / M[r * n + r];
+    }
+    return 0;
+}
+
+/* Statistical equilibrium of one cell with the diagonal ALO (eq. 'ourALI'):
+ * rate u->l = A_ul (1 - L) + B_ul Jeff + C_ul, rate l->u = B_lu Jeff + C_lu, all
+ * collisional pairs with C_ij = K_ij(T) n_coll and excitation by detailed balance.
+ * Reading: the paper prints the excitation factor exp(+h nu/kT); the physical form
+ * C_lu = C_ul (g_u/g_l) exp(-(E_u - E_l)/kT) is used, the only one that makes high
+ * densities thermalise to LTE. The last equation is replaced by sum_i n_i = n_spec
+ * (Reading). Rates enter the generator matrix M_ij = rate j->i, M_jj = -sum_i rate j->i. */
+static int stateq_cell(const or_model *m, int64_t c, const double *Jc, const double *Lc,
+                       const double *Ec, double *out) {
+    int n = m->n_lev;
+    double P[64 * 64];
+    double M[64 * 64], b[64];
+    if (n > 64) return -1;
+    memset(P, 0, sizeof(double) * n * n);
+    for (int l = 0; l < m->n_lines; l++) {
+        int u = m->up[l], lo = m->lo[l];
+        double Bul, Blu;
+        einstein_b(m, l, &Bul, &Blu);
+        P[u * n + lo] += m->A[l] * (1.0 - Lc[l]) + Bul * Ec[l];
+        P[lo * n + u] += Blu * Ec[l];
+    }
+    double T = m->T[c];
+    for (int i = 1; i < n; i++)
+        for (int j = 0; j < i; j++) {
+            double Cd = k_down(m, i, j, T) * m->n_coll[c];
+            double Cu = Cd * m->g[i] / m->g[j] * exp(-(m->E[i] - m->E[j]) / (K_BOLTZ * T));
+            P[i * n + j] += Cd;
+            P[j * n + i] += Cu;
+        }
+    for (int i = 0; i < n; i++)
+        for (int j = 0; j < n; j++) M[i * n + j] = 0.0;
+    for (int j = 0; j < n; j++)
+        for (int i = 0; i < n; i++) {
+            if (i == j) continue;
+            M[i * n + j] += P[j * n + i];
+            M[j * n + j] -= P[j * n + i];
+        }
+    for (int j = 0; j < n; j++) { M[(n - 1) * n + j] = 1.0; b[j] = 0.0; }
+    b[n - 1] = m->n_spec[c];
+    if (lu_solve(n, M, b)) return -2;
+    for (int i = 0; i < n; i++) out[i] = b[i];
+    return 0;
+}
+
+/* Level populations of all cells from J, L, Jeff ([n][n_lines]). Validity check
+ * (Sec. 6.1): a cell whose populations come out negative or non-finite is solved again
+ * with part of the ALO removed; here the diagonal ALO is dropped (L = 0, Jeff = J).
+ * Returns the number of such cells in *n_fallback. */
+int or_stateq(const or_model *m, const double *J, const double *L, const double *Jeff,
+              double *pops_out, int64_t *n_fallback) {
+    int nl = m->n_lines, n = m->n_lev;
+    int64_t nf = 0;
+    double zeros[64];
+    for (int l = 0; l < 64; l++) zeros[l] = 0.0;
+    for (int64_t c = 0; c < m->n; c++) {
+        double *out = &pops_out[c * n];
+        int rc = stateq_cell(m, c, &J[c * nl], &L[c * nl], &Jeff[c * nl], out);
+        int bad = rc != 0;
+        for (int i = 0; i < n && !bad; i++) if (!(out[i] >= 0.0) || !isfinite(out[i])) bad = 1;
+        if (bad) {
+            nf++;
+            if (stateq_cell(m, c, &J[c * nl], zeros, &J[c * nl], out)) return -1;
+        }
+    }
+    *n_fallback = nf;
+    return 0;
+}
+
+/* Maximum relative change over cells and levels with n_i/n_spec >= 1e-10 (Reading: the
+ * paper quotes the relative change in level populations without naming the norm). */
+double or_max_rel_change(const or_model *m, const double *old, const double *new_) {
+    double mx = 0.0;
+    for (int64_t c = 0; c < m->n; c++)
+        for (int i = 0; i < m->n_lev; i++) {
+            double a = new_[c * m->n_lev + i], b = old[c * m->n_lev + i];
+            if (a < 1e-10 * m->n_spec[c]) continue;
+            double d = fabs(a - b) / a;
+            if (d > mx) mx = d;
+        }
+    return mx;
+}
+
+/* Ng acceleration (Sec. 3.4; Ng 1974, Olson et al. 1986) from four iterates x0 (newest)
+ * .. x3 with differences D_i = x_i - x_{i+1}: minimise |D0 - a1 (D0-D1) - a2 (D0-D2)|^2
+ * with uniform weights, then x = (1-a1-a2) x0 + a1 x1 + a2 x2. Returns -1 if the
+ * normal equations are singular. */
+int or_ng(int64_t n, const double *x0, const double *x1, const double *x2, const double *x3,
+          double *out) {
+    double a11 = 0, a12 = 0, a22 = 0, b1 = 0, b2 = 0;
+    for (int64_t k = 0; k < n; k++) {
+        double D0 = x0[k] - x1[k], D1 = x1[k] - x2[k], D2 = x2[k] - x3[k];
+        double Q1 = D0 - D1, Q2 = D0 - D2;
+        a11 += Q1 * Q1; a12 += Q1 * Q2; a22 += Q2 * Q2;
+        b1 += Q1 * D0; b2 += Q2 * D0;
+    }
+    double det = a11 * a22 - a12 * a12;
+    if (det == 0.0 || !isfinite(det)) return -1;
+    double a1 = (b1 * a22 - b2 * a12) / det;
+    double a2 = (a11 * b2 - a12 * b1) / det;
+    for (int64_t k = 0; k < n; k++) out[k] = (1.0 - a1 - a2) * x0[k] + a1 * x1[k] + a2 * x2[k];
+    return 0;
+}
+
+/* Accelerated Lambda iteration (Sec. 2.2.1, 3.4): formal solve -> statistical
+ * equilibrium -> convergence check, optionally with an Ng step every ng_period
+ * iterations on the fractional populations n_i/n_spec (Reading: "uniform weighting" is
+ * taken over levels of the fractional populations). pops holds the start and receives
+ * the result. changes[it] gets each iteration's max relative change. Returns the
+ * number of iterations, negative on error; *converged is set when change < tol. */
+int or_ali(const or_model *m, double *pops, double tol, int max_iter, int ng_period,
+           double *changes, int *converged, int nthreads) {
+    int64_t N = m->n, nl = m->n_lines, nv = m->n * m->n_lev;
+    double *J = malloc(sizeof(double) * N * nl), *L = malloc(sizeof(double) * N * nl);
+    double *E = malloc(sizeof(double) * N * nl), *nw = malloc(sizeof(double) * nv);
+    double *hist[4];
+    for (int i = 0; i < 4; i++) hist[i] = malloc(sizeof(double) * nv);
+    double *ng_out = malloc(sizeof(double) * nv);
+    int64_t *orig = malloc(sizeof(int64_t) * N);
+    for (int64_t c = 0; c < N; c++) orig[c] = c;
+    int nh = 0, it = 0;
+    *converged = 0;
+    for (it = 0; it < max_iter; it++) {
+        if (or_formal_solve(m, pops, N, orig, J, L, E, NULL, nthreads)) { it = -1; break; }
+        int64_t nf;
+        if (or_stateq(m, J, L, E, nw, &nf)) { it = -2; break; }
+        double ch = or_max_rel_change(m, pops, nw);
+        changes[it] = ch;
+        memcpy(pops, nw, sizeof(double) * nv);
+        if (ch < tol) { *converged = 1; it++; break; }
+        if (ng_period > 0) {
+            double *t = hist[3]; hist[3] = hist[2]; hist[2] = hist[1]; hist[1] = hist[0]; hist[0] = t;
+            for (int64_t c = 0; c < N; c++)
+                for (int i = 0; i < m->n_lev; i++) hist[0][c * m->n_lev + i] = pops[c * m->n_lev + i] / m->n_spec[c];
+            if (nh < 4) nh++;
+            if (nh == 4 && (it + 1) % ng_period == 0) {
+                if (or_ng(nv, hist[0], hist[1], hist[2], hist[3], ng_out) == 0) {
+                    int ok = 1;
+                    for (int64_t k = 0; k < nv; k++) if (!(ng_out[k] >= 0.0)) { ok = 0; break; }
+                    if (ok)
+                        for (int64_t c = 0; c < N; c++)
+                            for (int i = 0; i < m->n_lev; i++)
+                                pops[c * m->n_lev + i] = ng_out[c * m->n_lev + i] * m->n_spec[c];
+                }
+                nh = 0;
+            }
+        }
+    }
+    free(J); free(L); free(E); free(nw); free(ng_out); free(orig);
+    for (int i = 0; i < 4; i++) free(hist[i]);
+    return it;
+}

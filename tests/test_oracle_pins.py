@@ -1,0 +1,480 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something independent of its own code: values the
+paper prints, closed-form solutions, dense linear algebra, invariants, and limits.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy.special import erf
+
+import synthetic as syn
+from oracle import Oracle, healpix_dirs, antipodes, gauss_hermite, planck, CONST
+from oracle.oracle import feautrier, ng
+
+GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_printed_values.json")))
+h, kB, c = CONST["h"], CONST["kB"], CONST["c"]
+
+
+def sig(x, d):
+    return float(f"{x:.{d}g}")
+
+
+# ------------------------------------------------------------------ printed values
+def test_printed_line_frequency_and_widths():
+    """nu_21 = 179.88 GHz and delta_nu = 519.03 kHz / 357.53 kHz (Sec. 4.1.1, 4.1.2)."""
+    g = GOLD
+    sp = syn.species_two_level()
+    m = syn.hubble_line_1d(n_cells=4)
+    nu21 = (sp.E[1] - sp.E[0]) / h
+    assert sig(nu21 / 1e9, g["line_frequency"]["digits"]) == g["line_frequency"]["nu21_GHz"]
+    for key in ("width_hubble", "width_powerlaw"):
+        e = g[key]
+        mm = syn.model_line_1d(np.array([0.0, 1.0]), 0.0, 1e10, e["T_K"], e["v_turb_m_s"], 1e-6, sp, 7)
+        o = Oracle(mm)
+        dnu = nu21 * o.width(0) / c
+        assert sig(dnu / 1e3, e["digits"]) == e["delta_nu_kHz"], (key, dnu)
+
+
+# ------------------------------------------------------------------ quadrature
+@pytest.mark.parametrize("Q", [1, 2, 7, 24, 31, 63, 100])
+def test_gauss_hermite_moments(Q):
+    """Profile-normalised Gauss-Hermite rule is exact for polynomials of degree < 2Q:
+    sum w r^(2k) = (2k-1)!!/2^k (moments of exp(-x^2)/sqrt(pi)), odd moments vanish."""
+    r, w = gauss_hermite(Q)
+    assert abs(w.sum() - 1.0) < 1e-12
+    if Q > 1:
+        assert abs((w * r * r).sum() - 0.5) < 1e-12
+    # scaled moments to keep the check well conditioned
+    for k in range(0, min(Q, 12)):
+        exact = math.prod(range(1, 2 * k, 2)) / 2 ** k
+        assert abs((w * r ** (2 * k)).sum() - exact) <= 1e-10 * max(1.0, exact)
+        assert abs((w * r ** (2 * k + 1)).sum()) <= 1e-10 * max(1.0, exact)
+
+
+@pytest.mark.parametrize("Q", [5, 31, 63])
+def test_gauss_hermite_vs_library_weights(Q):
+    """The paper's weight formula equals the library Gauss-Hermite weights / sqrt(pi)."""
+    from numpy.polynomial.hermite import hermgauss
+    r, w = gauss_hermite(Q)
+    r2, w2 = hermgauss(Q)
+    assert np.allclose(r, r2, rtol=1e-12, atol=1e-13)
+    assert np.allclose(w, w2 / math.sqrt(math.pi), rtol=1e-9, atol=1e-300)
+
+
+# ------------------------------------------------------------------ directions
+@pytest.mark.parametrize("nside", [1, 2, 4])
+def test_healpix_directions(nside):
+    """12 nside^2 unit vectors, antipodal, summing to zero; ring heights follow the
+    equal-area HEALPix formulas (4 i pixels on polar ring i at z = 1 - i^2/(3 n^2),
+    4 n pixels per belt ring at z = 4/3 - 2 i/(3 n))."""
+    d = healpix_dirs(nside)
+    R = 12 * nside * nside
+    assert d.shape == (R, 3)
+    assert np.allclose(np.linalg.norm(d, axis=1), 1.0, atol=1e-15)
+    a = antipodes(d)
+    assert np.all(a[a] == np.arange(R))
+    assert np.abs(d + d[a]).max() < 1e-15
+    assert np.abs(d.sum(0)).max() < 1e-13
+    zs, counts = np.unique(np.round(d[:, 2], 12), return_counts=True)
+    expect = {}
+    n = nside
+    for i in range(1, n):
+        expect[round(1 - i * i / (3 * n * n), 12)] = 4 * i
+        expect[round(-(1 - i * i / (3 * n * n)), 12)] = 4 * i
+    for i in range(n, 3 * n + 1):
+        expect[round(4 / 3 - 2 * i / (3 * n), 12)] = 4 * n
+    assert dict(zip(zs.tolist(), counts.tolist())) == expect
+    if nside == 1:
+        assert abs((d[:, 2] ** 2).mean() - 8.0 / 27.0) < 1e-15
+
+
+# ------------------------------------------------------------------ ray tracer
+def test_trace_lattice_axis_rays():
+    """On a cubic lattice with 26 neighbours, axis rays follow the lattice line exactly
+    and stop at the outer layer."""
+    m = syn.model_lattice_3d(m=7)
+    o = Oracle(m)
+    mm = 7
+    for p in [0, 57, 171, 3 * 49 + 3 * 7 + 3, 200]:
+        i, j, k = p // 49, (p // 7) % 7, p % 7
+        for r, (ax, sgn) in enumerate([(0, 1), (0, -1), (1, 1), (1, -1), (2, 1), (2, -1)]):
+            t = o.trace(p, r)
+            ijk = [i, j, k]
+            exp_cells = []
+            while 0 < ijk[ax] + (0 if not exp_cells and False else 0) and True:
+                break
+            cur = list(ijk)
+            while True:
+                if cur[ax] in (0, mm - 1) and cur != list(ijk):
+                    break
+                if cur[ax] + sgn < 0 or cur[ax] + sgn > mm - 1:
+                    break
+                cur[ax] += sgn
+                exp_cells.append((cur[0] * mm + cur[1]) * mm + cur[2])
+                if m.is_bdy[exp_cells[-1]]:
+                    break
+            assert t["cells"].tolist() == exp_cells, (p, r)
+            assert np.allclose(t["ds"], 1e12)
+            assert not t["dead_end"] or len(exp_cells) == 0
+
+
+def test_trace_invariants_random_mesh():
+    """Each step is a neighbour, projections increase strictly, and every ray ends at a
+    boundary cell or at a counted dead end."""
+    m = syn.model_clumpy_3d(n=3000, seed=3)
+    o = Oracle(m)
+    nbr = [set(m.nbr_idx[m.nbr_off[i]:m.nbr_off[i + 1]].tolist()) for i in range(m.n)]
+    rng = np.random.default_rng(1)
+    dead = 0
+    for p in rng.choice(m.n, 40, replace=False):
+        for r in range(o.dirs.shape[0]):
+            t = o.trace(p, r)
+            prev = p
+            s_prev = 0.0
+            for cell, ds in zip(t["cells"], t["ds"]):
+                assert cell in nbr[prev]
+                s = (m.pos[cell] - m.pos[p]) @ o.dirs[r]
+                assert ds > 0 and s > s_prev
+                assert abs((s - s_prev) - ds) <= 1e-9 * abs(s)
+                s_prev, prev = s, cell
+            if t["dead_end"]:
+                dead += 1
+            elif len(t["cells"]):
+                assert m.is_bdy[t["cells"][-1]]
+    assert dead < 0.05 * 40 * o.dirs.shape[0]
+
+
+def test_trace_sphere_chord_length():
+    """Spherically symmetric shells: the path length to the boundary along a ray equals
+    the paper's l(r, theta) = r cos(theta) + sqrt(R^2 - r^2 sin^2(theta)) (Sec. 4.1.1,
+    theta measured from the inward direction), minus the chord of an empty core."""
+    m = syn.model_sphere_1d(n=60)
+    o = Oracle(m)
+    r = m.pos[:, 2]
+    Rb, Rin = r[-1], r[0]
+    for p in [0, 1, 5, 20, 59]:
+        for k in range(o.dirs.shape[0]):
+            t = o.trace(p, k)
+            mu = o.dirs[k, 2]
+            cth = -mu
+            sth = math.sqrt(max(0.0, 1 - cth * cth))
+            ell = r[p] * cth + math.sqrt(Rb * Rb - r[p] ** 2 * sth * sth)
+            b = r[p] * sth
+            if cth > 0 and b < Rin:
+                ell -= 2 * math.sqrt(Rin * Rin - b * b)
+            if p == len(r) - 1 and mu >= 0:
+                ell = 0.0
+            assert abs(t["ds"].sum() - ell) <= 1e-9 * Rb, (p, k)
+
+
+def test_velocity_step_insertions_closed_form():
+    """Velocity-step rule (Sec. 3.2): with a constant gradient the line-of-sight velocity
+    step between neighbours is c dbeta dz, so each step inserts ceil(dv/(f b)) - 1 points."""
+    m = syn.hubble_line_1d(n_cells=50, c_dbeta=0.5)
+    o = Oracle(m)
+    b = o.width(0)
+    dz = m.pos[1, 2] - m.pos[0, 2]
+    t = o.trace(10, 0)
+    dv = 0.5 * dz
+    expect = math.ceil(dv / (b / 3.0)) - 1
+    assert expect > 3
+    assert np.all(t["nsub"] == expect)
+    assert np.allclose(t["vpar"], 0.5 * (m.pos[t["cells"], 2] - m.pos[10, 2]), rtol=1e-12)
+
+
+# ------------------------------------------------------------------ Feautrier
+def _tridiag(dtau, S, I0, IK):
+    K = S.shape[0]
+    M = np.zeros((K, K)); b = S.copy()
+    for k in range(K):
+        if k == 0:
+            t = dtau[0]; M[0, 0] = 1 + 2 / t + 2 / t ** 2; M[0, 1] = -2 / t ** 2; b[0] += 2 / t * I0
+        elif k == K - 1:
+            t = dtau[-1]; M[k, k] = 1 + 2 / t + 2 / t ** 2; M[k, k - 1] = -2 / t ** 2; b[k] += 2 / t * IK
+        else:
+            a = 2 / ((dtau[k - 1] + dtau[k]) * dtau[k - 1]); cc = 2 / ((dtau[k - 1] + dtau[k]) * dtau[k])
+            M[k, k - 1] = -a; M[k, k + 1] = -cc; M[k, k] = 1 + a + cc
+    return M, b
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_feautrier_vs_dense_lu(seed):
+    """The Rybicki-Hummer elimination gives the dense solution and the dense inverse's
+    diagonal of the assembled second-order system (Auer boundary rows)."""
+    rng = np.random.default_rng(seed)
+    K = int(rng.integers(2, 50))
+    dtau = np.exp(rng.uniform(np.log(1e-2), np.log(1e2), K - 1))
+    S = rng.uniform(0.1, 2.0, K)
+    I0, IK = rng.uniform(0, 1, 2)
+    M, b = _tridiag(dtau, S, I0, IK)
+    u = np.linalg.solve(M, b)
+    Minv = np.linalg.inv(M)
+    for ko in {0, K - 1, K // 2, int(rng.integers(0, K))}:
+        uo, lam = feautrier(dtau, S, I0, IK, ko)
+        assert abs(uo - u[ko]) <= 1e-11 * abs(u[ko])
+        assert abs(lam - Minv[ko, ko]) <= 1e-11 * abs(Minv[ko, ko])
+
+
+def test_feautrier_constant_source():
+    """Constant S with incoming intensity S: u = S everywhere, whatever the opacity."""
+    rng = np.random.default_rng(0)
+    for K in (2, 3, 17, 200):
+        dtau = np.exp(rng.uniform(np.log(1e-9), np.log(1e4), K - 1))
+        S = np.full(K, 3.7)
+        for ko in (0, K // 2, K - 1):
+            u, _ = feautrier(dtau, S, 3.7, 3.7, ko)
+            assert abs(u - 3.7) <= 1e-13 * 3.7
+
+
+def test_feautrier_thin_and_thick_limits():
+    """tau -> 0: u -> (I0 + IK)/2 and Lambda* -> 0; tau -> infinity: u -> S, Lambda* -> 1."""
+    K = 41
+    S = np.full(K, 2.0)
+    u, lam = feautrier(np.full(K - 1, 1e-9), S, 1.0, 0.0, 20)
+    assert abs(u - 0.5) < 1e-6 and lam < 1e-6
+    u, lam = feautrier(np.full(K - 1, 1e3), S, 1.0, 0.0, 20)
+    assert abs(u - 2.0) < 1e-12 and abs(1 - lam) < 1e-5
+
+
+def test_feautrier_second_order_convergence():
+    """Uniform slab of total optical depth T with constant S and incoming I on both
+    sides: u(tau) = S + (I - S)(exp(-tau) + exp(-(T - tau)))/2; the discrete solution
+    converges at second order in dtau."""
+    T, S0, I = 4.0, 1.0, 0.0
+    errs = []
+    for K in (41, 81, 161, 321):
+        dt = T / (K - 1)
+        ko = (K - 1) // 4
+        u, _ = feautrier(np.full(K - 1, dt), np.full(K, S0), I, I, ko)
+        tau = ko * dt
+        exact = S0 + (I - S0) * 0.5 * (math.exp(-tau) + math.exp(-(T - tau)))
+        errs.append(abs(u - exact))
+    rates = [math.log2(errs[i] / errs[i + 1]) for i in range(3)]
+    assert all(1.8 < r < 2.2 for r in rates), rates
+
+
+# ------------------------------------------------------------------ semi-analytic J
+def _lte_S_chi(o):
+    m = o.model
+    sp = m.species
+    pops = o.lte()
+    nu = (sp.E[1] - sp.E[0]) / h
+    Bul = sp.A[0] * c ** 2 / (2 * h * nu ** 3)
+    Blu = sp.g[1] / sp.g[0] * Bul
+    pre = h * nu / (4 * math.pi)
+    eta = pre * pops[:, 1] * sp.A[0]
+    chi = pre * (pops[:, 0] * Blu - pops[:, 1] * Bul)
+    return pops, nu, eta, chi
+
+
+def test_hubble_lemaitre_1d_analytic():
+    """J_nu(r) = S + (B - S)(exp(-tau(R-r)) + exp(-tau(R+r)))/2 with the erf optical
+    depth of eq. 'optical_depth' (Sec. 4.1.1): the paper reports < 1e-4 relative error
+    with 100 cells; refining the grid converges to it."""
+    g = GOLD["hubble_model"]
+    res = {}
+    for ncell in (100, 400):
+        m = syn.hubble_line_1d(n_cells=ncell, n_q=g["n_q"])
+        o = Oracle(m)
+        pops, nu, eta, chi_int = _lte_S_chi(o)
+        S = eta[0] / chi_int[0]
+        x = m.pos[:, 2]
+        dbeta = g["c_dbeta"] / c
+        dnu = nu * o.width(0) / c
+        picks = [ncell // 2, ncell // 4 + 1, 3 * ncell // 4]
+        J, L, E, Jnu = o.formal_solve(pops, np.array(picks), spectrum=True)
+        err = []
+        for i, p in enumerate(picks):
+            r = x[p]
+            for q in range(o.Q):
+                nuq = nu + o.roots[q] * dnu
+                def tau(ell):
+                    return chi_int[0] / (2 * nuq * dbeta) * (erf((nuq - nu) / dnu) - erf((nuq * (1 - dbeta * ell) - nu) / dnu))
+                # incoming CMB at the comoving frequency where it enters (the paper is
+                # silent on the frame of the boundary intensity; a 5e-6 effect here)
+                lp, lm = g["R_m"] - r, g["R_m"] + r
+                Bp = planck(nuq * (1 - dbeta * lp), 2.725)
+                Bm = planck(nuq * (1 - dbeta * lm), 2.725)
+                Jan = S + 0.5 * ((Bp - S) * math.exp(-tau(lp)) + (Bm - S) * math.exp(-tau(lm)))
+                err.append(2 * abs(Jnu[i, 0, q] - Jan) / (Jnu[i, 0, q] + Jan))
+        res[ncell] = np.array(err)
+    assert np.median(res[100]) < 1e-4
+    assert np.max(res[400]) < 1e-4
+    assert np.max(res[400]) < np.max(res[100]) / 4
+
+
+def test_hubble_lemaitre_3d_discrete_directions():
+    """Homogeneous sphere with the Hubble flow (eq. 'Hubble-Lemaitre3D'): the theta
+    integral becomes the average over the HEALPix directions, so only the radial
+    discretisation remains (the paper reports < 1e-4); errors shrink with refinement."""
+    R = 495e3
+    errs = {}
+    for nsh in (50, 200):
+        m = syn.hubble_sphere_1d(n_shells=nsh, n_q=31, nside=2)
+        o = Oracle(m)
+        pops, nu, eta, chi_int = _lte_S_chi(o)
+        S = eta[0] / chi_int[0]
+        dbeta = 0.01 / c
+        dnu = nu * o.width(0) / c
+        rr = m.pos[:, 2]
+        picks = [0, nsh // 3, 2 * nsh // 3]
+        _, _, _, Jnu = o.formal_solve(pops, np.array(picks), spectrum=True)
+        e = []
+        for i, p in enumerate(picks):
+            r = rr[p]
+            for q in range(o.Q):
+                nuq = nu + o.roots[q] * dnu
+                acc = 0.0
+                for d in o.dirs:
+                    cth = -d[2]
+                    sth2 = max(0.0, 1 - cth * cth)
+                    ell = r * cth + math.sqrt(R * R - r * r * sth2)
+                    tau = chi_int[0] / (2 * nuq * dbeta) * (erf((nuq - nu) / dnu) - erf((nuq * (1 - dbeta * ell) - nu) / dnu))
+                    acc += (planck(nuq * (1 - dbeta * ell), 2.725) - S) * math.exp(-tau)
+                acc /= o.dirs.shape[0]
+                Jan = S + acc
+                e.append(2 * abs(Jnu[i, 0, q] - Jan) / (Jnu[i, 0, q] + Jan))
+        errs[nsh] = max(e)
+    # near-tangent chords through a shell are O(sqrt(dr)) long, so the spherical
+    # discretisation converges between first and second order
+    assert errs[200] < 1e-5
+    assert errs[200] < errs[50] / 2
+
+
+def test_powerlaw_1d_analytic():
+    """Power-law density with an empty core (eq. 'density_distribution1D', Sec. 4.1.2),
+    as spherical shells with the two rays along the axis: the optical depths are the
+    closed forms chi_in R_in^2 (1/r - 1/R) outwards and chi_in R_in^2 (1/R_in - 1/r +
+    1/R_in - 1/R) inwards across the empty core. Refinement converges at second order."""
+    g = GOLD["powerlaw_model"]
+    errs = {}
+    for nsh in (100, 400):
+        r = np.geomspace(g["R_in_m"], g["R_m"], nsh)
+        m = syn.model_sphere_1d(n=nsh, r_min=g["R_in_m"], r_max=g["R_m"], n_q=31)
+        m.n_coll = g["n_in"] * (g["R_in_m"] / r) ** 2
+        m.n_spec = g["X"] * m.n_coll
+        m.T[:] = g["T"]; m.v_turb[:] = g["v_turb"]
+        m.dirs = np.array([[0, 0, 1.0], [0, 0, -1.0]])
+        o = Oracle(m)
+        pops, nu, eta, chi_int = _lte_S_chi(o)
+        S = eta[0] / chi_int[0]
+        dnu = nu * o.width(0) / c
+        picks = [nsh // 4, nsh // 2, 3 * nsh // 4]
+        _, _, _, Jnu = o.formal_solve(pops, np.array(picks), spectrum=True)
+        e = []
+        for i, p in enumerate(picks):
+            for q in range(o.Q):
+                nuq = nu + o.roots[q] * dnu
+                phi = math.exp(-o.roots[q] ** 2) / (dnu * math.sqrt(math.pi))
+                k0 = chi_int[0] * phi * g["R_in_m"] ** 2
+                t_out = k0 * (1 / r[p] - 1 / g["R_m"])
+                t_in = k0 * (2 / g["R_in_m"] - 1 / r[p] - 1 / g["R_m"])
+                Jan = S + 0.5 * (planck(nuq, 2.725) - S) * (math.exp(-t_out) + math.exp(-t_in))
+                e.append(2 * abs(Jnu[i, 0, q] - Jan) / (Jnu[i, 0, q] + Jan))
+        errs[nsh] = np.array(e)
+    assert errs[400].max() < 2e-2
+    assert errs[400].max() < errs[100].max() / 8
+
+
+# ------------------------------------------------------------------ statistical equilibrium
+def _two_cell_model(n_coll, T=30.0):
+    sp = syn.species_two_level(A21=1e-5)
+    return syn.model_line_1d(np.array([0.0, 1e10]), 0.0, n_coll, T, 150.0, 1e-8, sp, 5)
+
+
+def test_stateq_two_level_closed_form():
+    """2-level closed form n_u/n_l = (B_lu J + C_lu)/(A_ul + B_ul J + C_ul), n_u + n_l = n."""
+    m = _two_cell_model(1e9)
+    o = Oracle(m)
+    sp = m.species
+    nu = (sp.E[1] - sp.E[0]) / h
+    Bul = sp.A[0] * c ** 2 / (2 * h * nu ** 3); Blu = 3 * Bul
+    Cd = 2e-16 * 1e9; Cu = Cd * 3 * math.exp(-h * nu / (kB * 30.0))
+    for Jv in (0.0, 1e-18, 1e-16):
+        J = np.full((2, 1), Jv)
+        pops, nf = o.stateq(J, np.zeros((2, 1)), J)
+        ratio = (Blu * Jv + Cu) / (sp.A[0] + Bul * Jv + Cd)
+        assert abs(pops[0, 1] / pops[0, 0] - ratio) <= 1e-12 * ratio
+        assert abs(pops[0].sum() - m.n_spec[0]) <= 1e-14 * m.n_spec[0]
+        assert nf == 0
+
+
+def test_stateq_detailed_balance_and_high_density():
+    """J = B_nu(T) gives Boltzmann populations at any density (detailed balance), and a
+    very high density thermalises to Boltzmann whatever J. Fails with the excitation
+    factor exp(+h nu/kT) as printed, which is why the physical form is used."""
+    rng = np.random.default_rng(0)
+    sp = syn.species_rotor(5, rng)
+    for ncoll, useB in ((1e6, True), (1e10, True), (1e22, False)):
+        m = syn.model_line_1d(np.array([0.0, 1e10]), 0.0, ncoll, 40.0, 150.0, 1e-8, sp, 5)
+        o = Oracle(m)
+        nus = (sp.E[sp.up] - sp.E[sp.lo]) / h
+        Jv = planck(nus, 40.0) if useB else np.full(sp.n_lines, 1e-30)
+        J = np.tile(Jv, (2, 1))
+        pops, _ = o.stateq(J, np.zeros_like(J), J)
+        boltz = sp.g * np.exp(-sp.E / (kB * 40.0)); boltz /= boltz.sum()
+        assert np.allclose(pops[0] / m.n_spec[0], boltz, rtol=1e-8 if useB else 1e-6)
+
+
+def test_lte_normalised_boltzmann():
+    m = syn.model_tiny_3d(seed=1)
+    o = Oracle(m)
+    p = o.lte()
+    assert np.allclose(p.sum(1), m.n_spec, rtol=1e-14)
+    sp = m.species
+    r = p[:, 1] / p[:, 0]
+    assert np.allclose(r, sp.g[1] / sp.g[0] * np.exp(-(sp.E[1] - sp.E[0]) / (kB * m.T)), rtol=1e-13)
+
+
+# ------------------------------------------------------------------ Ng and ALI
+def test_ng_exact_on_rank_two_linear_map():
+    """For x <- G x + b whose error lives in a 2D invariant subspace, one Ng step from
+    four iterates lands on the fixed point (I - G)^-1 b."""
+    rng = np.random.default_rng(0)
+    n = 30
+    V = np.linalg.qr(rng.normal(size=(n, n)))[0]
+    lam = np.zeros(n); lam[:2] = [0.9, -0.5]
+    G = V @ np.diag(lam) @ V.T
+    b = rng.normal(size=n)
+    xstar = np.linalg.solve(np.eye(n) - G, b)
+    x = xstar + V[:, :2] @ rng.normal(size=2)
+    it = [x]
+    for _ in range(3):
+        it.append(G @ it[-1] + b)
+    x3, x2, x1, x0 = it
+    out = ng(x0, x1, x2, x3)
+    assert np.allclose(out, xstar, rtol=1e-10, atol=1e-10)
+
+
+def test_ali_fixed_point_is_plain_equilibrium():
+    """The converged ALI populations satisfy the plain statistical equilibrium with J
+    recomputed from them (no ALO); LTE start with and without Ng reach the same fixed
+    point."""
+    m = syn.model_sphere_1d(n=40, seed=2)
+    m.n_spec = m.n_spec * 3e3       # optically thick enough for the ALO to matter
+    o = Oracle(m, nthreads=4)
+    p1, ch1, ok1 = o.ali(tol=1e-11, max_iter=400, ng_period=0)
+    p2, ch2, ok2 = o.ali(tol=1e-11, max_iter=400, ng_period=4)
+    assert ok1 and ok2
+    J, L, E = o.formal_solve(p1)
+    plain, _ = o.stateq(J, np.zeros_like(L), J)
+    assert np.max(np.abs(plain - p1) / p1) < 1e-8
+    assert np.max(np.abs(p2 - p1) / p1) < 1e-8
+    assert len(ch2) < len(ch1)
+
+
+def test_optically_thick_interior_thermalises():
+    """Deep inside an optically thick cloud at high density J -> S -> B_nu(T)."""
+    m = syn.model_sphere_1d(n=60, seed=1)
+    m.n_spec = m.n_spec * 1e6
+    m.n_coll = m.n_coll * 1e6
+    o = Oracle(m)
+    pops = o.lte()
+    J, L, E = o.formal_solve(pops, np.array([2]))
+    nu = (m.species.E[1] - m.species.E[0]) / h
+    S = planck(nu, 20.0)
+    assert abs(J[0, 0] / S - 1) < 2e-2
