@@ -1,0 +1,215 @@
+/*
+ * magritte_gb300.h -- C ABI of the GB300 (sm_103a) implementation of the accelerated
+ * Lambda iteration (ALI) hot path of non-LTE line radiative transfer described in
+ * De Ceuster et al. 2019, "Magritte I" (arXiv:1912.08445).
+ *
+ * Steps behind this boundary, each in hand-written CUDA kernels:
+ *   ray tracing by neighbour walk (Sec. 3.2), Gauss-Hermite frequency bins (Sec. 3.1.2),
+ *   HEALPix directions (Sec. 3.1.3), Doppler-shifted Gaussian line profiles (Sec. 2.2.1),
+ *   the second-order Feautrier solve of each ray pair with the diagonal approximate
+ *   Lambda operator (Sec. 3.3, 3.4, eq. 'GFE', 'ALO', 'ourJeff'), per-cell statistical
+ *   equilibrium (eq. 'ourALI'), the validity check (Sec. 6.1) and Ng acceleration
+ *   (Sec. 3.4).
+ *
+ * Conventions
+ *   - Units are SI: m, m/s, K, m^-3, J, s^-1, m^3 s^-1. Intensities are W m^-2 Hz^-1 sr^-1.
+ *   - Every function returns an int status: MG_OK (0), a negative error code, or a
+ *     positive warning. mg_last_error() gives a message for the last non-OK status.
+ *   - Ownership: the caller owns every host array it passes. Setters copy the data in;
+ *     the library keeps no caller pointer. Getters copy into caller buffers of the
+ *     documented size. The context owns all device memory it allocates.
+ *   - Functions ending in _dev take device pointers (on the context's device) and read
+ *     or write them in stream order on the context's stream; they never free them.
+ *   - A context is not thread safe; distinct contexts are independent.
+ *   - Array layouts are C order (row major); "[n][3]" means 3 doubles per point.
+ */
+#ifndef MAGRITTE_GB300_H
+#define MAGRITTE_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define MG_OK                      0
+#define MG_ERR_ARG               (-1)  /* invalid argument, size or layout              */
+#define MG_ERR_STATE             (-2)  /* call out of order (e.g. solve before tracing) */
+#define MG_ERR_CUDA              (-3)  /* a CUDA runtime call failed                    */
+#define MG_ERR_OOM               (-4)  /* device or host allocation failed              */
+#define MG_ERR_NOT_CONVERGED     (-5)  /* ALI reached max_iter above tolerance          */
+#define MG_ERR_NUMERIC           (-6)  /* non-finite result that no fallback repaired   */
+#define MG_ERR_CAPACITY          (-7)  /* a ray pair exceeds the kernel's staging limit */
+#define MG_WARN_DEAD_END_RAYS      1   /* some rays ended at a cell with no farther neighbour */
+#define MG_WARN_NEG_POP_FALLBACK   2   /* some cells fell back to plain Lambda iteration    */
+
+/* precision of the formal solve */
+#define MG_FP64   0   /* everything in FP64                                              */
+#define MG_MIXED  1   /* formal solve in FP32; statistical equilibrium in FP64           */
+
+/* geometry of a mesh */
+#define MG_GEOM_3D            0  /* point cloud with neighbour lists                     */
+#define MG_GEOM_SPHERICAL_1D  1  /* spherically symmetric shells: points on the +z axis at
+                                    increasing radii; radii below the first form an empty
+                                    core (a first radius of 0 is a centre point)          */
+
+/* initial populations */
+#define MG_INIT_LTE    0
+#define MG_INIT_GIVEN  1   /* keep what mg_set_populations stored */
+
+typedef struct mg_ctx mg_ctx;
+
+typedef struct {
+    int32_t precision;     /* MG_FP64 or MG_MIXED                                         */
+    int32_t device;        /* CUDA device ordinal                                         */
+    double  tol;           /* ALI stops when the max relative population change < tol     */
+    int32_t max_iter;      /* ALI iteration cap                                           */
+    int32_t ng_period;     /* Ng step every ng_period iterations from 4 iterates; 0 = off */
+    double  dshift_frac;   /* velocity-step limit as a fraction of the local line width  */
+    double  chi_min;       /* opacity floor, m^-1                                         */
+    double  dtau_min;      /* optical-depth increment floor                               */
+    double  T_cmb;         /* temperature of the incoming boundary black body, K          */
+    double  line_cut;      /* lines farther than line_cut widths from a bin are skipped   */
+    int64_t max_steps;     /* cap on traced cells per half-ray                            */
+    int32_t profile;       /* 1: time each kernel launch with CUDA events                 */
+    int32_t spectrum;      /* 1: keep the per-bin mean intensity for mg_get_spectrum      */
+} mg_options;
+
+/* Fills *opt with defaults: MG_FP64, device 0, tol 1e-6, max_iter 300, ng_period 4,
+ * dshift_frac 1/3, chi_min 1e-30, dtau_min 1e-12, T_cmb 2.725, line_cut 7.5,
+ * max_steps 100000, profile 0, spectrum 0. */
+void mg_default_options(mg_options *opt);
+
+/* Creates a context on opt->device (NULL opt = defaults). *out receives the handle.
+ * Errors: MG_ERR_ARG (bad option), MG_ERR_CUDA (device unusable). */
+int mg_create(mg_ctx **out, const mg_options *opt);
+int mg_destroy(mg_ctx *ctx);
+const char *mg_last_error(const mg_ctx *ctx);
+
+/* Uses the given cudaStream_t (as void*) for all later work, e.g. a PyTorch stream; NULL
+ * restores the context's own stream. The caller keeps the stream alive. */
+int mg_set_stream(mg_ctx *ctx, void *stream);
+
+/* Spatial discretisation (Sec. 3.1.1): n points, positions pos[n][3] and velocities
+ * vel[n][3], neighbour lists in CSR form (nbr_off[n+1] int64, nbr_idx[nbr_off[n]] int32,
+ * indices in [0, n)), boundary flags is_bdy[n] (1 = on the convex hull). For
+ * MG_GEOM_SPHERICAL_1D the points lie on +z with increasing radius and vel is radial
+ * (along z). Errors: MG_ERR_ARG on bad sizes or indices. Invalidates traced rays. */
+int mg_set_mesh(mg_ctx *ctx, int64_t n, const double *pos, const double *vel,
+                const int64_t *nbr_off, const int32_t *nbr_idx, const uint8_t *is_bdy,
+                int32_t geometry);
+
+/* Per-point physical fields [n]: collision-partner density, temperature, turbulent
+ * velocity and species density (Sec. 2.2.1). Requires mg_set_mesh first. */
+int mg_set_model(mg_ctx *ctx, const double *n_coll, const double *T, const double *v_turb,
+                 const double *n_species);
+
+/* Species (Sec. 2.2.1): n_lev levels with energies E (J) and weights g, mass (kg);
+ * n_lines radiative lines up[l] -> lo[l] (up > lo in energy) with Einstein A (s^-1);
+ * collisional de-excitation coefficients K_down[(n_lev(n_lev-1)/2)][n_T] (m^3 s^-1) on
+ * the temperature grid T_grid[n_T], pairs ordered (1,0),(2,0),(2,1),(3,0),...
+ * Einstein B follow from A; excitation coefficients follow by detailed balance,
+ * C_lu = C_ul (g_u/g_l) exp(-(E_u - E_l)/kT). Limits: n_lev <= 64. */
+int mg_set_species(mg_ctx *ctx, int32_t n_lev, const double *E, const double *g, double mass,
+                   int32_t n_lines, const int32_t *up, const int32_t *lo, const double *A,
+                   int32_t n_T, const double *T_grid, const double *K_down);
+
+/* Ray directions: HEALPix pixel centres for nside (12 nside^2 rays, Sec. 3.1.3), or R
+ * custom unit vectors dirs[R][3]. Every direction must have an exact antipode in the
+ * set (ray pairs, Sec. 3.3). Invalidates traced rays. */
+int mg_set_directions(mg_ctx *ctx, int32_t nside);
+int mg_set_directions_custom(mg_ctx *ctx, int32_t R, const double *dirs);
+/* Copies the directions [R][3] and antipode indices [R] into caller buffers. */
+int mg_get_directions(const mg_ctx *ctx, int32_t *R, double *dirs, int32_t *antipode);
+
+/* Gauss-Hermite frequency bins per line (Sec. 3.1.2): n_q roots r_q and the
+ * profile-normalised weights (sum 1). Limits: 1 <= n_q <= 128. */
+int mg_set_quadrature(mg_ctx *ctx, int32_t n_q);
+int mg_get_quadrature(const mg_ctx *ctx, double *roots, double *weights);
+
+typedef struct {
+    int64_t n_rays;          /* n * R half-rays                                    */
+    int64_t n_elements;      /* traced cells over all half-rays                    */
+    int64_t n_expanded;      /* cells plus points inserted by the velocity-step rule */
+    int64_t max_pair_len;    /* longest ray pair in expanded points, origin included */
+    int64_t n_dead_end;      /* half-rays that ended at a cell with no farther neighbour */
+    double  mean_pair_len;   /* mean expanded ray-pair length                      */
+} mg_ray_stats;
+
+/* Traces every (point, direction) half-ray on the device (Sec. 3.2): from the current
+ * cell, step to the neighbour with a strictly larger projection on the ray that lies
+ * closest to the ray (ties: smaller squared distance, then smaller projection, then
+ * smaller index); stop after a boundary cell or at a dead end. Between consecutive
+ * points, ceil(dv/(f min(b_a, b_b))) - 1 points are inserted when the line-of-sight
+ * velocity step dv exceeds f = dshift_frac of the smaller local width. Requires mesh,
+ * model and directions. Returns MG_WARN_DEAD_END_RAYS when some rays dead-ended. */
+int mg_trace_rays(mg_ctx *ctx, mg_ray_stats *out);
+
+/* Copies half-ray (point, ray): cells[len] (traced cell indices), nsub[len] (points
+ * inserted before each cell), ds[len] (path length from the previous point, m) and
+ * vpar[len] (line-of-sight velocity relative to the origin, m/s). cap is the buffer
+ * length; *len receives the ray length (MG_ERR_ARG if it exceeds cap). */
+int mg_get_ray(const mg_ctx *ctx, int64_t point, int32_t ray, int32_t *cells, int32_t *nsub,
+               double *ds, double *vpar, int64_t cap, int64_t *len);
+
+/* Level populations [n][n_lev] (m^-3). mg_init_populations(MG_INIT_LTE) sets Boltzmann
+ * populations at the local temperature. */
+int mg_init_populations(mg_ctx *ctx, int32_t mode);
+int mg_set_populations(mg_ctx *ctx, const double *pops);
+int mg_get_populations(const mg_ctx *ctx, double *pops);
+int mg_set_populations_dev(mg_ctx *ctx, const double *d_pops);
+int mg_get_populations_dev(const mg_ctx *ctx, double *d_pops);
+
+/* Formal solution from the current populations (Sec. 3.3-3.4): for every point, ray
+ * pair and frequency bin, solves the Feautrier equation along the pair and forms, per
+ * point and line,
+ *   J    = (1/P) sum_pairs sum_q w_q u,                       (mean intensity)
+ *   L    = (1/P) sum sum w_q Lambda*_oo chi_l/chi,            (diagonal ALO weight)
+ *   Jeff = (1/P) sum sum w_q (u - Lambda*_oo eta_l/chi).      (effective intensity)
+ * Requires traced rays, quadrature, species and populations. Asynchronous. */
+int mg_formal_solve(mg_ctx *ctx);
+/* Copies J, L, Jeff, each [n][n_lines], to host buffers (any may be NULL). */
+int mg_get_radiation(const mg_ctx *ctx, double *J, double *L, double *Jeff);
+int mg_get_radiation_dev(const mg_ctx *ctx, double *d_J, double *d_L, double *d_Jeff);
+/* Per-bin mean intensity (1/P) sum_pairs u, [n][n_lines][n_q]; needs opt.spectrum = 1. */
+int mg_get_spectrum(const mg_ctx *ctx, double *Jnu);
+
+/* Statistical equilibrium with the diagonal ALO (eq. 'ourALI') for every cell, the
+ * validity check (negative or non-finite populations -> the cell is solved again
+ * without the ALO, Sec. 6.1) and the convergence measure: *max_rel_change = max over
+ * cells and levels with n_i >= 1e-10 n of |n_new - n_old| / n_new (NULL allowed).
+ * Returns MG_WARN_NEG_POP_FALLBACK when some cell fell back. Synchronises. */
+int mg_update_populations(mg_ctx *ctx, double *max_rel_change);
+
+typedef struct {
+    int32_t iterations;      /* regular iterations done                            */
+    int32_t ng_steps;        /* Ng extrapolations accepted                         */
+    int32_t converged;       /* 1 when the last change < tol                       */
+    int32_t pad;
+    double  last_change;     /* max relative change of the last iteration          */
+    int64_t n_fallback;      /* cells that fell back, summed over iterations       */
+    double  seconds;         /* wall time of the loop                              */
+} mg_ali_report;
+
+/* Accelerated Lambda iteration from the current populations: formal solve ->
+ * statistical equilibrium -> convergence, with an Ng step every opt.ng_period
+ * iterations (Sec. 3.4, 6.1), until the change < opt.tol or opt.max_iter.
+ * Returns MG_ERR_NOT_CONVERGED when the cap is reached (populations are kept). */
+int mg_iterate(mg_ctx *ctx, mg_ali_report *rep);
+
+/* Kernel timing (opt.profile = 1): total milliseconds and launch counts per kernel
+ * since the last reset, for up to cap kernels; names[i] points to static strings. */
+int mg_kernel_times(const mg_ctx *ctx, int32_t cap, const char **names, double *ms,
+                    int64_t *launches, int32_t *count);
+int mg_reset_kernel_times(mg_ctx *ctx);
+
+/* Algorithmic work of one formal solve: ray-pair solves (points x pairs x bins) and
+ * cell-frequency updates (sum over solves of the expanded pair length). */
+int mg_work_counts(const mg_ctx *ctx, int64_t *solves, int64_t *cell_freq_updates);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MAGRITTE_GB300_H */

@@ -724,3 +724,34 @@ int or_ali(const or_model *m, double *pops, double tol, int max_iter, int ng_per
     for (int i = 0; i < 4; i++) free(hist[i]);
     return it;
 }
+
+/* All half-rays of a list of origins, in CSR form by (origin, ray): first call with
+ * cells == NULL to get the counts in len[n_orig * R]; second call fills cells, nsub, ds,
+ * vpar at offsets off[n_orig * R] (exclusive prefix sums of len). dead[n_orig * R] flags
+ * dead ends. */
+int or_trace_all(const or_model *m, int64_t n_orig, const int64_t *origins, const int64_t *off,
+                 int32_t *len, int32_t *cells, int32_t *nsub, double *ds, double *vpar, uint8_t *dead,
+                 int nthreads) {
+    int err = 0;
+    int64_t cap = m->max_steps;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+    #pragma omp parallel for schedule(dynamic, 16) reduction(|:err)
+#endif
+    for (int64_t io = 0; io < n_orig; io++) {
+        int32_t *c = malloc(sizeof(int32_t) * cap), *ns = malloc(sizeof(int32_t) * cap);
+        double *d = malloc(sizeof(double) * cap), *v = malloc(sizeof(double) * cap);
+        for (int r = 0; r < m->R; r++) {
+            int64_t ln; int de;
+            if (or_trace(m, origins[io], r, cap, c, ns, d, v, &ln, &de)) { err = 1; continue; }
+            int64_t k = io * m->R + r;
+            if (!cells) { len[k] = (int32_t)ln; if (dead) dead[k] = (uint8_t)de; continue; }
+            memcpy(cells + off[k], c, sizeof(int32_t) * ln);
+            memcpy(nsub + off[k], ns, sizeof(int32_t) * ln);
+            memcpy(ds + off[k], d, sizeof(double) * ln);
+            memcpy(vpar + off[k], v, sizeof(double) * ln);
+        }
+        free(c); free(ns); free(d); free(v);
+    }
+    return err ? -1 : 0;
+}

@@ -162,6 +162,7 @@ def _lib():
         L.or_ng.argtypes = [C.c_int64, P, P, P, P, P]
         L.or_ali.argtypes = [P, P, C.c_double, C.c_int, C.c_int, P, P, C.c_int]
         L.or_feautrier.argtypes = [C.c_int64, C.c_int64, P, P, C.c_double, C.c_double, P, P, P]
+        L.or_trace_all.argtypes = [P, C.c_int64, P, P, P, P, P, P, P, P, C.c_int]
         L.or_width.argtypes = [P, C.c_int64]
         L.or_width.restype = C.c_double
         _LIB = L
@@ -227,6 +228,29 @@ class Oracle:
         n = ln.value
         return dict(cells=cells[:n].copy(), nsub=nsub[:n].copy(), ds=ds[:n].copy(),
                     vpar=vpar[:n].copy(), dead_end=bool(de.value))
+
+    def trace_all(self, origins=None):
+        """All half-rays of the given origins: dict with off [n_orig*R+1] and flat
+        cells, nsub, ds, vpar, plus dead [n_orig*R]."""
+        if origins is None:
+            origins = np.arange(self.model.n, dtype=np.int64)
+        origins = np.ascontiguousarray(origins, np.int64)
+        k = origins.shape[0] * self.dirs.shape[0]
+        ln = np.zeros(k, np.int32)
+        dead = np.zeros(k, np.uint8)
+        L = _lib()
+        if L.or_trace_all(self.mp, origins.shape[0], _ptr(origins), None, _ptr(ln), None, None, None, None,
+                          _ptr(dead), self.nthreads):
+            raise RuntimeError("or_trace_all failed")
+        off = np.zeros(k + 1, np.int64)
+        np.cumsum(ln, out=off[1:])
+        tot = int(off[-1])
+        cells = np.empty(tot, np.int32); nsub = np.empty(tot, np.int32)
+        ds = np.empty(tot); vpar = np.empty(tot)
+        if L.or_trace_all(self.mp, origins.shape[0], _ptr(origins), _ptr(off), _ptr(ln), _ptr(cells), _ptr(nsub),
+                          _ptr(ds), _ptr(vpar), None, self.nthreads):
+            raise RuntimeError("or_trace_all failed")
+        return dict(off=off, cells=cells, nsub=nsub, ds=ds, vpar=vpar, dead=dead.astype(bool))
 
     def lte(self):
         pops = np.empty((self.model.n, self.model.species.n_lev))

@@ -1,0 +1,300 @@
+"""ctypes binding of libmagritte_gb300 (argument marshalling only).
+
+Every step of the hot path runs in the library's CUDA kernels; this module only converts
+numpy arrays and device pointers into the C ABI declared in include/magritte_gb300.h.
+There is no fallback: if the library cannot be loaded, import fails.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+MG_OK = 0
+MG_ERR_ARG, MG_ERR_STATE, MG_ERR_CUDA, MG_ERR_OOM = -1, -2, -3, -4
+MG_ERR_NOT_CONVERGED, MG_ERR_NUMERIC, MG_ERR_CAPACITY = -5, -6, -7
+MG_WARN_DEAD_END_RAYS, MG_WARN_NEG_POP_FALLBACK = 1, 2
+MG_FP64, MG_MIXED = 0, 1
+MG_GEOM_3D, MG_GEOM_SPHERICAL_1D = 0, 1
+MG_INIT_LTE, MG_INIT_GIVEN = 0, 1
+
+
+class mg_options(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("device", C.c_int32), ("tol", C.c_double),
+                ("max_iter", C.c_int32), ("ng_period", C.c_int32), ("dshift_frac", C.c_double),
+                ("chi_min", C.c_double), ("dtau_min", C.c_double), ("T_cmb", C.c_double),
+                ("line_cut", C.c_double), ("max_steps", C.c_int64), ("profile", C.c_int32),
+                ("spectrum", C.c_int32)]
+
+
+class mg_ray_stats(C.Structure):
+    _fields_ = [("n_rays", C.c_int64), ("n_elements", C.c_int64), ("n_expanded", C.c_int64),
+                ("max_pair_len", C.c_int64), ("n_dead_end", C.c_int64), ("mean_pair_len", C.c_double)]
+
+
+class mg_ali_report(C.Structure):
+    _fields_ = [("iterations", C.c_int32), ("ng_steps", C.c_int32), ("converged", C.c_int32),
+                ("pad", C.c_int32), ("last_change", C.c_double), ("n_fallback", C.c_int64),
+                ("seconds", C.c_double)]
+
+
+class MagritteError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{msg} (status {code})")
+        self.code = code
+
+
+_P = C.c_void_p
+_SIGS = {
+    "mg_default_options": (None, [_P]),
+    "mg_create": (C.c_int, [_P, _P]),
+    "mg_destroy": (C.c_int, [_P]),
+    "mg_last_error": (C.c_char_p, [_P]),
+    "mg_set_stream": (C.c_int, [_P, _P]),
+    "mg_set_mesh": (C.c_int, [_P, C.c_int64, _P, _P, _P, _P, _P, C.c_int32]),
+    "mg_set_model": (C.c_int, [_P, _P, _P, _P, _P]),
+    "mg_set_species": (C.c_int, [_P, C.c_int32, _P, _P, C.c_double, C.c_int32, _P, _P, _P, C.c_int32, _P, _P]),
+    "mg_set_directions": (C.c_int, [_P, C.c_int32]),
+    "mg_set_directions_custom": (C.c_int, [_P, C.c_int32, _P]),
+    "mg_get_directions": (C.c_int, [_P, _P, _P, _P]),
+    "mg_set_quadrature": (C.c_int, [_P, C.c_int32]),
+    "mg_get_quadrature": (C.c_int, [_P, _P, _P]),
+    "mg_trace_rays": (C.c_int, [_P, _P]),
+    "mg_get_ray": (C.c_int, [_P, C.c_int64, C.c_int32, _P, _P, _P, _P, C.c_int64, _P]),
+    "mg_init_populations": (C.c_int, [_P, C.c_int32]),
+    "mg_set_populations": (C.c_int, [_P, _P]),
+    "mg_get_populations": (C.c_int, [_P, _P]),
+    "mg_set_populations_dev": (C.c_int, [_P, _P]),
+    "mg_get_populations_dev": (C.c_int, [_P, _P]),
+    "mg_formal_solve": (C.c_int, [_P]),
+    "mg_get_radiation": (C.c_int, [_P, _P, _P, _P]),
+    "mg_get_radiation_dev": (C.c_int, [_P, _P, _P, _P]),
+    "mg_get_spectrum": (C.c_int, [_P, _P]),
+    "mg_update_populations": (C.c_int, [_P, _P]),
+    "mg_iterate": (C.c_int, [_P, _P]),
+    "mg_kernel_times": (C.c_int, [_P, C.c_int32, _P, _P, _P, _P]),
+    "mg_reset_kernel_times": (C.c_int, [_P]),
+    "mg_work_counts": (C.c_int, [_P, _P, _P]),
+}
+
+_LIB = None
+
+
+def lib_path():
+    return _build.LIB
+
+
+def load(build_if_missing=True):
+    """Loads the shared library (building it first if needed) and declares signatures."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = _build.LIB
+    if build_if_missing:
+        path = _build.build()
+    if not os.path.exists(path):
+        raise ImportError(f"libmagritte_gb300 not built: {path}")
+    lib = C.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _LIB = lib
+    return lib
+
+
+def declared_symbols():
+    return list(_SIGS)
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if isinstance(a, int):
+        return C.c_void_p(a)
+    return C.c_void_p(a.ctypes.data)
+
+
+def _c(a, dt):
+    return np.ascontiguousarray(a, dtype=dt)
+
+
+def default_options(**kw):
+    o = mg_options()
+    load().mg_default_options(C.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise KeyError(k)
+        setattr(o, k, v)
+    return o
+
+
+class Context:
+    """Owns one mg_ctx. Methods mirror the C functions of the same name."""
+
+    def __init__(self, **options):
+        self.lib = load()
+        self.opt = default_options(**options)
+        h = C.c_void_p()
+        rc = self.lib.mg_create(C.byref(h), C.byref(self.opt))
+        if rc != MG_OK:
+            raise MagritteError(rc, "mg_create failed")
+        self.h = h
+        self.n = 0
+        self.n_lev = 0
+        self.n_lines = 0
+        self.Q = 0
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.mg_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _chk(self, rc, what, warn_ok=True):
+        if rc < 0 or (rc > 0 and not warn_ok):
+            msg = self.lib.mg_last_error(self.h)
+            raise MagritteError(rc, f"{what}: {msg.decode() if msg else ''}")
+        return rc
+
+    # ---- set-up
+    def set_stream(self, stream_ptr):
+        return self._chk(self.lib.mg_set_stream(self.h, C.c_void_p(stream_ptr) if stream_ptr else None), "mg_set_stream")
+
+    def set_mesh(self, pos, vel, nbr_off, nbr_idx, is_bdy, geometry=MG_GEOM_3D):
+        pos, vel = _c(pos, np.float64), _c(vel, np.float64)
+        off, idx, bdy = _c(nbr_off, np.int64), _c(nbr_idx, np.int32), _c(is_bdy, np.uint8)
+        n = pos.shape[0]
+        self._chk(self.lib.mg_set_mesh(self.h, n, _ptr(pos), _ptr(vel), _ptr(off), _ptr(idx), _ptr(bdy),
+                                       int(geometry)), "mg_set_mesh")
+        self.n = n
+
+    def set_model(self, n_coll, T, v_turb, n_species):
+        a = [_c(x, np.float64) for x in (n_coll, T, v_turb, n_species)]
+        self._chk(self.lib.mg_set_model(self.h, *[_ptr(x) for x in a]), "mg_set_model")
+
+    def set_species(self, E, g, mass, up, lo, A, T_grid, K_down):
+        E, g, A = _c(E, np.float64), _c(g, np.float64), _c(A, np.float64)
+        up, lo = _c(up, np.int32), _c(lo, np.int32)
+        Tg, K = _c(T_grid, np.float64), _c(K_down, np.float64)
+        self._chk(self.lib.mg_set_species(self.h, E.shape[0], _ptr(E), _ptr(g), float(mass), A.shape[0],
+                                          _ptr(up), _ptr(lo), _ptr(A), Tg.shape[0], _ptr(Tg), _ptr(K)),
+                  "mg_set_species")
+        self.n_lev, self.n_lines = E.shape[0], A.shape[0]
+
+    def set_directions(self, nside):
+        self._chk(self.lib.mg_set_directions(self.h, int(nside)), "mg_set_directions")
+
+    def set_directions_custom(self, dirs):
+        d = _c(dirs, np.float64)
+        self._chk(self.lib.mg_set_directions_custom(self.h, d.shape[0], _ptr(d)), "mg_set_directions_custom")
+
+    def get_directions(self):
+        R = C.c_int32(0)
+        self._chk(self.lib.mg_get_directions(self.h, C.byref(R), None, None), "mg_get_directions")
+        d = np.empty((R.value, 3)); a = np.empty(R.value, np.int32)
+        self._chk(self.lib.mg_get_directions(self.h, None, _ptr(d), _ptr(a)), "mg_get_directions")
+        return d, a
+
+    def set_quadrature(self, n_q):
+        self._chk(self.lib.mg_set_quadrature(self.h, int(n_q)), "mg_set_quadrature")
+        self.Q = int(n_q)
+
+    def get_quadrature(self):
+        r = np.empty(self.Q); w = np.empty(self.Q)
+        self._chk(self.lib.mg_get_quadrature(self.h, _ptr(r), _ptr(w)), "mg_get_quadrature")
+        return r, w
+
+    def trace_rays(self):
+        st = mg_ray_stats()
+        rc = self._chk(self.lib.mg_trace_rays(self.h, C.byref(st)), "mg_trace_rays")
+        return {k: getattr(st, k) for k, _ in st._fields_}, rc
+
+    def get_ray(self, point, ray, cap=1 << 16):
+        cells = np.empty(cap, np.int32); nsub = np.empty(cap, np.int32)
+        ds = np.empty(cap); vpar = np.empty(cap); ln = C.c_int64(0)
+        self._chk(self.lib.mg_get_ray(self.h, int(point), int(ray), _ptr(cells), _ptr(nsub), _ptr(ds), _ptr(vpar),
+                                      cap, C.byref(ln)), "mg_get_ray")
+        n = ln.value
+        return dict(cells=cells[:n].copy(), nsub=nsub[:n].copy(), ds=ds[:n].copy(), vpar=vpar[:n].copy())
+
+    # ---- populations and solves
+    def init_populations(self, mode=MG_INIT_LTE):
+        self._chk(self.lib.mg_init_populations(self.h, int(mode)), "mg_init_populations")
+
+    def set_populations(self, pops):
+        p = _c(pops, np.float64)
+        self._chk(self.lib.mg_set_populations(self.h, _ptr(p)), "mg_set_populations")
+
+    def get_populations(self, out=None):
+        p = np.empty((self.n, self.n_lev)) if out is None else out
+        self._chk(self.lib.mg_get_populations(self.h, _ptr(p)), "mg_get_populations")
+        return p
+
+    def set_populations_dev(self, dev_ptr):
+        self._chk(self.lib.mg_set_populations_dev(self.h, C.c_void_p(dev_ptr)), "mg_set_populations_dev")
+
+    def get_populations_dev(self, dev_ptr):
+        self._chk(self.lib.mg_get_populations_dev(self.h, C.c_void_p(dev_ptr)), "mg_get_populations_dev")
+
+    def formal_solve(self):
+        self._chk(self.lib.mg_formal_solve(self.h), "mg_formal_solve")
+
+    def get_radiation(self):
+        J = np.empty((self.n, self.n_lines)); L = np.empty_like(J); E = np.empty_like(J)
+        self._chk(self.lib.mg_get_radiation(self.h, _ptr(J), _ptr(L), _ptr(E)), "mg_get_radiation")
+        return J, L, E
+
+    def get_spectrum(self):
+        out = np.empty((self.n, self.n_lines, self.Q))
+        self._chk(self.lib.mg_get_spectrum(self.h, _ptr(out)), "mg_get_spectrum")
+        return out
+
+    def update_populations(self):
+        ch = C.c_double(0)
+        rc = self._chk(self.lib.mg_update_populations(self.h, C.byref(ch)), "mg_update_populations")
+        return ch.value, rc
+
+    def iterate(self, allow_not_converged=False):
+        rep = mg_ali_report()
+        rc = self.lib.mg_iterate(self.h, C.byref(rep))
+        if rc < 0 and not (allow_not_converged and rc == MG_ERR_NOT_CONVERGED):
+            self._chk(rc, "mg_iterate")
+        return {k: getattr(rep, k) for k, _ in rep._fields_ if k != "pad"}, rc
+
+    def kernel_times(self):
+        cap = 64
+        names = (C.c_char_p * cap)(); ms = np.zeros(cap); la = np.zeros(cap, np.int64); cnt = C.c_int32(0)
+        self._chk(self.lib.mg_kernel_times(self.h, cap, names, _ptr(ms), _ptr(la), C.byref(cnt)), "mg_kernel_times")
+        return {names[i].decode(): (float(ms[i]), int(la[i])) for i in range(min(cnt.value, cap))}
+
+    def reset_kernel_times(self):
+        self._chk(self.lib.mg_reset_kernel_times(self.h), "mg_reset_kernel_times")
+
+    def work_counts(self):
+        s = C.c_int64(0); u = C.c_int64(0)
+        self._chk(self.lib.mg_work_counts(self.h, C.byref(s), C.byref(u)), "mg_work_counts")
+        return s.value, u.value
+
+    # ---- convenience: load a synthetic model
+    def load_model(self, m, nside=None, dirs=None, n_q=None):
+        """Copies a synthetic.Model into the context (mesh, fields, species, directions,
+        quadrature)."""
+        sp = m.species
+        self.set_mesh(m.pos, m.vel, m.nbr_off, m.nbr_idx, m.is_bdy, m.geometry)
+        self.set_species(sp.E, sp.g, sp.mass, sp.up, sp.lo, sp.A, sp.T_grid, sp.K_down)
+        self.set_model(m.n_coll, m.T, m.v_turb, m.n_spec)
+        d = dirs if dirs is not None else m.dirs
+        if d is not None:
+            self.set_directions_custom(d)
+        else:
+            self.set_directions(nside if nside is not None else m.nside)
+        self.set_quadrature(n_q if n_q is not None else m.n_q)

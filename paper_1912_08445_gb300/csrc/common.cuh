@@ -1,0 +1,176 @@
+// Internal declarations shared by the translation units of libmagritte_gb300.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <string>
+#include <vector>
+#include "../../include/magritte_gb300.h"
+
+namespace mg {
+
+// CODATA 2018 constants.
+constexpr double kH = 6.62607015e-34;
+constexpr double kKB = 1.380649e-23;
+constexpr double kC = 299792458.0;
+constexpr double kSqrtPi = 1.7724538509055160273;
+constexpr double kPi = 3.14159265358979323846;
+
+constexpr int kMaxLev = 64;
+
+// Per-line constants of the species, copied to the device once.
+struct LineConst {
+    double nu;      // line-centre frequency (E_u - E_l)/h
+    double A;       // Einstein A_ul
+    double Bul;     // A c^2 / (2 h nu^3)
+    double Blu;     // (g_u/g_l) B_ul
+    double pre;     // h nu / (4 pi)
+    int32_t up, lo;
+};
+
+// Overlap descriptor of a (line l, other line l') pair used by the profile sum:
+// x_l' = (dnl + rat * (a_q (1 - v/c) - v)) / b with dnl = c (nu_l - nu_l')/nu_l'
+// and rat = nu_l/nu_l'.
+struct Overlap {
+    double dnl;
+    double rat;
+    double inv_nu2;   // 1/nu_l' (profile normalisation delta_nu = nu_l' b / c)
+    int32_t l2;
+    int32_t pad;
+};
+
+struct KernelTimer {
+    std::string name;
+    double ms = 0.0;
+    int64_t launches = 0;
+};
+
+}  // namespace mg
+
+struct mg_ctx {
+    mg_options opt{};
+    int device = 0;
+    cudaStream_t own_stream = nullptr;
+    cudaStream_t stream = nullptr;
+    mutable std::string err;
+
+    // ---- mesh
+    bool have_mesh = false;
+    int64_t n = 0;
+    int32_t geometry = MG_GEOM_3D;
+    int64_t n_edges = 0;
+    double *d_pos = nullptr, *d_vel = nullptr;
+    int64_t *d_nbr_off = nullptr;
+    int32_t *d_nbr_idx = nullptr;
+    uint8_t *d_bdy = nullptr;
+    std::vector<double> h_T, h_vturb;      // kept to compute widths once the mass is known
+
+    // ---- model
+    bool have_model = false;
+    double *d_ncoll = nullptr, *d_T = nullptr, *d_nspec = nullptr;
+    double *d_b = nullptr;        // velocity width per point
+    float *d_bf = nullptr;
+
+    // ---- species
+    bool have_species = false;
+    int32_t n_lev = 0, n_lines = 0, n_T = 0;
+    double mass = 0.0;
+    std::vector<double> h_E, h_g, h_Tgrid, h_Kdown;
+    std::vector<mg::LineConst> h_lines;
+    mg::LineConst *d_lines = nullptr;
+    double *d_E = nullptr, *d_g = nullptr, *d_Tgrid = nullptr, *d_Kdown = nullptr;
+    double *d_coll = nullptr;     // [n][n_pairs][2] (down, up) collision rates
+    bool coll_ready = false;
+    std::vector<int32_t> h_ovl_off;
+    std::vector<mg::Overlap> h_ovl;
+    int32_t *d_ovl_off = nullptr;
+    mg::Overlap *d_ovl = nullptr;
+
+    // ---- directions
+    bool have_dirs = false;
+    int32_t R = 0, P = 0;
+    std::vector<double> h_dirs;
+    std::vector<int32_t> h_anti, h_pf, h_pb;
+    double *d_dirs = nullptr;
+    int32_t *d_pf = nullptr, *d_pb = nullptr;
+
+    // ---- quadrature
+    bool have_quad = false;
+    int32_t Q = 0;
+    std::vector<double> h_roots, h_weights;
+    double *d_roots = nullptr, *d_weights = nullptr;
+
+    // ---- ray store: per (point, ray) half-ray, CSR by point then ray
+    bool traced = false;
+    int64_t *d_ray_off = nullptr;  // [n*R + 1]
+    int32_t *d_cells = nullptr;    // traced cell
+    int32_t *d_xcum = nullptr;     // expanded points up to and including the element
+    double *d_ds = nullptr;        // path length from the previous point
+    double *d_vpar = nullptr;      // line-of-sight velocity relative to the origin
+    float *d_dsf = nullptr, *d_vparf = nullptr;
+    int64_t n_elements = 0, n_expanded = 0, max_pair_len = 0, n_dead = 0;
+    int64_t work_solves = 0, work_updates = 0;
+
+    // ---- state
+    bool have_pops = false;
+    double *d_pops = nullptr, *d_pops_new = nullptr;
+    double *d_hist[4] = {nullptr, nullptr, nullptr, nullptr};
+    double *d_ng_tmp = nullptr, *d_ng_part = nullptr;
+    double *d_line = nullptr;      // [n][L][2] (eta_int, chi_int)
+    float *d_linef = nullptr;
+    double *d_J = nullptr, *d_L = nullptr, *d_Jeff = nullptr, *d_Lc = nullptr;
+    double *d_Jnu = nullptr;
+    bool have_rad = false;
+
+    // ---- scalars
+    unsigned long long *d_scal = nullptr;   // [0] max change bits, [1] fallbacks, [2] flags
+    unsigned long long *h_scal = nullptr;   // pinned
+    int32_t *d_err = nullptr;               // kernel error word
+
+    // ---- profiling
+    std::vector<mg::KernelTimer> timers;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+};
+
+// ---------------------------------------------------------------- helpers
+int mg_fail(const mg_ctx *ctx, int code, const std::string &msg);
+int mg_cuda_check(const mg_ctx *ctx, cudaError_t e, const char *what);
+#define MG_CUDA(call)                                                     \
+    do {                                                                  \
+        cudaError_t e_ = (call);                                          \
+        if (e_ != cudaSuccess) return mg_cuda_check(ctx, e_, #call);      \
+    } while (0)
+
+template <typename T>
+int mg_alloc(mg_ctx *ctx, T **p, size_t count) {
+    if (*p) { cudaFree(*p); *p = nullptr; }
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc((void **)p, count * sizeof(T));
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        return mg_fail(ctx, MG_ERR_OOM, std::string("cudaMalloc failed: ") + cudaGetErrorString(e));
+    }
+    return MG_OK;
+}
+template <typename T>
+void mg_free(T *&p) {
+    if (p) cudaFree(p);
+    p = nullptr;
+}
+
+// Kernel timing scope: records events around a launch when opt.profile is set.
+struct MgTimed {
+    mg_ctx *ctx;
+    int idx;
+    MgTimed(mg_ctx *c, const char *name);
+    ~MgTimed();
+};
+
+// ---------------------------------------------------------------- launchers
+int mg_launch_trace(mg_ctx *ctx);
+int mg_launch_line_data(mg_ctx *ctx);
+int mg_launch_feautrier(mg_ctx *ctx);
+int mg_launch_lte(mg_ctx *ctx);
+int mg_launch_collision_rates(mg_ctx *ctx);
+int mg_launch_stateq(mg_ctx *ctx);
+int mg_launch_ng(mg_ctx *ctx, int *accepted);
+int mg_launch_push_history(mg_ctx *ctx);

@@ -1,0 +1,286 @@
+// K2 (line data) and K3 (Feautrier formal solve with the diagonal ALO), Sec. 3.3-3.4.
+#include <cmath>
+#include "common.cuh"
+
+using namespace mg;
+
+namespace {
+
+// ---------------------------------------------------------------- K2 line data
+// eta_int = h nu/4pi n_u A_ul, chi_int = h nu/4pi (n_l B_lu - n_u B_ul) (eq. 'lines'),
+// stored per point as [L][2] so that one gather brings all lines of a point.
+__global__ void k_line_data(int64_t n, int L, int nlev, const double *__restrict__ pops,
+                            const LineConst *__restrict__ lc, double *__restrict__ line, float *__restrict__ linef) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n * L) return;
+    const int64_t c = t / L;
+    const int l = (int)(t - c * L);
+    const LineConst k = lc[l];
+    const double nu_ = pops[c * nlev + k.up], nl_ = pops[c * nlev + k.lo];
+    const double eta = k.pre * nu_ * k.A;
+    const double chi = k.pre * (nl_ * k.Blu - nu_ * k.Bul);
+    line[2 * t] = eta;
+    line[2 * t + 1] = chi;
+    if (linef) {
+        linef[2 * t] = (float)eta;
+        linef[2 * t + 1] = (float)chi;
+    }
+}
+
+struct SolveArgs {
+    int64_t n;
+    int32_t R, P, L, Q;
+    const int32_t *pf, *pb;
+    const int64_t *ray_off;
+    const int32_t *cells, *xcum;
+    const double *ds, *vpar;
+    const double *b;
+    const double *line;
+    const LineConst *lc;
+    const double *roots, *weights;
+    const int32_t *ovl_off;
+    const Overlap *ovl;
+    double chi_min, dtau_min, T_cmb;
+    double *J, *Lout, *Jeff, *Lc, *Jnu;
+    int32_t kmax;
+    int32_t *err;
+};
+
+__device__ __forceinline__ double planck_d(double nu, double T) {
+    return 2.0 * kH * nu * nu * nu / (kC * kC) / expm1(kH * nu / (kKB * T));
+}
+
+// Stages the expanded points of half-ray (o, r) into the pair arrays. Point x of the
+// half (0 = nearest the origin) sits at pair index base + dir * x; its path length to the
+// neighbouring point towards the origin goes to ds slot (dir < 0 ? idx : idx - 1).
+__device__ void stage_half64(const SolveArgs &a, int64_t o, int r, int base, int dir, double *s_ds, double *s_v,
+                             double *s_b, double *s_line) {
+    const int L = a.L;
+    const int64_t off = a.ray_off[o * a.R + r];
+    const int len = (int)(a.ray_off[o * a.R + r + 1] - off);
+    for (int e = threadIdx.x; e < len; e += blockDim.x) {
+        const int64_t c = a.cells[off + e];
+        const int64_t prev = e ? a.cells[off + e - 1] : o;
+        const int x0 = e ? a.xcum[off + e - 1] : 0;
+        const int ns = a.xcum[off + e] - x0 - 1;
+        const double pv = e ? a.vpar[off + e - 1] : 0.0;
+        const double ve = a.vpar[off + e], dse = a.ds[off + e];
+        const double bp = a.b[prev], bc = a.b[c];
+        const double *lp = a.line + prev * 2 * L, *lcur = a.line + c * 2 * L;
+        for (int j = 1; j <= ns + 1; j++) {
+            const double w = (double)j / (double)(ns + 1);
+            const int idx = base + dir * (x0 + j - 1);
+            s_ds[dir < 0 ? idx : idx - 1] = dse / (double)(ns + 1);
+            s_v[idx] = (1.0 - w) * pv + w * ve;
+            s_b[idx] = (1.0 - w) * bp + w * bc;
+            for (int k = 0; k < 2 * L; k++) s_line[idx * 2 * L + k] = (1.0 - w) * lp[k] + w * lcur[k];
+        }
+    }
+}
+
+// Opacity, emissivity and line l's own share at pair point k for bin (l, q).
+struct Pt64 {
+    double chi, eta, chil, etal;
+};
+
+__device__ __forceinline__ Pt64 point64(const SolveArgs &a, int l, double aq, int k, const double *s_v,
+                                        const double *s_b, const double *s_line) {
+    const double v = s_v[k], bk = s_b[k];
+    const double ibk = 1.0 / bk;
+    Pt64 p{0.0, 0.0, 0.0, 0.0};
+    const int o0 = a.ovl_off[l], o1 = a.ovl_off[l + 1];
+    const double base = aq * (1.0 - v / kC) - v;
+    for (int i = o0; i < o1; i++) {
+        const Overlap ov = a.ovl[i];
+        const double x = (ov.dnl + ov.rat * base) * ibk;
+        const double phi = exp(-x * x) * kC * ov.inv_nu2 * ibk / kSqrtPi;
+        const double et = s_line[k * 2 * a.L + 2 * ov.l2] * phi;
+        const double ch = s_line[k * 2 * a.L + 2 * ov.l2 + 1] * phi;
+        p.eta += et;
+        p.chi += ch;
+        if (i == o0) { p.etal = et; p.chil = ch; }
+    }
+    return p;
+}
+
+// One CTA per origin point; the CTA loops over the ray pairs, staging each expanded pair
+// in shared memory, and each thread solves its frequency bins.
+//
+// Sweep in rescaled Rybicki-Hummer variables from a far end towards the origin: with
+// dtau_k between points k and k+1, F_k = dtau_k Phi_k and z_k = dtau_k psi_k,
+//   boundary row:  Phi_0 = dtau_0/2 + 1,              psi_0 = (dtau_0 S_0/2 + I) iota_0,
+//   interior row:  Phi_k = t_k + Phi_{k-1} iota_{k-1}, psi_k = (t_k S_k + psi_{k-1}) iota_k,
+//   with t_k = (dtau_{k-1} + dtau_k)/2 and iota_k = 1/(1 + dtau_k Phi_k).
+// At the origin, with sigma = 2/(dtau_- + dtau_+):
+//   D = 1 + sigma (Phi_b iota_b + Phi_f iota_f),  Lambda*_oo = 1/D,
+//   u - Lambda* S_o = sigma (psi_b + psi_f)/D,    1 - Lambda* = sigma (Phi_b iota_b + Phi_f iota_f)/D,
+// all sums of non-negative terms. An empty half contributes Phi iota = 1, psi = I_o and
+// dtau = 0 (the origin row is then the boundary row).
+struct Side64 {
+    double phi_iota, psi, dtau;
+};
+
+__device__ __forceinline__ Side64 sweep64(const SolveArgs &a, int l, double aq, double nu_o, int kstart, int kend,
+                                          int step, const double *s_ds, const double *s_v, const double *s_b,
+                                          const double *s_line, Pt64 &po) {
+    // kstart: far end, kend: origin; step = +1 (backward half) or -1 (forward half)
+    Pt64 p = point64(a, l, aq, kstart, s_v, s_b, s_line);
+    double chi_prev = fmax(p.chi, a.chi_min);
+    double S_prev = p.eta / chi_prev;
+    const double I = planck_d(nu_o * (1.0 - s_v[kstart] / kC), a.T_cmb);
+    double Phi = 0.0, iota = 0.0, psi = 0.0, dt_prev = 0.0;
+    int row = 0;
+    for (int k = kstart + step;; k += step) {
+        Pt64 q = point64(a, l, aq, k, s_v, s_b, s_line);
+        const double chi = fmax(q.chi, a.chi_min);
+        const double S = q.eta / chi;
+        const double dsk = s_ds[step > 0 ? k - 1 : k];
+        const double dt = fmax(0.5 * (chi_prev + chi) * dsk, a.dtau_min);
+        if (row == 0) {
+            Phi = 0.5 * dt + 1.0;
+            iota = 1.0 / (1.0 + dt * Phi);
+            psi = (0.5 * dt * S_prev + I) * iota;
+        } else {
+            const double t = 0.5 * (dt_prev + dt);
+            Phi = t + Phi * iota;
+            iota = 1.0 / (1.0 + dt * Phi);
+            psi = (t * S_prev + psi) * iota;
+        }
+        row++;
+        dt_prev = dt;
+        chi_prev = chi;
+        S_prev = S;
+        if (k == kend) {
+            q.chi = chi;
+            po = q;
+            break;
+        }
+    }
+    return Side64{Phi * iota, psi, dt_prev};
+}
+
+__global__ void k_feautrier64(SolveArgs a) {
+    extern __shared__ double smem[];
+    const int L = a.L, Q = a.Q, F = L * Q;
+    const int kmax = a.kmax;
+    double *s_ds = smem;
+    double *s_v = s_ds + kmax;
+    double *s_b = s_v + kmax;
+    double *s_line = s_b + kmax;
+    double *acc = s_line + (size_t)kmax * 2 * L;   // [F][4]
+    const int64_t o = blockIdx.x;
+    for (int f = threadIdx.x; f < 4 * F; f += blockDim.x) acc[f] = 0.0;
+    const double bo = a.b[o];
+    for (int p = 0; p < a.P; p++) {
+        const int rf = a.pf[p], rb = a.pb[p];
+        const int64_t ofb = a.ray_off[o * a.R + rb], ofl = a.ray_off[o * a.R + rf];
+        const int lb = (int)(a.ray_off[o * a.R + rb + 1] - ofb);
+        const int lf = (int)(a.ray_off[o * a.R + rf + 1] - ofl);
+        const int Kb = lb ? a.xcum[ofb + lb - 1] : 0;
+        const int Kf = lf ? a.xcum[ofl + lf - 1] : 0;
+        const int K = Kb + 1 + Kf;
+        if (K > kmax) {
+            if (threadIdx.x == 0) atomicOr(a.err, 2);
+            continue;
+        }
+        __syncthreads();
+        stage_half64(a, o, rb, Kb - 1, -1, s_ds, s_v, s_b, s_line);
+        stage_half64(a, o, rf, Kb + 1, +1, s_ds, s_v, s_b, s_line);
+        if (threadIdx.x == 0) {
+            s_v[Kb] = 0.0;
+            s_b[Kb] = bo;
+        }
+        for (int k = threadIdx.x; k < 2 * L; k += blockDim.x) s_line[Kb * 2 * L + k] = a.line[o * 2 * L + k];
+        __syncthreads();
+        for (int f = threadIdx.x; f < F; f += blockDim.x) {
+            const int l = f / Q, q = f - l * Q;
+            const double aq = a.roots[q] * bo;
+            const double nu_o = a.lc[l].nu * (1.0 + aq / kC);
+            Side64 sb, sf;
+            Pt64 po{0, 0, 0, 0};
+            double u, lam, uml, oml;
+            if (K == 1) {
+                const double I = planck_d(nu_o, a.T_cmb);
+                u = I; lam = 0.0; uml = I; oml = 1.0;
+                po = point64(a, l, aq, Kb, s_v, s_b, s_line);
+                po.chi = fmax(po.chi, a.chi_min);
+            } else {
+                if (Kb > 0) sb = sweep64(a, l, aq, nu_o, 0, Kb, +1, s_ds, s_v, s_b, s_line, po);
+                if (Kf > 0) sf = sweep64(a, l, aq, nu_o, K - 1, Kb, -1, s_ds, s_v, s_b, s_line, po);
+                if (Kb == 0 || Kf == 0) {
+                    const double Io = planck_d(nu_o, a.T_cmb);
+                    if (Kb == 0) sb = Side64{1.0, Io, 0.0};
+                    if (Kf == 0) sf = Side64{1.0, Io, 0.0};
+                }
+                const double So = po.eta / po.chi;
+                const double sig = 2.0 / (sb.dtau + sf.dtau);
+                const double pi2 = sb.phi_iota + sf.phi_iota;
+                const double D = 1.0 + sig * pi2;
+                const double iD = 1.0 / D;
+                u = (So + sig * (sb.psi + sf.psi)) * iD;
+                lam = iD;
+                uml = sig * (sb.psi + sf.psi) * iD;
+                oml = sig * pi2 * iD;
+            }
+            const double ichi = 1.0 / po.chi;
+            acc[4 * f + 0] += u;
+            acc[4 * f + 1] += lam * po.chil * ichi;
+            acc[4 * f + 2] += uml + lam * (po.eta - po.etal) * ichi;
+            acc[4 * f + 3] += oml + lam * (po.chi - po.chil) * ichi;
+        }
+    }
+    __syncthreads();
+    const double invP = 1.0 / a.P;
+    for (int t = threadIdx.x; t < 4 * L; t += blockDim.x) {
+        const int l = t >> 2, k = t & 3;
+        double s = 0.0;
+        for (int q = 0; q < Q; q++) s += a.weights[q] * acc[4 * (l * Q + q) + k];
+        s *= invP;
+        double *dst = k == 0 ? a.J : (k == 1 ? a.Lout : (k == 2 ? a.Jeff : a.Lc));
+        dst[o * L + l] = s;
+    }
+    if (a.Jnu)
+        for (int f = threadIdx.x; f < F; f += blockDim.x) a.Jnu[o * F + f] = acc[4 * f] * invP;
+}
+
+}  // namespace
+
+int mg_launch_line_data(mg_ctx *ctx) {
+    const int64_t m = ctx->n * ctx->n_lines;
+    MgTimed t(ctx, "line_data");
+    k_line_data<<<(unsigned)((m + 255) / 256), 256, 0, ctx->stream>>>(
+        ctx->n, ctx->n_lines, ctx->n_lev, ctx->d_pops, ctx->d_lines, ctx->d_line,
+        ctx->opt.precision == MG_MIXED ? ctx->d_linef : nullptr);
+    MG_CUDA(cudaGetLastError());
+    return MG_OK;
+}
+
+int mg_launch_feautrier_mixed(mg_ctx *ctx);
+
+int mg_launch_feautrier(mg_ctx *ctx) {
+    if (ctx->opt.precision == MG_MIXED) return mg_launch_feautrier_mixed(ctx);
+    SolveArgs a{};
+    a.n = ctx->n; a.R = ctx->R; a.P = ctx->P; a.L = ctx->n_lines; a.Q = ctx->Q;
+    a.pf = ctx->d_pf; a.pb = ctx->d_pb; a.ray_off = ctx->d_ray_off; a.cells = ctx->d_cells; a.xcum = ctx->d_xcum;
+    a.ds = ctx->d_ds; a.vpar = ctx->d_vpar; a.b = ctx->d_b; a.line = ctx->d_line; a.lc = ctx->d_lines;
+    a.roots = ctx->d_roots; a.weights = ctx->d_weights; a.ovl_off = ctx->d_ovl_off; a.ovl = ctx->d_ovl;
+    a.chi_min = ctx->opt.chi_min; a.dtau_min = ctx->opt.dtau_min; a.T_cmb = ctx->opt.T_cmb;
+    a.J = ctx->d_J; a.Lout = ctx->d_L; a.Jeff = ctx->d_Jeff; a.Lc = ctx->d_Lc;
+    a.Jnu = ctx->opt.spectrum ? ctx->d_Jnu : nullptr;
+    a.kmax = (int32_t)ctx->max_pair_len;
+    a.err = ctx->d_err;
+    const int F = a.L * a.Q;
+    size_t smem = sizeof(double) * ((size_t)a.kmax * (3 + 2 * a.L) + 4 * (size_t)F);
+    if (smem > 227 * 1024)
+        return mg_fail(ctx, MG_ERR_CAPACITY, "FP64 formal solve: longest ray pair does not fit in shared memory");
+    MG_CUDA(cudaFuncSetAttribute(k_feautrier64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int threads = ((F + 31) / 32) * 32;
+    if (threads > 256) threads = 256;
+    MG_CUDA(cudaMemsetAsync(ctx->d_err, 0, 4, ctx->stream));
+    {
+        MgTimed t(ctx, "feautrier_fp64");
+        k_feautrier64<<<(unsigned)ctx->n, threads, smem, ctx->stream>>>(a);
+    }
+    MG_CUDA(cudaGetLastError());
+    return MG_OK;
+}

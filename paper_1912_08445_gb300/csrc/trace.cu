@@ -1,0 +1,357 @@
+// K1: ray tracing by neighbour walk (Sec. 3.2) with the velocity-step rule (Sec. 3.1.1).
+// This translation unit is compiled with --fmad=false: every floating-point decision of
+// the walk (projections, distances, velocity steps) is reproducible bit for bit.
+#include <cmath>
+#include "common.cuh"
+
+using namespace mg;
+
+namespace {
+
+struct TraceArgs {
+    int64_t n;
+    int32_t R;
+    int32_t geometry;
+    const double *pos, *vel, *b, *dirs;
+    const int64_t *nbr_off;
+    const int32_t *nbr_idx;
+    const uint8_t *bdy;
+    double dshift_frac;
+    int64_t max_steps;
+    // count pass
+    int32_t *len, *xlen;
+    // fill pass
+    const int64_t *ray_off;
+    int32_t *cells, *xcum;
+    double *ds, *vpar;
+    int32_t *err;
+};
+
+// Points inserted between two consecutive points by the velocity-step rule: when the
+// line-of-sight velocity changes by dv > f min(b_a, b_b), ceil(dv/(f min)) - 1 points.
+__device__ __forceinline__ int32_t velocity_inserts(double va, double ba, double vb, double bb, double f) {
+    double dv = fabs(vb - va);
+    double wmin = ba < bb ? ba : bb;
+    double lim = f * wmin;
+    if (dv > lim) return (int32_t)ceil(dv / lim) - 1;
+    return 0;
+}
+
+// Records one element of the half-ray (count pass: counts only).
+template <bool FILL>
+__device__ __forceinline__ bool emit(const TraceArgs &a, int64_t base, int32_t &len, int32_t &x, int32_t cell,
+                                     double ds, double vp, double &va, double &ba) {
+    if (len >= a.max_steps) return false;
+    double bb = a.b[cell];
+    int32_t ns = velocity_inserts(va, ba, vp, bb, a.dshift_frac);
+    x += ns + 1;
+    if (FILL) {
+        a.cells[base + len] = cell;
+        a.xcum[base + len] = x;
+        a.ds[base + len] = ds;
+        a.vpar[base + len] = vp;
+    }
+    len++;
+    va = vp;
+    ba = bb;
+    return true;
+}
+
+// 3D point cloud: from the current cell, the neighbour with a strictly larger projection
+// on the ray that lies closest to the ray (ties: smaller squared distance, smaller
+// projection, smaller index); stop after a boundary cell or at a dead end.
+template <bool FILL>
+__device__ void walk_3d(const TraceArgs &a, int64_t o, int r, int64_t base, int32_t &len, int32_t &x,
+                        bool &dead, bool &overflow) {
+    const double n0 = a.dirs[3 * r], n1 = a.dirs[3 * r + 1], n2 = a.dirs[3 * r + 2];
+    const double xo0 = a.pos[3 * o], xo1 = a.pos[3 * o + 1], xo2 = a.pos[3 * o + 2];
+    const double vo0 = a.vel[3 * o], vo1 = a.vel[3 * o + 1], vo2 = a.vel[3 * o + 2];
+    int64_t cur = o;
+    double s_cur = 0.0;
+    double va = 0.0, ba = a.b[o];
+    len = 0;
+    x = 0;
+    dead = false;
+    overflow = false;
+    for (;;) {
+        int64_t best = -1;
+        double bs = 0.0, bd2 = 0.0;
+        const int64_t e1 = a.nbr_off[cur + 1];
+        for (int64_t e = a.nbr_off[cur]; e < e1; e++) {
+            const int64_t c = a.nbr_idx[e];
+            const double dx = a.pos[3 * c] - xo0;
+            const double dy = a.pos[3 * c + 1] - xo1;
+            const double dz = a.pos[3 * c + 2] - xo2;
+            const double s = dx * n0 + dy * n1 + dz * n2;
+            if (!(s > s_cur)) continue;
+            const double px = dx - s * n0, py = dy - s * n1, pz = dz - s * n2;
+            const double d2 = px * px + py * py + pz * pz;
+            const bool better = (best < 0) || (d2 < bd2) || (d2 == bd2 && s < bs) || (d2 == bd2 && s == bs && c < best);
+            if (better) { best = c; bs = s; bd2 = d2; }
+        }
+        if (best < 0) { dead = true; return; }
+        const double vp = n0 * (a.vel[3 * best] - vo0) + n1 * (a.vel[3 * best + 1] - vo1) +
+                          n2 * (a.vel[3 * best + 2] - vo2);
+        if (!emit<FILL>(a, base, len, x, (int32_t)best, bs - s_cur, vp, va, ba)) { overflow = true; return; }
+        s_cur = bs;
+        cur = best;
+        if (a.bdy[best]) return;
+    }
+}
+
+// Spherically symmetric shells on +z: crossings of the ray with sphere j at
+// s = -r_o mu +- sqrt(r_j^2 - r_o^2 (1 - mu^2)), in increasing s; an empty core below the
+// first radius carries no path length; a first radius of 0 is a centre point.
+template <bool FILL>
+__device__ void walk_sph1d(const TraceArgs &a, int64_t o, int r, int64_t base, int32_t &len, int32_t &x,
+                           bool &overflow) {
+    const double mu = a.dirs[3 * r + 2];
+    const double ro = a.pos[3 * o + 2];
+    const double p2 = ro * ro * (1.0 - mu * mu);
+    const double vro = a.vel[3 * o + 2];
+    const int64_t N = a.n;
+    const double r0 = a.pos[2];
+    double va = 0.0, ba = a.b[o];
+    double s_prev = 0.0;
+    len = 0;
+    x = 0;
+    overflow = false;
+    int64_t j = o;
+    bool through_core = false;
+    const bool inward = (mu < 0.0 && ro > 0.0);
+    if (inward) {
+        for (j = o - 1; j >= 0; j--) {
+            const double rj = a.pos[3 * j + 2];
+            const double q = rj * rj - p2;
+            if (rj == 0.0 && p2 == 0.0) {
+                const double s = -ro * mu;
+                if (!emit<FILL>(a, base, len, x, (int32_t)j, s - s_prev, -vro * mu, va, ba)) { overflow = true; return; }
+                s_prev = s;
+                j--;
+                break;
+            }
+            if (!(q > 0.0) || rj == 0.0) break;
+            const double s = -ro * mu - sqrt(q);
+            const double vp = a.vel[3 * j + 2] * (ro * mu + s) / rj - vro * mu;
+            if (!emit<FILL>(a, base, len, x, (int32_t)j, s - s_prev, vp, va, ba)) { overflow = true; return; }
+            s_prev = s;
+        }
+        if (j < 0 && r0 > 0.0) through_core = true;
+        j = j + 1;
+        if (j == 0 && r0 == 0.0) j = 1;
+    }
+    const int64_t jstart = inward ? j : o + 1;
+    for (int64_t k = jstart; k < N; k++) {
+        const double rk = a.pos[3 * k + 2];
+        const double q = rk * rk - p2;
+        if (q < 0.0) continue;
+        const double s = -ro * mu + sqrt(q);
+        const bool core_chord = through_core && k == jstart;
+        if (!(s > s_prev) && !core_chord) continue;
+        const double dsv = core_chord ? 0.0 : s - s_prev;
+        const double vp = (rk > 0.0 ? a.vel[3 * k + 2] * (ro * mu + s) / rk : 0.0) - vro * mu;
+        if (!emit<FILL>(a, base, len, x, (int32_t)k, dsv, vp, va, ba)) { overflow = true; return; }
+        s_prev = s;
+    }
+}
+
+// One thread per (origin, direction); consecutive threads take consecutive origins of the
+// same direction so that neighbouring walks share cache lines.
+template <bool FILL>
+__global__ void k_trace(TraceArgs a) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= a.n * a.R) return;
+    const int r = (int)(t / a.n);
+    const int64_t o = t - (int64_t)r * a.n;
+    const int64_t ray = o * a.R + r;
+    const int64_t base = FILL ? a.ray_off[ray] : 0;
+    int32_t len = 0, x = 0;
+    bool dead = false, overflow = false;
+    if (a.geometry == MG_GEOM_SPHERICAL_1D) walk_sph1d<FILL>(a, o, r, base, len, x, overflow);
+    else walk_3d<FILL>(a, o, r, base, len, x, dead, overflow);
+    if (overflow) atomicOr(a.err, 1);
+    if (!FILL) {
+        a.len[ray] = len;
+        a.xlen[ray] = dead ? -x - 1 : x;   // sign marks a dead end
+    }
+}
+
+// ---------------------------------------------------------------- exclusive scan
+// Exclusive prefix sum of int32 counts into int64 offsets, in three passes: per-block
+// sums, a single-block scan of the block sums, then per-block scans with their offsets.
+constexpr int kScanBlock = 1024;
+
+__device__ __forceinline__ int64_t warp_incl_scan(int64_t v) {
+    const int lane = threadIdx.x & 31;
+    for (int d = 1; d < 32; d <<= 1) {
+        int64_t y = __shfl_up_sync(0xffffffffu, v, d);
+        if (lane >= d) v += y;
+    }
+    return v;
+}
+
+__device__ int64_t block_excl_scan(int64_t v, int64_t *total) {
+    __shared__ int64_t wsum[32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int64_t inc = warp_incl_scan(v);
+    if (lane == 31) wsum[w] = inc;
+    __syncthreads();
+    if (w == 0) {
+        int64_t s = (lane < (int)(blockDim.x >> 5)) ? wsum[lane] : 0;
+        s = warp_incl_scan(s);
+        wsum[lane] = s;
+    }
+    __syncthreads();
+    int64_t off = w ? wsum[w - 1] : 0;
+    if (total) *total = wsum[(blockDim.x >> 5) - 1];
+    __syncthreads();
+    return off + inc - v;
+}
+
+__global__ void k_scan_blocks(const int32_t *cnt, int64_t m, int64_t *bsum) {
+    int64_t i = (int64_t)blockIdx.x * kScanBlock + threadIdx.x;
+    int64_t v = i < m ? cnt[i] : 0;
+    int64_t tot;
+    block_excl_scan(v, &tot);
+    if (threadIdx.x == 0) bsum[blockIdx.x] = tot;
+}
+
+__global__ void k_scan_sums(int64_t *bsum, int64_t nb) {
+    // single block: sequential chunks of kScanBlock
+    int64_t carry = 0;
+    for (int64_t c0 = 0; c0 < nb; c0 += kScanBlock) {
+        int64_t i = c0 + threadIdx.x;
+        int64_t v = i < nb ? bsum[i] : 0;
+        int64_t tot;
+        int64_t ex = block_excl_scan(v, &tot);
+        if (i < nb) bsum[i] = ex + carry;
+        carry += tot;
+        __syncthreads();
+    }
+}
+
+__global__ void k_scan_apply(const int32_t *cnt, int64_t m, const int64_t *bsum, int64_t *out) {
+    int64_t i = (int64_t)blockIdx.x * kScanBlock + threadIdx.x;
+    int64_t v = i < m ? cnt[i] : 0;
+    int64_t ex = block_excl_scan(v, nullptr);
+    if (i < m) out[i] = bsum[blockIdx.x] + ex;
+    if (i == m - 1) out[m] = bsum[blockIdx.x] + ex + v;
+}
+
+// ---------------------------------------------------------------- statistics
+__global__ void k_ray_stats(int64_t n, int R, int P, const int32_t *pf, const int32_t *pb, const int32_t *len,
+                            int32_t *xlen, unsigned long long *st) {
+    // st: [0] elements, [1] expanded, [2] max pair length, [3] dead ends
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned long long el = 0, ex = 0, mx = 0, dead = 0;
+    if (t < n * R) {
+        int32_t xv = xlen[t];
+        if (xv < 0) { dead = 1; xv = -xv - 1; xlen[t] = xv; }
+        el = (unsigned long long)len[t];
+        ex = (unsigned long long)xv;
+    }
+    __syncthreads();
+    if (t < n * P) {
+        const int64_t o = t / P;
+        const int p = (int)(t - o * P);
+        int32_t a = xlen[o * R + pf[p]], b = xlen[o * R + pb[p]];
+        a = a < 0 ? -a - 1 : a;
+        b = b < 0 ? -b - 1 : b;
+        mx = (unsigned long long)(a + b + 1);
+    }
+    for (int d = 16; d; d >>= 1) {
+        el += __shfl_down_sync(0xffffffffu, el, d);
+        ex += __shfl_down_sync(0xffffffffu, ex, d);
+        dead += __shfl_down_sync(0xffffffffu, dead, d);
+        unsigned long long m2 = __shfl_down_sync(0xffffffffu, mx, d);
+        mx = m2 > mx ? m2 : mx;
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(&st[0], el);
+        atomicAdd(&st[1], ex);
+        atomicMax(&st[2], mx);
+        atomicAdd(&st[3], dead);
+    }
+}
+
+__global__ void k_to_float(const double *a, float *b, int64_t m) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < m) b[i] = (float)a[i];
+}
+
+}  // namespace
+
+int mg_scan_counts(mg_ctx *ctx, const int32_t *d_cnt, int64_t m, int64_t *d_out) {
+    int64_t nb = (m + kScanBlock - 1) / kScanBlock;
+    int64_t *bsum = nullptr;
+    int rc;
+    if ((rc = mg_alloc(ctx, &bsum, nb))) return rc;
+    k_scan_blocks<<<(unsigned)nb, kScanBlock, 0, ctx->stream>>>(d_cnt, m, bsum);
+    k_scan_sums<<<1, kScanBlock, 0, ctx->stream>>>(bsum, nb);
+    k_scan_apply<<<(unsigned)nb, kScanBlock, 0, ctx->stream>>>(d_cnt, m, bsum, d_out);
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    cudaFree(bsum);
+    if (e != cudaSuccess) return mg_cuda_check(ctx, e, "scan");
+    return MG_OK;
+}
+
+int mg_launch_trace(mg_ctx *ctx) {
+    const int64_t nr = ctx->n * ctx->R;
+    int rc;
+    int32_t *d_len = nullptr, *d_xlen = nullptr;
+    if ((rc = mg_alloc(ctx, &d_len, nr)) || (rc = mg_alloc(ctx, &d_xlen, nr))) return rc;
+    if ((rc = mg_alloc(ctx, &ctx->d_ray_off, nr + 1))) return rc;
+    MG_CUDA(cudaMemsetAsync(ctx->d_err, 0, sizeof(int32_t), ctx->stream));
+    TraceArgs a{};
+    a.n = ctx->n; a.R = ctx->R; a.geometry = ctx->geometry;
+    a.pos = ctx->d_pos; a.vel = ctx->d_vel; a.b = ctx->d_b; a.dirs = ctx->d_dirs;
+    a.nbr_off = ctx->d_nbr_off; a.nbr_idx = ctx->d_nbr_idx; a.bdy = ctx->d_bdy;
+    a.dshift_frac = ctx->opt.dshift_frac; a.max_steps = ctx->opt.max_steps;
+    a.len = d_len; a.xlen = d_xlen; a.err = ctx->d_err;
+    const int bs = 128;
+    const unsigned grid = (unsigned)((nr + bs - 1) / bs);
+    {
+        MgTimed t(ctx, "trace_count");
+        k_trace<false><<<grid, bs, 0, ctx->stream>>>(a);
+    }
+    MG_CUDA(cudaGetLastError());
+    if ((rc = mg_scan_counts(ctx, d_len, nr, ctx->d_ray_off))) return rc;
+    int64_t total = 0;
+    int32_t kerr = 0;
+    MG_CUDA(cudaMemcpy(&total, ctx->d_ray_off + nr, 8, cudaMemcpyDeviceToHost));
+    MG_CUDA(cudaMemcpy(&kerr, ctx->d_err, 4, cudaMemcpyDeviceToHost));
+    if (kerr) {
+        cudaFree(d_len); cudaFree(d_xlen);
+        return mg_fail(ctx, MG_ERR_CAPACITY, "ray tracing: a half-ray exceeded max_steps");
+    }
+    if ((rc = mg_alloc(ctx, &ctx->d_cells, total)) || (rc = mg_alloc(ctx, &ctx->d_xcum, total)) ||
+        (rc = mg_alloc(ctx, &ctx->d_ds, total)) || (rc = mg_alloc(ctx, &ctx->d_vpar, total)) ||
+        (rc = mg_alloc(ctx, &ctx->d_dsf, total)) || (rc = mg_alloc(ctx, &ctx->d_vparf, total)))
+        return rc;
+    a.ray_off = ctx->d_ray_off; a.cells = ctx->d_cells; a.xcum = ctx->d_xcum; a.ds = ctx->d_ds; a.vpar = ctx->d_vpar;
+    {
+        MgTimed t(ctx, "trace_fill");
+        k_trace<true><<<grid, bs, 0, ctx->stream>>>(a);
+    }
+    MG_CUDA(cudaGetLastError());
+    if (total) {
+        k_to_float<<<(unsigned)((total + 255) / 256), 256, 0, ctx->stream>>>(ctx->d_ds, ctx->d_dsf, total);
+        k_to_float<<<(unsigned)((total + 255) / 256), 256, 0, ctx->stream>>>(ctx->d_vpar, ctx->d_vparf, total);
+    }
+    MG_CUDA(cudaMemsetAsync(ctx->d_scal, 0, 4 * sizeof(unsigned long long), ctx->stream));
+    const int64_t np = std::max<int64_t>(nr, ctx->n * ctx->P);
+    k_ray_stats<<<(unsigned)((np + 255) / 256), 256, 0, ctx->stream>>>(ctx->n, ctx->R, ctx->P, ctx->d_pf, ctx->d_pb,
+                                                                          d_len, d_xlen, ctx->d_scal);
+    MG_CUDA(cudaGetLastError());
+    unsigned long long st[4];
+    MG_CUDA(cudaMemcpyAsync(st, ctx->d_scal, sizeof(st), cudaMemcpyDeviceToHost, ctx->stream));
+    MG_CUDA(cudaStreamSynchronize(ctx->stream));
+    cudaFree(d_len);
+    cudaFree(d_xlen);
+    ctx->n_elements = (int64_t)st[0];
+    ctx->n_expanded = (int64_t)st[1];
+    ctx->max_pair_len = (int64_t)st[2];
+    ctx->n_dead = (int64_t)st[3];
+    ctx->traced = true;
+    return MG_OK;
+}
