@@ -1,0 +1,313 @@
+"""Benchmark of the ALI hot path on synthetic inputs shaped like the paper's models.
+
+A step is one accelerated Lambda iteration on the 3D clumpy cloud (50k points, 48 HEALPix
+rays = 24 ray pairs, 5-level rotor with 4 lines x 31 Gauss-Hermite bins): line data ->
+Feautrier formal solve of every (point, ray pair, bin) -> statistical equilibrium ->
+convergence measure. The rays are traced once before the timed region (the mesh is
+static across iterations, Sec. 3.2).
+
+metric: point-ray-pair-frequency Feautrier solves per second (whole job).
+value : device-resident inputs, CUDA events around K steps on the library's stream.
+e2e   : the same steps through the C ABI with host buffers: populations copied in from
+        pinned memory and read back every step.
+Multi-GPU (torchrun): every rank solves its own independently seeded model; no
+collective on the data path (weak scaling); max time over ranks.
+
+--impl reference times the FP64 CPU oracle on host cores on a bounded sample of the
+same workload (the reference arm: there is no other implementation to run).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+WORKLOAD = dict(workload="3D clumpy cloud, 50k points, k=16 symmetric NN, 48 rays (HEALPix nside=2), "
+                         "5-level linear rotor, 4 lines x 31 Gauss-Hermite bins, radial outflow to 10 km/s",
+                n_points=50_000, n_rays=48, n_lines=4, n_bins=31)
+METRIC = "point-ray-pair-frequency Feautrier solves/s"
+UNIT = "solves/s"
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class Clocks:
+    """Samples nvidia-smi SM clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": []}
+        if self.proc is None:
+            return out
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1])); mx.append(float(p[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if sm:
+            out = {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                   "samples": len(sm)}
+        try:
+            os.remove(self.path)
+        except OSError:
+            pass
+        return out
+
+
+def build_model(seed):
+    import synthetic as syn
+    return syn.model_clumpy_3d(n=WORKLOAD["n_points"], seed=seed)
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+# ------------------------------------------------------------------ oracle (CPU) timing
+def time_oracle(model, target_s=15.0, seed=0):
+    """Times the FP64 oracle's formal solve on a bounded sample of origin points, grown
+    until it takes about target_s seconds; returns solves/s, threads and the sample."""
+    from oracle import Oracle
+    threads = os.cpu_count() or 1
+    o = Oracle(model, nthreads=threads)
+    pops = o.lte()
+    rng = np.random.default_rng(seed)
+    P = o.dirs.shape[0] // 2
+    F = model.species.n_lines * o.Q
+    k = 16
+    while True:
+        origins = np.sort(rng.choice(model.n, k, replace=False))
+        t0 = time.perf_counter()
+        o.formal_solve(pops, origins)
+        dt = time.perf_counter() - t0
+        if dt > target_s / 4 or k >= model.n:
+            break
+        k = min(model.n, int(k * max(2.0, target_s / 4 / max(dt, 1e-3))))
+    solves = k * P * F
+    return solves / dt, threads, f"{k} of {model.n} origin points ({solves} solves, {dt:.1f} s)"
+
+
+# ------------------------------------------------------------------ GPU arm
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+    import paper_1912_08445_gb300 as mg
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    stream = torch.cuda.Stream()
+    model = build_model(seed=rank)
+    prec = mg.MG_MIXED if args.precision == "mixed" else mg.MG_FP64
+    ctx = mg.Context(device=local, precision=prec, profile=0)
+    ctx.set_stream(stream.cuda_stream)
+    ctx.load_model(model)
+    st, _ = ctx.trace_rays()
+    ctx.init_populations()
+    solves, updates = ctx.work_counts()
+    n, lev = model.n, model.species.n_lev
+
+    def step():
+        ctx.formal_solve()
+        ctx.update_populations()
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize()
+        if ws > 1:
+            dist.barrier()
+        clocks = Clocks(local)
+        clocks.start()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        clk = clocks.stop()
+
+        # per-kernel times of the dominant kernel (events on the same stream)
+        ctx.close()
+        ctx = mg.Context(device=local, precision=prec, profile=1)
+        ctx.set_stream(stream.cuda_stream)
+        ctx.load_model(model)
+        ctx.trace_rays()
+        ctx.init_populations()
+        step()
+        ctx.reset_kernel_times()
+        for _ in range(max(2, min(args.steps, 5))):
+            step()
+        kt = ctx.kernel_times()
+
+        # end to end through the C ABI with pinned host buffers
+        h_in = torch.empty((n, lev), dtype=torch.float64, pin_memory=True).numpy()
+        h_out = torch.empty((n, lev), dtype=torch.float64, pin_memory=True).numpy()
+        h_in[:] = ctx.get_populations()
+        for _ in range(2):
+            ctx.set_populations(h_in); step(); ctx.get_populations(out=h_out)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            ctx.set_populations(h_in)
+            step()
+            ctx.get_populations(out=h_out)
+        torch.cuda.synchronize()
+        e2e_s = time.perf_counter() - t0
+
+    t = torch.tensor([ms, e2e_s * 1e3], dtype=torch.float64, device=f"cuda:{local}")
+    if ws > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.barrier()
+    ms_max, e2e_ms_max = float(t[0]), float(t[1])
+
+    if rank == 0:
+        pk, pk_kind = peaks()
+        kname = "feautrier_mixed" if prec == mg.MG_MIXED else "feautrier_fp64"
+        k_ms, k_n = kt.get(kname, (float("nan"), 1))
+        k_avg = k_ms / max(k_n, 1)
+        # algorithmic work of one formal-solve launch: cell-frequency updates x flops per
+        # update (FP32: 16 FMA-pipe flops + 2 MUFU ops; FP64: 18 flops, exp and divide
+        # counted as one each)
+        flops_per_update = 18.0
+        if prec == mg.MG_MIXED:
+            peak = 152 * 128 * 2 * 2.07e9 / 1e12
+            peak_note = "FP32 FMA lanes x 2 x 2.07 GHz (derived)"
+        else:
+            peak = 1.25
+            peak_note = "nominal FP64 1.25 TFLOP/s (GB300)"
+        achieved = updates * flops_per_update / (k_avg * 1e-3) / 1e12
+        roof = {"bound": "alu", "achieved": round(achieved, 4), "peak": peak, "unit": "TFLOP/s",
+                "frac": round(achieved / peak, 4), "traffic": None, "kernel": kname,
+                "kernel_ms": round(k_avg, 3), "peak_source": peak_note,
+                "cell_freq_updates_per_launch": updates,
+                "hbm_algorithmic_frac_of_measured": None}
+        cpu_v, cores, sample = time_oracle(model) if args.cpu_baseline else (None, None, None)
+        value = ws * solves * args.steps / (ms_max * 1e-3)
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64" if prec == mg.MG_MIXED else "f64", "data": "synthetic",
+            "config": dict(WORKLOAD, precision=args.precision, l2="inputs larger than L2 (ray store "
+                           f"{st['n_elements'] * 24 / 1e9:.2f} GB read per step)",
+                           parallelism=f"replicas x{ws}", solves_per_step=solves,
+                           cell_freq_updates_per_step=updates, mean_pair_len=round(st["mean_pair_len"], 1)),
+            "e2e": {"value": ws * solves * args.steps / (e2e_ms_max * 1e-3), "unit": UNIT,
+                    "h2d_bytes_per_step": n * lev * 8, "d2h_bytes_per_step": n * lev * 8},
+            "gpu_launches": 3 * args.steps,
+            "clocks": clk,
+            "roofline": roof,
+            "cpu_baseline": None if cpu_v is None else {"value": cpu_v, "unit": UNIT, "cores": cores,
+                                                        "kind": "oracle", "sample": sample},
+            "peaks_source": pk_kind,
+        }
+        print(json.dumps(line))
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+# ------------------------------------------------------------------ reference arm
+def run_reference(args):
+    ws, rank, local = dist_env()
+    if rank != 0:
+        return
+    model = build_model(seed=0)
+    from oracle import Oracle
+    threads = os.cpu_count() or 1
+    o = Oracle(model, nthreads=threads)
+    pops = o.lte()
+    P = o.dirs.shape[0] // 2
+    F = model.species.n_lines * o.Q
+    k = 24
+    rng = np.random.default_rng(0)
+    origins = np.sort(rng.choice(model.n, k, replace=False))
+    for _ in range(args.warmup):
+        o.formal_solve(pops, origins[:4])
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        J, L, E = o.formal_solve(pops, origins)
+    dt = time.perf_counter() - t0
+    solves = k * P * F * args.steps
+    v = solves / dt
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": dict(WORKLOAD, precision="fp64"),
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": f"{k} of {model.n} origin points per step ({k * P * F} solves)"},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

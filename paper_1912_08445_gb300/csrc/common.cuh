@@ -17,6 +17,12 @@ constexpr double kPi = 3.14159265358979323846;
 
 constexpr int kMaxLev = 64;
 
+// Scales of the FP32 formal solve: intensities in units of kI0 (W m^-2 Hz^-1 sr^-1);
+// float line data hold chi_int * kChiScale and eta_int * kEtaScale = chi scale / kI0.
+constexpr float kI0 = 1e-20f;
+constexpr double kChiScale = 1e5;
+constexpr double kEtaScale = 1e25;
+
 // Per-line constants of the species, copied to the device once.
 struct LineConst {
     double nu;      // line-centre frequency (E_u - E_l)/h
@@ -77,6 +83,7 @@ struct mg_ctx {
     std::vector<double> h_E, h_g, h_Tgrid, h_Kdown;
     std::vector<mg::LineConst> h_lines;
     mg::LineConst *d_lines = nullptr;
+    float *d_lconst = nullptr;    // [2L]: c/(nu_l sqrt(pi))/kChiScale, nu_l in GHz (FP32 solve)
     double *d_E = nullptr, *d_g = nullptr, *d_Tgrid = nullptr, *d_Kdown = nullptr;
     double *d_coll = nullptr;     // [n][n_pairs][2] (down, up) collision rates
     bool coll_ready = false;
@@ -168,6 +175,7 @@ struct MgTimed {
 // ---------------------------------------------------------------- launchers
 int mg_launch_trace(mg_ctx *ctx);
 int mg_launch_line_data(mg_ctx *ctx);
+int mg_launch_line_data_mixed(mg_ctx *ctx);
 int mg_launch_feautrier(mg_ctx *ctx);
 int mg_launch_lte(mg_ctx *ctx);
 int mg_launch_collision_rates(mg_ctx *ctx);

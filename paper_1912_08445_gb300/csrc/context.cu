@@ -107,7 +107,7 @@ extern "C" int mg_destroy(mg_ctx *ctx) {
     free_rays(ctx);
     mg_free(ctx->d_pos); mg_free(ctx->d_vel); mg_free(ctx->d_nbr_off); mg_free(ctx->d_nbr_idx);
     mg_free(ctx->d_bdy); mg_free(ctx->d_ncoll); mg_free(ctx->d_T); mg_free(ctx->d_nspec);
-    mg_free(ctx->d_b); mg_free(ctx->d_bf); mg_free(ctx->d_lines); mg_free(ctx->d_E); mg_free(ctx->d_g);
+    mg_free(ctx->d_b); mg_free(ctx->d_bf); mg_free(ctx->d_lines); mg_free(ctx->d_lconst); mg_free(ctx->d_E); mg_free(ctx->d_g);
     mg_free(ctx->d_Tgrid); mg_free(ctx->d_Kdown); mg_free(ctx->d_coll); mg_free(ctx->d_ovl_off);
     mg_free(ctx->d_ovl); mg_free(ctx->d_dirs); mg_free(ctx->d_pf); mg_free(ctx->d_pb);
     mg_free(ctx->d_roots); mg_free(ctx->d_weights); mg_free(ctx->d_pops); mg_free(ctx->d_pops_new);
@@ -319,7 +319,14 @@ extern "C" int mg_set_species(mg_ctx *ctx, int32_t n_lev, const double *E, const
         c.Blu = g[up[l]] / g[lo[l]] * c.Bul;
         c.pre = kH * c.nu / (4.0 * kPi);
     }
+    std::vector<float> lconst(2 * n_lines);
+    for (int l = 0; l < n_lines; l++) {
+        lconst[l] = (float)(kC / (ctx->h_lines[l].nu * kSqrtPi) / kChiScale);
+        lconst[n_lines + l] = (float)(ctx->h_lines[l].nu * 1e-9);
+    }
     int rc;
+    if ((rc = mg_alloc(ctx, &ctx->d_lconst, 2 * n_lines))) return rc;
+    if ((rc = upload(ctx, ctx->d_lconst, lconst.data(), 4 * 2 * n_lines))) return rc;
     if ((rc = mg_alloc(ctx, &ctx->d_lines, n_lines)) || (rc = mg_alloc(ctx, &ctx->d_E, n_lev)) ||
         (rc = mg_alloc(ctx, &ctx->d_g, n_lev)) || (rc = mg_alloc(ctx, &ctx->d_Tgrid, n_T)) ||
         (rc = mg_alloc(ctx, &ctx->d_Kdown, (size_t)npairs * n_T)))

@@ -246,11 +246,11 @@ __global__ void k_feautrier64(SolveArgs a) {
 }  // namespace
 
 int mg_launch_line_data(mg_ctx *ctx) {
+    if (ctx->opt.precision == MG_MIXED) return mg_launch_line_data_mixed(ctx);
     const int64_t m = ctx->n * ctx->n_lines;
     MgTimed t(ctx, "line_data");
     k_line_data<<<(unsigned)((m + 255) / 256), 256, 0, ctx->stream>>>(
-        ctx->n, ctx->n_lines, ctx->n_lev, ctx->d_pops, ctx->d_lines, ctx->d_line,
-        ctx->opt.precision == MG_MIXED ? ctx->d_linef : nullptr);
+        ctx->n, ctx->n_lines, ctx->n_lev, ctx->d_pops, ctx->d_lines, ctx->d_line, nullptr);
     MG_CUDA(cudaGetLastError());
     return MG_OK;
 }

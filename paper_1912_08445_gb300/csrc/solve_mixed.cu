@@ -1,6 +1,346 @@
-// K3 in mixed precision (FP32 formal solve). Placeholder until the FP32 kernel lands.
+// K3 in mixed precision: the Feautrier formal solve of Sec. 3.3-3.4 in FP32 (the
+// statistical equilibrium that follows stays in FP64).
+//
+// Layout: one CTA per origin point, one warp per line (lanes = Gauss-Hermite bins; a
+// warp loops when there are more lines than warps or more bins than lanes). For each ray
+// pair the CTA stages the expanded pair in shared memory:
+//   pt[k]   = (ds_k / 2, v_k, sqrt(log2 e)/b_k, 0)          (float4)
+//   ln[k][l] = (X_l = chi_int c / (nu_l b sqrt(pi)), S_l = eta_int/chi_int / I0)  (float2)
+// so that chi = X exp(-x^2) and, for a line that overlaps no other line, the source
+// function S is frequency independent. Intensities are carried in units of
+// I0 = 1e-20 W m^-2 Hz^-1 sr^-1 and the float line data are scaled (chi x 1e5,
+// eta x 1e25) so that no FP32 quantity underflows.
+//
+// Per point and bin the sweep costs one ex2 and one rcp (MUFU) and ~12 FMA-pipe ops:
+//   x' = (a_q - v (1 + a_q/c)) ib,  e = 2^(-x'^2),  chi = max(X e, chi_min),
+//   dtau = max((chi_prev + chi) ds/2, dtau_min),  t = (dtau_prev + dtau)/2,
+//   Phi = t + Phi iota,  iota = 1/(1 + dtau Phi),  psi = (t S + psi) iota,
+// the rescaled Rybicki-Hummer recursion described with the FP64 kernel.
+#include <cmath>
 #include "common.cuh"
 
+using namespace mg;
+
+namespace {
+
+constexpr float kSqrtLog2e = 1.2011224087864498f;
+
+__device__ __forceinline__ float ex2f(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float rcpf(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__global__ void k_line_data_f32(int64_t n, int L, int nlev, const double *__restrict__ pops,
+                                const LineConst *__restrict__ lc, double *__restrict__ line,
+                                float *__restrict__ linef) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n * L) return;
+    const int64_t c = t / L;
+    const int l = (int)(t - c * L);
+    const LineConst k = lc[l];
+    const double nu_ = pops[c * nlev + k.up], nl_ = pops[c * nlev + k.lo];
+    const double eta = k.pre * nu_ * k.A;
+    const double chi = k.pre * (nl_ * k.Blu - nu_ * k.Bul);
+    line[2 * t] = eta;
+    line[2 * t + 1] = chi;
+    linef[2 * t] = (float)(eta * kEtaScale);
+    linef[2 * t + 1] = (float)(chi * kChiScale);
+}
+
+struct MixArgs {
+    int64_t n;
+    int32_t R, P, L, Q;
+    const int32_t *pf, *pb;
+    const int64_t *ray_off;
+    const int32_t *cells, *xcum;
+    const float *ds, *vpar, *b;
+    const float *line;           // [n][L][2] scaled (eta, chi)
+    const float *kline;          // [L] c / (nu_l sqrt(pi)) / kChiScale
+    const float *nu_ghz;         // [L]
+    const double *roots, *weights;
+    const int32_t *ovl_off;
+    const Overlap *ovl;
+    float chi_min, dtau_min, inv_chi_min;
+    float planck_a, planck_b;    // B'(nu) = a nu_G^3 / expm1(b nu_G): a = 2h 1e27/c^2/I0, b = h 1e9/(k T_cmb)
+    double *J, *Lout, *Jeff, *Lc, *Jnu;
+    int32_t kmax;
+    int32_t overlap;             // some line overlaps another
+    int32_t *err;
+};
+
+__device__ __forceinline__ float planck_f(const MixArgs &a, float nu_g) {
+    return a.planck_a * nu_g * nu_g * nu_g / expm1f(a.planck_b * nu_g);
+}
+
+// Stages half-ray (o, r) in FP32: point x of the half sits at pair index base + dir x.
+__device__ void stage_half32(const MixArgs &a, int64_t o, int r, int base, int dir, float4 *pt, float2 *ln) {
+    const int L = a.L;
+    const int64_t off = a.ray_off[o * a.R + r];
+    const int len = (int)(a.ray_off[o * a.R + r + 1] - off);
+    for (int e = threadIdx.x; e < len; e += blockDim.x) {
+        const int64_t c = a.cells[off + e];
+        const int64_t prev = e ? a.cells[off + e - 1] : o;
+        const int x0 = e ? a.xcum[off + e - 1] : 0;
+        const int ns = a.xcum[off + e] - x0 - 1;
+        const float pv = e ? a.vpar[off + e - 1] : 0.0f;
+        const float ve = a.vpar[off + e];
+        const float hds = 0.5f * a.ds[off + e] / (float)(ns + 1);
+        const float bp = a.b[prev], bc = a.b[c];
+        const float2 *lp = reinterpret_cast<const float2 *>(a.line) + prev * L;
+        const float2 *lq = reinterpret_cast<const float2 *>(a.line) + c * L;
+        for (int j = 1; j <= ns + 1; j++) {
+            const float w = (float)j / (float)(ns + 1);
+            const int idx = base + dir * (x0 + j - 1);
+            const float bb = (1.0f - w) * bp + w * bc;
+            const float ib = 1.0f / bb;
+            // the path length is stored with the point farther from the origin
+            pt[idx] = make_float4(hds, (1.0f - w) * pv + w * ve, kSqrtLog2e * ib, 0.0f);
+            for (int l = 0; l < L; l++) {
+                const float2 p0 = lp[l], p1 = lq[l];
+                const float et = (1.0f - w) * p0.x + w * p1.x;
+                const float ch = (1.0f - w) * p0.y + w * p1.y;
+                const float X = ch * a.kline[l] * ib;
+                const float S = ch > 0.0f ? et / ch : 0.0f;
+                ln[(size_t)idx * L + l] = make_float2(X, S);
+            }
+        }
+    }
+}
+
+struct Side32 {
+    float phi_iota, psi, dtau;
+};
+
+// Opacity and emissivity at point k for bin (l, aq); fast path: line l alone.
+template <bool OVL>
+__device__ __forceinline__ void point32(const MixArgs &a, int l, float aq, float A1, int k, const float4 *pt,
+                                        const float2 *ln, float &chi, float &S, float &chil, float &etal) {
+    const float4 p = pt[k];
+    if (!OVL) {
+        const float2 d = ln[(size_t)k * a.L + l];
+        const float x = fmaf(-p.y, A1, aq) * p.z;
+        const float e = ex2f(-x * x);
+        chil = d.x * e;
+        etal = chil * d.y;
+        if (chil >= a.chi_min) {
+            chi = chil;
+            S = d.y;
+        } else {   // opacity floor: S = eta / chi_min
+            chi = a.chi_min;
+            S = etal * a.inv_chi_min;
+        }
+        return;
+    }
+    // general case: sum over the lines that can reach this bin
+    float ch = 0.f, et = 0.f;
+    const int o0 = a.ovl_off[l], o1 = a.ovl_off[l + 1];
+    const float base = fmaf(-p.y, A1, aq);
+    for (int i = o0; i < o1; i++) {
+        const Overlap ov = a.ovl[i];
+        const float2 d = ln[(size_t)k * a.L + ov.l2];
+        const float x = ((float)ov.dnl + (float)ov.rat * base) * p.z;
+        const float c2 = d.x * ex2f(-x * x);
+        ch += c2;
+        et += c2 * d.y;
+        if (i == o0) { chil = c2; etal = c2 * d.y; }
+    }
+    chi = fmaxf(ch, a.chi_min);
+    S = et / chi;
+}
+
+template <bool OVL>
+__device__ __forceinline__ Side32 sweep32(const MixArgs &a, int l, float aq, float A1, float nu_og, int kstart,
+                                          int kend, int step, const float4 *pt, const float2 *ln, float &chi_o,
+                                          float &S_o, float &chil_o, float &etal_o) {
+    float chi_p, S_p, cl, el;
+    point32<OVL>(a, l, aq, A1, kstart, pt, ln, chi_p, S_p, cl, el);
+    const float I = planck_f(a, nu_og * (1.0f - pt[kstart].y * (float)(1.0 / kC)));
+    float Phi, iota, psi, dt_p;
+    // boundary row (first interval)
+    {
+        const int k = kstart + step;
+        float chi, S;
+        point32<OVL>(a, l, aq, A1, k, pt, ln, chi, S, cl, el);
+        const float hds = pt[step > 0 ? k : kstart].x;
+        const float dt = fmaxf((chi_p + chi) * hds, a.dtau_min);
+        Phi = fmaf(0.5f, dt, 1.0f);
+        iota = rcpf(fmaf(dt, Phi, 1.0f));
+        psi = fmaf(0.5f * dt, S_p, I) * iota;
+        dt_p = dt;
+        chi_p = chi;
+        S_p = S;
+        if (k == kend) {
+            chi_o = chi; S_o = S; chil_o = cl; etal_o = el;
+            return Side32{Phi * iota, psi, dt_p};
+        }
+    }
+    for (int k = kstart + 2 * step;; k += step) {
+        float chi, S;
+        point32<OVL>(a, l, aq, A1, k, pt, ln, chi, S, cl, el);
+        const float hds = pt[step > 0 ? k : k - step].x;
+        const float dt = fmaxf((chi_p + chi) * hds, a.dtau_min);
+        const float t = 0.5f * (dt_p + dt);
+        Phi = fmaf(Phi, iota, t);
+        iota = rcpf(fmaf(dt, Phi, 1.0f));
+        psi = fmaf(t, S_p, psi) * iota;
+        dt_p = dt;
+        chi_p = chi;
+        S_p = S;
+        if (k == kend) {
+            chi_o = chi; S_o = S; chil_o = cl; etal_o = el;
+            break;
+        }
+    }
+    return Side32{Phi * iota, psi, dt_p};
+}
+
+template <bool OVL>
+__global__ void __launch_bounds__(256) k_feautrier_mixed(MixArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int L = a.L, Q = a.Q;
+    const int kmax = a.kmax;
+    float4 *pt = reinterpret_cast<float4 *>(smem_raw);
+    float2 *ln = reinterpret_cast<float2 *>(pt + kmax);
+    float4 *acc = reinterpret_cast<float4 *>(ln + (size_t)kmax * L);   // [L*Q]: (sum u, L, Jeff, 1-L)
+    const int64_t o = blockIdx.x;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+    for (int f = threadIdx.x; f < L * Q; f += blockDim.x) acc[f] = make_float4(0.f, 0.f, 0.f, 0.f);
+    const float bo = a.b[o];
+    const float2 *lo = reinterpret_cast<const float2 *>(a.line) + o * L;
+    for (int p = 0; p < a.P; p++) {
+        const int rf = a.pf[p], rb = a.pb[p];
+        const int64_t ofb = a.ray_off[o * a.R + rb], ofl = a.ray_off[o * a.R + rf];
+        const int lb = (int)(a.ray_off[o * a.R + rb + 1] - ofb);
+        const int lf = (int)(a.ray_off[o * a.R + rf + 1] - ofl);
+        const int Kb = lb ? a.xcum[ofb + lb - 1] : 0;
+        const int Kf = lf ? a.xcum[ofl + lf - 1] : 0;
+        const int K = Kb + 1 + Kf;
+        if (K > kmax) {
+            if (threadIdx.x == 0) atomicOr(a.err, 2);
+            continue;
+        }
+        __syncthreads();
+        stage_half32(a, o, rb, Kb - 1, -1, pt, ln);
+        stage_half32(a, o, rf, Kb + 1, +1, pt, ln);
+        if (threadIdx.x == 0) pt[Kb] = make_float4(0.f, 0.f, kSqrtLog2e / bo, 0.f);
+        for (int l = threadIdx.x; l < L; l += blockDim.x) {
+            const float2 d = lo[l];
+            const float X = d.y * a.kline[l] / bo;
+            ln[(size_t)Kb * L + l] = make_float2(X, d.y > 0.f ? d.x / d.y : 0.f);
+        }
+        __syncthreads();
+        for (int l = warp; l < L; l += nwarps) {
+            const float nu_g = a.nu_ghz[l];
+            for (int q = lane; q < Q; q += 32) {
+                const float aq = (float)(a.roots[q] * a.b[o]);
+                const float A1 = 1.0f + aq * (float)(1.0 / kC);
+                const float nu_og = nu_g * A1;
+                float u, lam, uml, oml, chi_o = 0.f, S_o = 0.f, chil = 0.f, etal = 0.f;
+                if (K == 1) {
+                    const float I = planck_f(a, nu_og);
+                    point32<OVL>(a, l, aq, A1, Kb, pt, ln, chi_o, S_o, chil, etal);
+                    u = I; lam = 0.f; uml = I; oml = 1.f;
+                } else {
+                    Side32 sb{1.f, 0.f, 0.f}, sf{1.f, 0.f, 0.f};
+                    if (Kb > 0) sb = sweep32<OVL>(a, l, aq, A1, nu_og, 0, Kb, +1, pt, ln, chi_o, S_o, chil, etal);
+                    if (Kf > 0) sf = sweep32<OVL>(a, l, aq, A1, nu_og, K - 1, Kb, -1, pt, ln, chi_o, S_o, chil, etal);
+                    if (Kb == 0 || Kf == 0) {
+                        const float Io = planck_f(a, nu_og);
+                        if (Kb == 0) sb.psi = Io;
+                        if (Kf == 0) sf.psi = Io;
+                    }
+                    const float sig = 2.0f / (sb.dtau + sf.dtau);
+                    const float pi2 = sb.phi_iota + sf.phi_iota;
+                    const float iD = 1.0f / fmaf(sig, pi2, 1.0f);
+                    const float ps = sig * (sb.psi + sf.psi);
+                    u = (S_o + ps) * iD;
+                    lam = iD;
+                    uml = ps * iD;
+                    oml = sig * pi2 * iD;
+                }
+                const float ichi = 1.0f / chi_o;
+                const float eta_o = S_o * chi_o;
+                float4 r = acc[l * Q + q];
+                r.x += u;
+                r.y += lam * chil * ichi;
+                r.z += uml + lam * (eta_o - etal) * ichi;
+                r.w += oml + lam * (chi_o - chil) * ichi;
+                acc[l * Q + q] = r;
+            }
+        }
+    }
+    __syncthreads();
+    // per-line weighted sums over bins, fixed order, in FP64
+    const double invP = 1.0 / a.P;
+    for (int t = threadIdx.x; t < 4 * L; t += blockDim.x) {
+        const int l = t >> 2, k = t & 3;
+        double s = 0.0;
+        for (int q = 0; q < Q; q++) {
+            const float4 r = acc[l * Q + q];
+            const float v = k == 0 ? r.x : (k == 1 ? r.y : (k == 2 ? r.z : r.w));
+            s += a.weights[q] * (double)v;
+        }
+        s *= invP;
+        if (k == 0 || k == 2) s *= (double)kI0;
+        double *dst = k == 0 ? a.J : (k == 1 ? a.Lout : (k == 2 ? a.Jeff : a.Lc));
+        dst[o * L + l] = s;
+    }
+    if (a.Jnu)
+        for (int f = threadIdx.x; f < L * Q; f += blockDim.x) a.Jnu[o * L * Q + f] = (double)acc[f].x * invP * (double)kI0;
+}
+
+}  // namespace
+
+int mg_launch_line_data_mixed(mg_ctx *ctx) {
+    const int64_t m = ctx->n * ctx->n_lines;
+    MgTimed t(ctx, "line_data");
+    k_line_data_f32<<<(unsigned)((m + 255) / 256), 256, 0, ctx->stream>>>(ctx->n, ctx->n_lines, ctx->n_lev,
+                                                                          ctx->d_pops, ctx->d_lines, ctx->d_line,
+                                                                          ctx->d_linef);
+    MG_CUDA(cudaGetLastError());
+    return MG_OK;
+}
+
 int mg_launch_feautrier_mixed(mg_ctx *ctx) {
-    return mg_fail(ctx, MG_ERR_ARG, "mixed precision formal solve not built yet");
+    const int L = ctx->n_lines, Q = ctx->Q;
+    bool overlap = false;
+    for (int l = 0; l < L; l++) overlap |= (ctx->h_ovl_off[l + 1] - ctx->h_ovl_off[l]) > 1;
+    MixArgs a{};
+    a.n = ctx->n; a.R = ctx->R; a.P = ctx->P; a.L = L; a.Q = Q;
+    a.pf = ctx->d_pf; a.pb = ctx->d_pb; a.ray_off = ctx->d_ray_off; a.cells = ctx->d_cells; a.xcum = ctx->d_xcum;
+    a.ds = ctx->d_dsf; a.vpar = ctx->d_vparf; a.b = ctx->d_bf; a.line = ctx->d_linef;
+    a.kline = ctx->d_lconst; a.nu_ghz = ctx->d_lconst + L;
+    a.roots = ctx->d_roots; a.weights = ctx->d_weights; a.ovl_off = ctx->d_ovl_off; a.ovl = ctx->d_ovl;
+    a.chi_min = (float)ctx->opt.chi_min; a.dtau_min = (float)ctx->opt.dtau_min;
+    a.inv_chi_min = (float)(1.0 / ctx->opt.chi_min);
+    a.planck_a = (float)(2.0 * kH * 1e27 / (kC * kC) / (double)kI0);
+    a.planck_b = (float)(kH * 1e9 / (kKB * ctx->opt.T_cmb));
+    a.J = ctx->d_J; a.Lout = ctx->d_L; a.Jeff = ctx->d_Jeff; a.Lc = ctx->d_Lc;
+    a.Jnu = ctx->opt.spectrum ? ctx->d_Jnu : nullptr;
+    a.kmax = (int32_t)ctx->max_pair_len;
+    a.overlap = overlap;
+    a.err = ctx->d_err;
+    size_t smem = (size_t)a.kmax * (16 + 8 * (size_t)L) + 16 * (size_t)L * Q;
+    if (smem > 227 * 1024) {
+        return mg_fail(ctx, MG_ERR_CAPACITY, "mixed formal solve: longest ray pair does not fit in shared memory");
+    }
+    int threads = 32 * std::min(L, 8);
+    MG_CUDA(cudaMemsetAsync(ctx->d_err, 0, 4, ctx->stream));
+    if (overlap) {
+        MG_CUDA(cudaFuncSetAttribute(k_feautrier_mixed<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        MgTimed t(ctx, "feautrier_mixed");
+        k_feautrier_mixed<true><<<(unsigned)ctx->n, threads, smem, ctx->stream>>>(a);
+    } else {
+        MG_CUDA(cudaFuncSetAttribute(k_feautrier_mixed<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        MgTimed t(ctx, "feautrier_mixed");
+        k_feautrier_mixed<false><<<(unsigned)ctx->n, threads, smem, ctx->stream>>>(a);
+    }
+    MG_CUDA(cudaGetLastError());
+    return MG_OK;
 }

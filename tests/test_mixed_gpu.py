@@ -1,0 +1,78 @@
+"""Mixed-precision path (FP32 formal solve, FP64 statistical equilibrium) against the FP64
+oracle. Tolerance 1e-4 relative (the paper's 2|a-b|/(a+b)) on the radiation field from
+identical populations and on converged populations against the oracle's tightly
+converged fixed point."""
+import numpy as np
+import pytest
+
+import synthetic as syn
+from oracle import Oracle
+from helpers import rel_err, gpu_context
+
+pytestmark = pytest.mark.gpu
+TOL_MIX = 1e-4
+
+
+def _case(name):
+    if name == "sphere1d":
+        return syn.model_sphere_1d(n=200, seed=1), None
+    if name == "sphere1d_thick":
+        m = syn.model_sphere_1d(n=120, seed=2)
+        m.n_spec = m.n_spec * 3e3
+        return m, None
+    if name == "tiny":
+        return syn.model_tiny_3d(seed=4, n=20), None
+    if name == "hubble":
+        return syn.hubble_line_1d(n_cells=100, n_q=31), None
+    if name == "clumpy3000":
+        return syn.model_clumpy_3d(n=3000, seed=3), np.sort(np.random.default_rng(1).choice(3000, 150, replace=False))
+    raise KeyError(name)
+
+
+@pytest.mark.parametrize("name", ["sphere1d", "sphere1d_thick", "tiny", "hubble", "clumpy3000"])
+def test_formal_solve_mixed_parity(name):
+    m, origins = _case(name)
+    o = Oracle(m, nthreads=16)
+    ctx = gpu_context(m, oracle_dirs=o.dirs, precision=1, spectrum=1)
+    ctx.trace_rays()
+    ctx.init_populations()
+    ctx.formal_solve()
+    J, L, E = ctx.get_radiation()
+    sel = slice(None) if origins is None else origins
+    Jo, Lo, Eo = o.formal_solve(o.lte(), origins)
+    assert np.max(rel_err(J[sel], Jo)) < TOL_MIX
+    assert np.max(rel_err(E[sel], Eo)) < TOL_MIX
+    # L is a weight in [0, 1]: absolute error against its scale
+    assert np.max(np.abs(L[sel] - Lo)) < TOL_MIX * max(1e-6, float(np.max(np.abs(Lo))))
+
+
+def test_formal_solve_mixed_clumpy_50k_sampled():
+    """The bench workload (50k points, 48 rays, 4 lines x 31 bins) in the bench's launch
+    configuration: sampled origins against the oracle."""
+    m = syn.model_clumpy_3d(n=50_000, seed=0)
+    o = Oracle(m, nthreads=16)
+    ctx = gpu_context(m, precision=1)
+    ctx.trace_rays()
+    ctx.init_populations()
+    ctx.formal_solve()
+    J, L, E = ctx.get_radiation()
+    origins = np.sort(np.random.default_rng(5).choice(m.n, 24, replace=False))
+    Jo, Lo, Eo = o.formal_solve(o.lte(), origins)
+    assert np.max(rel_err(J[origins], Jo)) < TOL_MIX
+    assert np.max(rel_err(E[origins], Eo)) < TOL_MIX
+
+
+@pytest.mark.parametrize("name", ["sphere1d", "sphere1d_thick"])
+def test_mixed_ali_fixed_point(name):
+    """Converged mixed-precision populations against the oracle's fixed point (oracle run
+    to a 1e-11 change with Ng): within 1e-4 relative."""
+    m, _ = _case(name)
+    o = Oracle(m, nthreads=16)
+    ref, ch, conv = o.ali(tol=1e-11, max_iter=600, ng_period=4)
+    assert conv
+    ctx = gpu_context(m, oracle_dirs=o.dirs, precision=1, tol=1e-8, max_iter=600, ng_period=4)
+    ctx.trace_rays()
+    ctx.init_populations()
+    rep, rc = ctx.iterate()
+    assert rep["converged"]
+    assert np.max(rel_err(ctx.get_populations(), ref)) < TOL_MIX
