@@ -167,7 +167,7 @@ __device__ __forceinline__ Side32 sweep32(const MixArgs &a, int l, float aq, flo
         const int k = kstart + step;
         float chi, S;
         point32<OVL>(a, l, aq, A1, k, pt, ln, chi, S, cl, el);
-        const float hds = pt[step > 0 ? k : kstart].x;
+        const float hds = pt[kstart].x;   // interval (kstart, k): stored with the farther point
         const float dt = fmaxf((chi_p + chi) * hds, a.dtau_min);
         Phi = fmaf(0.5f, dt, 1.0f);
         iota = rcpf(fmaf(dt, Phi, 1.0f));
@@ -183,7 +183,7 @@ __device__ __forceinline__ Side32 sweep32(const MixArgs &a, int l, float aq, flo
     for (int k = kstart + 2 * step;; k += step) {
         float chi, S;
         point32<OVL>(a, l, aq, A1, k, pt, ln, chi, S, cl, el);
-        const float hds = pt[step > 0 ? k : k - step].x;
+        const float hds = pt[k - step].x;
         const float dt = fmaxf((chi_p + chi) * hds, a.dtau_min);
         const float t = 0.5f * (dt_p + dt);
         Phi = fmaf(Phi, iota, t);

@@ -64,13 +64,15 @@ def test_formal_solve_mixed_clumpy_50k_sampled():
 
 @pytest.mark.parametrize("name", ["sphere1d", "sphere1d_thick"])
 def test_mixed_ali_fixed_point(name):
-    """Converged mixed-precision populations against the oracle's fixed point (oracle run
-    to a 1e-11 change with Ng): within 1e-4 relative."""
+    """Mixed-precision ALI converged to the method's criterion (max relative change
+    < 1e-6) against the oracle's fixed point (oracle run to a 1e-11 change with Ng):
+    within 1e-4 relative. (The FP32 map's own rounding floor lies near 1e-7, so the
+    mixed path is not asked for a tighter change.)"""
     m, _ = _case(name)
     o = Oracle(m, nthreads=16)
     ref, ch, conv = o.ali(tol=1e-11, max_iter=600, ng_period=4)
     assert conv
-    ctx = gpu_context(m, oracle_dirs=o.dirs, precision=1, tol=1e-8, max_iter=600, ng_period=4)
+    ctx = gpu_context(m, oracle_dirs=o.dirs, precision=1, tol=1e-6, max_iter=600, ng_period=4)
     ctx.trace_rays()
     ctx.init_populations()
     rep, rc = ctx.iterate()
