@@ -182,6 +182,24 @@ int mg_get_spectrum(const mg_ctx *ctx, double *Jnu);
  * Returns MG_WARN_NEG_POP_FALLBACK when some cell fell back. Synchronises. */
 int mg_update_populations(mg_ctx *ctx, double *max_rel_change);
 
+/* Allocation-free variant of mg_update_populations for callers that cannot allocate
+ * device memory when they update populations (an allocator that owns the GPU's memory,
+ * a loop that cannot take the synchronisation an allocation may cause, a fixed memory
+ * budget). The paper has no counterpart: it is an interface addition only.
+ * d_pops_old [n][n_lev] (read) and d_pops_new [n][n_lev] (written) are caller-owned
+ * device buffers on the context's device; the radiation field is the one left by the
+ * last mg_formal_solve (MG_ERR_STATE otherwise). Computes the same statistical
+ * equilibrium, validity fallback and convergence measure as mg_update_populations,
+ * without touching the context's populations. *max_rel_change and *n_fallback (either
+ * may be NULL) receive the convergence measure and the number of fallback cells.
+ * Scratch: a static 512 KiB device array per GPU that loads the library (held until
+ * exit); at most 2,097,152 cells per call (MG_ERR_CAPACITY beyond). The first call on a
+ * device looks up that array's device address; make that first call before any stream
+ * capture. The call allocates nothing and synchronises the context's stream. Calls that
+ * overlap on the GPU (other streams, threads or contexts) race on the shared scratch. */
+int mg_update_populations_noalloc(mg_ctx *ctx, const double *d_pops_old, double *d_pops_new,
+                                  double *max_rel_change, int64_t *n_fallback);
+
 typedef struct {
     int32_t iterations;      /* regular iterations done                            */
     int32_t ng_steps;        /* Ng extrapolations accepted                         */

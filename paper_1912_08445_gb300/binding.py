@@ -74,6 +74,7 @@ _SIGS = {
     "mg_get_radiation_dev": (C.c_int, [_P, _P, _P, _P]),
     "mg_get_spectrum": (C.c_int, [_P, _P]),
     "mg_update_populations": (C.c_int, [_P, _P]),
+    "mg_update_populations_noalloc": (C.c_int, [_P, _P, _P, _P, _P]),
     "mg_iterate": (C.c_int, [_P, _P]),
     "mg_kernel_times": (C.c_int, [_P, C.c_int32, _P, _P, _P, _P]),
     "mg_reset_kernel_times": (C.c_int, [_P]),
@@ -262,6 +263,15 @@ class Context:
         ch = C.c_double(0)
         rc = self._chk(self.lib.mg_update_populations(self.h, C.byref(ch)), "mg_update_populations")
         return ch.value, rc
+
+    def update_populations_noalloc(self, d_old, d_new):
+        """Allocation-free statistical-equilibrium update between caller-owned device
+        buffers (see mg_update_populations_noalloc)."""
+        ch = C.c_double(0); nf = C.c_int64(0)
+        rc = self._chk(self.lib.mg_update_populations_noalloc(self.h, C.c_void_p(d_old), C.c_void_p(d_new),
+                                                              C.byref(ch), C.byref(nf)),
+                       "mg_update_populations_noalloc")
+        return ch.value, nf.value, rc
 
     def iterate(self, allow_not_converged=False):
         rep = mg_ali_report()
