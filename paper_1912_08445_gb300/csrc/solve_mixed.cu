@@ -295,6 +295,234 @@ __global__ void __launch_bounds__(256) k_feautrier_mixed(MixArgs a) {
         for (int f = threadIdx.x; f < L * Q; f += blockDim.x) a.Jnu[o * L * Q + f] = (double)acc[f].x * invP * (double)kI0;
 }
 
+
+// ---------------------------------------------------------------------------------
+// Warp-per-(origin, line) variant for models whose lines do not overlap (the common
+// case): each warp loops over all ray pairs of its origin and sweeps its line's bins,
+// staging the expanded points of the ray pair through a private ring of kRing points in
+// shared memory (one point per lane per refill), so no CTA barrier is ever needed and
+// the pair sums stay in registers in a fixed order. The boundary row is the interior
+// update started from the virtual state (Phi iota = 1, psi = I, dtau = 0), so every
+// point, the origin included, takes the same update.
+constexpr int kRing = 32;
+constexpr int kWarps2 = 4;
+
+struct RingPt {
+    float4 g;   // (ds/2 to the next point towards the origin, v, sqrt(log2 e)/b, X)
+    float S;
+};
+
+// Expanded point x (0 = nearest the origin) of half-ray [off, off + len): element e is
+// found by walking down from the anchor element that contains the chunk's first point.
+__device__ __forceinline__ void stage_ring_point(const MixArgs &a, int64_t o, int l, int64_t off, int x, int &e,
+                                                 float4 &g, float &S) {
+    while (e > 0 && a.xcum[off + e - 1] > x) e--;
+    const int x0 = e ? a.xcum[off + e - 1] : 0;
+    const int ns = a.xcum[off + e] - x0 - 1;
+    const float w = (float)(x - x0 + 1) / (float)(ns + 1);
+    const int64_t c = a.cells[off + e];
+    const int64_t prev = e ? a.cells[off + e - 1] : o;
+    const float pv = e ? a.vpar[off + e - 1] : 0.0f;
+    const float v = (1.0f - w) * pv + w * a.vpar[off + e];
+    const float hds = 0.5f * a.ds[off + e] / (float)(ns + 1);
+    const float bb = (1.0f - w) * a.b[prev] + w * a.b[c];
+    const float ib = 1.0f / bb;
+    const float2 p0 = reinterpret_cast<const float2 *>(a.line)[prev * a.L + l];
+    const float2 p1 = reinterpret_cast<const float2 *>(a.line)[c * a.L + l];
+    const float et = (1.0f - w) * p0.x + w * p1.x;
+    const float ch = (1.0f - w) * p0.y + w * p1.y;
+    g = make_float4(hds, v, kSqrtLog2e * ib, ch * a.kline[l] * ib);
+    S = ch > 0.0f ? et / ch : 0.0f;
+}
+
+template <int NB>
+struct BinState {
+    float aq[NB], A1[NB];
+    float chi_p[NB], S_p[NB], dt_p[NB], Phi[NB], iota[NB], psi[NB];
+};
+
+template <int NB>
+__device__ __forceinline__ void first_point(const MixArgs &a, BinState<NB> &st, const float4 g, const float S,
+                                            const float nu_g) {
+#pragma unroll
+    for (int i = 0; i < NB; i++) {
+        const float x = fmaf(-g.y, st.A1[i], st.aq[i]) * g.z;
+        const float chil = g.w * ex2f(-x * x);
+        const bool fl = chil < a.chi_min;
+        st.chi_p[i] = fl ? a.chi_min : chil;
+        st.S_p[i] = fl ? chil * S * a.inv_chi_min : S;
+        st.Phi[i] = 1.0f;
+        st.iota[i] = 1.0f;
+        st.dt_p[i] = 0.0f;
+        st.psi[i] = planck_f(a, nu_g * st.A1[i] * (1.0f - g.y * (float)(1.0 / kC)));
+    }
+}
+
+// Update with the interval (previous point, this point) of half length hds_p.
+template <int NB>
+__device__ __forceinline__ void step_point(const MixArgs &a, BinState<NB> &st, const float4 g, const float S,
+                                           const float hds_p) {
+#pragma unroll
+    for (int i = 0; i < NB; i++) {
+        const float x = fmaf(-g.y, st.A1[i], st.aq[i]) * g.z;
+        const float chil = g.w * ex2f(-x * x);
+        const bool fl = chil < a.chi_min;
+        const float chi = fl ? a.chi_min : chil;
+        const float Sx = fl ? chil * S * a.inv_chi_min : S;
+        const float dt = fmaxf((st.chi_p[i] + chi) * hds_p, a.dtau_min);
+        const float t = 0.5f * (st.dt_p[i] + dt);
+        st.Phi[i] = fmaf(st.Phi[i], st.iota[i], t);
+        st.iota[i] = rcpf(fmaf(dt, st.Phi[i], 1.0f));
+        st.psi[i] = fmaf(t, st.S_p[i], st.psi[i]) * st.iota[i];
+        st.dt_p[i] = dt;
+        st.chi_p[i] = chi;
+        st.S_p[i] = Sx;
+    }
+}
+
+// Sweeps half-ray r from its far end to the origin; returns per bin (Phi iota, psi, dtau)
+// of the row next to the origin, or the empty-half values when the half has no point.
+template <int NB>
+__device__ __forceinline__ void sweep_half(const MixArgs &a, int64_t o, int l, int r, float nu_g, const float4 go,
+                                           const float So, RingPt *ring, BinState<NB> &st, float (&pi)[NB],
+                                           float (&ps)[NB], float (&dt)[NB]) {
+    const int lane = threadIdx.x & 31;
+    const int64_t off = a.ray_off[o * a.R + r];
+    const int len = (int)(a.ray_off[o * a.R + r + 1] - off);
+    const int Kh = len ? a.xcum[off + len - 1] : 0;
+    if (Kh == 0) {
+#pragma unroll
+        for (int i = 0; i < NB; i++) {
+            pi[i] = 1.0f;
+            ps[i] = planck_f(a, nu_g * st.A1[i]);
+            dt[i] = 0.0f;
+        }
+        return;
+    }
+    int anchor = len - 1;      // element holding the next point to stage
+    int xnext = Kh - 1;        // next point to stage (descending towards the origin)
+    float hds_p = 0.0f;
+    bool first = true;
+    while (xnext >= 0) {
+        const int cnt = min(kRing, xnext + 1);
+        __syncwarp();
+        int e = anchor;
+        if (lane < cnt) {
+            float4 g; float S;
+            stage_ring_point(a, o, l, off, xnext - lane, e, g, S);
+            ring[lane].g = g;
+            ring[lane].S = S;
+        }
+        anchor = __shfl_sync(0xffffffffu, e, cnt - 1);
+        __syncwarp();
+        int j = 0;
+        if (first) {
+            const float4 g = ring[0].g;
+            first_point<NB>(a, st, g, ring[0].S, nu_g);
+            hds_p = g.x;
+            j = 1;
+            first = false;
+        }
+        for (; j < cnt; j++) {
+            const float4 g = ring[j].g;
+            step_point<NB>(a, st, g, ring[j].S, hds_p);
+            hds_p = g.x;
+        }
+        xnext -= cnt;
+    }
+    step_point<NB>(a, st, go, So, hds_p);   // the origin
+#pragma unroll
+    for (int i = 0; i < NB; i++) {
+        pi[i] = st.Phi[i] * st.iota[i];
+        ps[i] = st.psi[i];
+        dt[i] = st.dt_p[i];
+    }
+}
+
+template <int NB>
+__global__ void __launch_bounds__(32 * kWarps2, NB == 1 ? 8 : 6) k_feautrier_warp(MixArgs a) {
+    __shared__ RingPt rings[kWarps2][kRing];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t item = (int64_t)blockIdx.x * kWarps2 + warp;
+    if (item >= a.n * a.L) return;
+    const int64_t o = item / a.L;
+    const int l = (int)(item - o * a.L);
+    RingPt *ring = rings[warp];
+    const int Q = a.Q;
+    const float bo = a.b[o];
+    const float ibo = 1.0f / bo;
+    const float2 dlo = reinterpret_cast<const float2 *>(a.line)[o * a.L + l];
+    const float4 go = make_float4(0.0f, 0.0f, kSqrtLog2e * ibo, dlo.y * a.kline[l] * ibo);
+    const float So = dlo.y > 0.0f ? dlo.x / dlo.y : 0.0f;
+    const float nu_g = a.nu_ghz[l];
+    BinState<NB> st;
+    float acc[NB][4];
+#pragma unroll
+    for (int i = 0; i < NB; i++) {
+        const int q = lane + 32 * i;
+        st.aq[i] = q < Q ? (float)(a.roots[q] * (double)bo) : 0.0f;
+        st.A1[i] = 1.0f + st.aq[i] * (float)(1.0 / kC);
+        acc[i][0] = acc[i][1] = acc[i][2] = acc[i][3] = 0.0f;
+    }
+    // the origin's own opacity per bin (v = 0 there)
+    float chio[NB], Sov[NB], chilo[NB];
+#pragma unroll
+    for (int i = 0; i < NB; i++) {
+        const float x = st.aq[i] * go.z;
+        const float chil = go.w * ex2f(-x * x);
+        const bool fl = chil < a.chi_min;
+        chilo[i] = chil;
+        chio[i] = fl ? a.chi_min : chil;
+        Sov[i] = fl ? chil * So * a.inv_chi_min : So;
+    }
+    for (int p = 0; p < a.P; p++) {
+        float pib[NB], psb[NB], dtb[NB], pif[NB], psf[NB], dtf[NB];
+        sweep_half<NB>(a, o, l, a.pb[p], nu_g, go, So, ring, st, pib, psb, dtb);
+        sweep_half<NB>(a, o, l, a.pf[p], nu_g, go, So, ring, st, pif, psf, dtf);
+#pragma unroll
+        for (int i = 0; i < NB; i++) {
+            float u, lam, uml, oml;
+            if (dtb[i] == 0.0f && dtf[i] == 0.0f) {   // isolated origin: both halves empty
+                u = psb[i]; lam = 0.0f; uml = psb[i]; oml = 1.0f;
+            } else {
+                const float sig = 2.0f / (dtb[i] + dtf[i]);
+                const float pi2 = pib[i] + pif[i];
+                const float iD = 1.0f / fmaf(sig, pi2, 1.0f);
+                const float s2 = sig * (psb[i] + psf[i]);
+                u = (Sov[i] + s2) * iD;
+                lam = iD;
+                uml = s2 * iD;
+                oml = sig * pi2 * iD;
+            }
+            const float ichi = 1.0f / chio[i];
+            acc[i][0] += u;
+            acc[i][1] += lam * chilo[i] * ichi;
+            acc[i][2] += uml + lam * (Sov[i] * chio[i] - chilo[i] * So) * ichi;
+            acc[i][3] += oml + lam * (chio[i] - chilo[i]) * ichi;
+        }
+    }
+    // weighted sums over bins: fixed shuffle tree in FP64
+    const double invP = 1.0 / a.P;
+    double s[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+    for (int i = 0; i < NB; i++) {
+        const int q = lane + 32 * i;
+        const double w = q < Q ? a.weights[q] : 0.0;
+#pragma unroll
+        for (int k = 0; k < 4; k++) s[k] += w * (double)acc[i][k];
+        if (a.Jnu && q < Q) a.Jnu[(o * a.L + l) * Q + q] = (double)acc[i][0] * invP * (double)kI0;
+    }
+#pragma unroll
+    for (int k = 0; k < 4; k++)
+        for (int d = 16; d; d >>= 1) s[k] += __shfl_down_sync(0xffffffffu, s[k], d);
+    if (lane == 0) {
+        a.J[o * a.L + l] = s[0] * invP * (double)kI0;
+        a.Lout[o * a.L + l] = s[1] * invP;
+        a.Jeff[o * a.L + l] = s[2] * invP * (double)kI0;
+        a.Lc[o * a.L + l] = s[3] * invP;
+    }
+}
+
 }  // namespace
 
 int mg_launch_line_data_mixed(mg_ctx *ctx) {
@@ -327,7 +555,7 @@ int mg_launch_feautrier_mixed(mg_ctx *ctx) {
     a.overlap = overlap;
     a.err = ctx->d_err;
     size_t smem = (size_t)a.kmax * (16 + 8 * (size_t)L) + 16 * (size_t)L * Q;
-    if (smem > 227 * 1024) {
+    if ((overlap || Q > 64) && smem > 227 * 1024) {
         return mg_fail(ctx, MG_ERR_CAPACITY, "mixed formal solve: longest ray pair does not fit in shared memory");
     }
     int threads = 32 * std::min(L, 8);
@@ -336,6 +564,12 @@ int mg_launch_feautrier_mixed(mg_ctx *ctx) {
         MG_CUDA(cudaFuncSetAttribute(k_feautrier_mixed<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         MgTimed t(ctx, "feautrier_mixed");
         k_feautrier_mixed<true><<<(unsigned)ctx->n, threads, smem, ctx->stream>>>(a);
+    } else if (Q <= 32 || Q <= 64) {
+        const int64_t items = ctx->n * L;
+        const unsigned grid = (unsigned)((items + kWarps2 - 1) / kWarps2);
+        MgTimed t(ctx, "feautrier_mixed");
+        if (Q <= 32) k_feautrier_warp<1><<<grid, 32 * kWarps2, 0, ctx->stream>>>(a);
+        else k_feautrier_warp<2><<<grid, 32 * kWarps2, 0, ctx->stream>>>(a);
     } else {
         MG_CUDA(cudaFuncSetAttribute(k_feautrier_mixed<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         MgTimed t(ctx, "feautrier_mixed");
