@@ -155,6 +155,7 @@ def run_gpu(args):
     ctx.load_model(model)
     st, _ = ctx.trace_rays()
     ctx.init_populations()
+    tuned = ctx.autotune(reps=2) if prec == mg.MG_MIXED else (-1, None, 0)
     solves, updates = ctx.work_counts()
     n, lev = model.n, model.species.n_lev
 
@@ -187,6 +188,7 @@ def run_gpu(args):
         ctx.load_model(model)
         ctx.trace_rays()
         ctx.init_populations()
+        ctx.set_variant(tuned[0])
         step()
         ctx.reset_kernel_times()
         for _ in range(max(2, min(args.steps, 5))):
@@ -245,7 +247,8 @@ def run_gpu(args):
             "config": dict(WORKLOAD, precision=args.precision, l2="inputs larger than L2 (ray store "
                            f"{st['n_elements'] * 24 / 1e9:.2f} GB read per step)",
                            parallelism=f"replicas x{ws}", solves_per_step=solves,
-                           cell_freq_updates_per_step=updates, mean_pair_len=round(st["mean_pair_len"], 1)),
+                           cell_freq_updates_per_step=updates, mean_pair_len=round(st["mean_pair_len"], 1),
+                           launch_variant=tuned[0], variants_tried=tuned[2]),
             "e2e": {"value": ws * solves * args.steps / (e2e_ms_max * 1e-3), "unit": UNIT,
                     "h2d_bytes_per_step": n * lev * 8, "d2h_bytes_per_step": n * lev * 8},
             "gpu_launches": 3 * args.steps,

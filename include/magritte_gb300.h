@@ -216,6 +216,16 @@ typedef struct {
  * Returns MG_ERR_NOT_CONVERGED when the cap is reached (populations are kept). */
 int mg_iterate(mg_ctx *ctx, mg_ali_report *rep);
 
+/* Autotuner of the mixed-precision formal solve: times every launch variant of the
+ * Feautrier kernel that suits the model (lines per warp, bins per lane, blocks per SM;
+ * CUDA events, best of reps launches after one warm-up) on the current populations,
+ * keeps the fastest for later solves and reports it. Leaves a valid radiation field.
+ * Requires precision MG_MIXED, traced rays, quadrature and populations. */
+int mg_autotune(mg_ctx *ctx, int32_t reps, int32_t *variant, double *ms, int32_t *n_tried);
+/* Selects a launch variant by index (-1: the model's default). Invalid indices fall back
+ * to the default at launch. */
+int mg_set_variant(mg_ctx *ctx, int32_t variant);
+
 /* Kernel timing (opt.profile = 1): total milliseconds and launch counts per kernel
  * since the last reset, for up to cap kernels; names[i] points to static strings. */
 int mg_kernel_times(const mg_ctx *ctx, int32_t cap, const char **names, double *ms,

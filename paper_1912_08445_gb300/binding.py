@@ -79,6 +79,8 @@ _SIGS = {
     "mg_kernel_times": (C.c_int, [_P, C.c_int32, _P, _P, _P, _P]),
     "mg_reset_kernel_times": (C.c_int, [_P]),
     "mg_work_counts": (C.c_int, [_P, _P, _P]),
+    "mg_autotune": (C.c_int, [_P, C.c_int32, _P, _P, _P]),
+    "mg_set_variant": (C.c_int, [_P, C.c_int32]),
 }
 
 _LIB = None
@@ -288,6 +290,14 @@ class Context:
 
     def reset_kernel_times(self):
         self._chk(self.lib.mg_reset_kernel_times(self.h), "mg_reset_kernel_times")
+
+    def autotune(self, reps=2):
+        v = C.c_int32(0); ms = C.c_double(0); nt = C.c_int32(0)
+        self._chk(self.lib.mg_autotune(self.h, int(reps), C.byref(v), C.byref(ms), C.byref(nt)), "mg_autotune")
+        return v.value, ms.value, nt.value
+
+    def set_variant(self, v):
+        self._chk(self.lib.mg_set_variant(self.h, int(v)), "mg_set_variant")
 
     def work_counts(self):
         s = C.c_int64(0); u = C.c_int64(0)

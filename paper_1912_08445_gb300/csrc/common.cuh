@@ -133,6 +133,9 @@ struct mg_ctx {
     unsigned long long *h_scal = nullptr;   // pinned
     int32_t *d_err = nullptr;               // kernel error word
 
+    // ---- launch variant of the mixed formal solve (-1: default for the model)
+    int mixed_variant = -1;
+
     // ---- profiling
     std::vector<mg::KernelTimer> timers;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -177,6 +180,7 @@ int mg_launch_trace(mg_ctx *ctx);
 int mg_launch_line_data(mg_ctx *ctx);
 int mg_launch_line_data_mixed(mg_ctx *ctx);
 int mg_launch_feautrier(mg_ctx *ctx);
+int mg_autotune_mixed(mg_ctx *ctx, int reps, int *best, double *best_ms, int *n_tried);
 int mg_launch_lte(mg_ctx *ctx);
 int mg_launch_collision_rates(mg_ctx *ctx);
 int mg_launch_stateq(mg_ctx *ctx);

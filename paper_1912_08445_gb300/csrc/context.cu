@@ -756,6 +756,33 @@ extern "C" int mg_iterate(mg_ctx *ctx, mg_ali_report *rep) {
     return r.converged ? MG_OK : mg_fail(ctx, MG_ERR_NOT_CONVERGED, "ALI did not reach the tolerance");
 }
 
+// ------------------------------------------------------------------ autotuning
+extern "C" int mg_autotune(mg_ctx *ctx, int32_t reps, int32_t *variant, double *ms, int32_t *n_tried) {
+    if (!ctx) return MG_ERR_ARG;
+    int rc;
+    if ((rc = check_solve_ready(ctx))) return rc;
+    if (ctx->opt.precision != MG_MIXED) return mg_fail(ctx, MG_ERR_STATE, "mg_autotune: only the mixed path has variants");
+    cudaSetDevice(ctx->device);
+    if ((rc = ensure_state(ctx))) return rc;
+    if (ctx->h_ovl_off.size() != (size_t)ctx->n_lines + 1)
+        if ((rc = upload_overlaps(ctx))) return rc;
+    if ((rc = mg_launch_line_data(ctx))) return rc;
+    int b = -1, nt = 0;
+    double bms = 0;
+    if ((rc = mg_autotune_mixed(ctx, reps < 1 ? 1 : reps, &b, &bms, &nt))) return rc;
+    if (variant) *variant = b;
+    if (ms) *ms = bms;
+    if (n_tried) *n_tried = nt;
+    ctx->have_rad = true;
+    return MG_OK;
+}
+
+extern "C" int mg_set_variant(mg_ctx *ctx, int32_t variant) {
+    if (!ctx) return MG_ERR_ARG;
+    ctx->mixed_variant = variant;
+    return MG_OK;
+}
+
 // ------------------------------------------------------------------ timing and counts
 extern "C" int mg_kernel_times(const mg_ctx *ctx, int32_t cap, const char **names, double *ms,
                                int64_t *launches, int32_t *count) {

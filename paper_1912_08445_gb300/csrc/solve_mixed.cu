@@ -297,25 +297,25 @@ __global__ void __launch_bounds__(256) k_feautrier_mixed(MixArgs a) {
 
 
 // ---------------------------------------------------------------------------------
-// Warp-per-(origin, line) variant for models whose lines do not overlap (the common
-// case): each warp loops over all ray pairs of its origin and sweeps its line's bins,
-// staging the expanded points of the ray pair through a private ring of kRing points in
-// shared memory (one point per lane per refill), so no CTA barrier is ever needed and
-// the pair sums stay in registers in a fixed order. The boundary row is the interior
-// update started from the virtual state (Phi iota = 1, psi = I, dtau = 0), so every
-// point, the origin included, takes the same update.
+// Warp-per-(origin, line group) variant for models whose lines do not overlap (the
+// common case). A warp serves G lines (G lane groups of 32/G lanes) and every lane NB
+// bins of its line, so each shared-memory read and loop step is shared by NB updates.
+// The warp loops over all ray pairs of its origin and stages the expanded points through
+// a private ring of kRing points (one point per lane per refill): no CTA barrier is ever
+// needed and the pair sums stay in registers in a fixed order. The boundary row is the
+// interior update started from the virtual state (Phi iota = 1, psi = I, dtau = 0).
+// The opacity floor costs three instructions: chi = max(chi_l, chi_min) and
+// S = min(S_l, chi_l S_l / chi_min), which is eta/chi with chi floored.
 constexpr int kRing = 32;
 constexpr int kWarps2 = 4;
 
-struct RingPt {
-    float4 g;   // (ds/2 to the next point towards the origin, v, sqrt(log2 e)/b, X)
-    float S;
+struct RingGeom {
+    float4 g;   // (ds/2 to the next point towards the origin, v, sqrt(log2 e)/b, unused)
 };
 
-// Expanded point x (0 = nearest the origin) of half-ray [off, off + len): element e is
-// found by walking down from the anchor element that contains the chunk's first point.
-__device__ __forceinline__ void stage_ring_point(const MixArgs &a, int64_t o, int l, int64_t off, int x, int &e,
-                                                 float4 &g, float &S) {
+template <int G>
+__device__ __forceinline__ void stage_ring_point(const MixArgs &a, int64_t o, int l0, int64_t off, int x, int &e,
+                                                 float4 &g, float2 (&ln)[G]) {
     while (e > 0 && a.xcum[off + e - 1] > x) e--;
     const int x0 = e ? a.xcum[off + e - 1] : 0;
     const int ns = a.xcum[off + e] - x0 - 1;
@@ -327,12 +327,16 @@ __device__ __forceinline__ void stage_ring_point(const MixArgs &a, int64_t o, in
     const float hds = 0.5f * a.ds[off + e] / (float)(ns + 1);
     const float bb = (1.0f - w) * a.b[prev] + w * a.b[c];
     const float ib = 1.0f / bb;
-    const float2 p0 = reinterpret_cast<const float2 *>(a.line)[prev * a.L + l];
-    const float2 p1 = reinterpret_cast<const float2 *>(a.line)[c * a.L + l];
-    const float et = (1.0f - w) * p0.x + w * p1.x;
-    const float ch = (1.0f - w) * p0.y + w * p1.y;
-    g = make_float4(hds, v, kSqrtLog2e * ib, ch * a.kline[l] * ib);
-    S = ch > 0.0f ? et / ch : 0.0f;
+    g = make_float4(hds, v, kSqrtLog2e * ib, 0.0f);
+#pragma unroll
+    for (int k = 0; k < G; k++) {
+        const int l = l0 + k < a.L ? l0 + k : a.L - 1;
+        const float2 p0 = reinterpret_cast<const float2 *>(a.line)[prev * a.L + l];
+        const float2 p1 = reinterpret_cast<const float2 *>(a.line)[c * a.L + l];
+        const float et = (1.0f - w) * p0.x + w * p1.x;
+        const float ch = (1.0f - w) * p0.y + w * p1.y;
+        ln[k] = make_float2(fmaxf(ch, 0.0f) * a.kline[l] * ib, ch > 0.0f ? et / ch : 0.0f);
+    }
 }
 
 template <int NB>
@@ -342,15 +346,15 @@ struct BinState {
 };
 
 template <int NB>
-__device__ __forceinline__ void first_point(const MixArgs &a, BinState<NB> &st, const float4 g, const float S,
+__device__ __forceinline__ void first_point(const MixArgs &a, BinState<NB> &st, const float4 g, const float2 d,
                                             const float nu_g) {
+    const float SI = d.y * a.inv_chi_min;
 #pragma unroll
     for (int i = 0; i < NB; i++) {
         const float x = fmaf(-g.y, st.A1[i], st.aq[i]) * g.z;
-        const float chil = g.w * ex2f(-x * x);
-        const bool fl = chil < a.chi_min;
-        st.chi_p[i] = fl ? a.chi_min : chil;
-        st.S_p[i] = fl ? chil * S * a.inv_chi_min : S;
+        const float chil = d.x * ex2f(-x * x);
+        st.chi_p[i] = fmaxf(chil, a.chi_min);
+        st.S_p[i] = fminf(d.y, chil * SI);
         st.Phi[i] = 1.0f;
         st.iota[i] = 1.0f;
         st.dt_p[i] = 0.0f;
@@ -360,15 +364,15 @@ __device__ __forceinline__ void first_point(const MixArgs &a, BinState<NB> &st, 
 
 // Update with the interval (previous point, this point) of half length hds_p.
 template <int NB>
-__device__ __forceinline__ void step_point(const MixArgs &a, BinState<NB> &st, const float4 g, const float S,
+__device__ __forceinline__ void step_point(const MixArgs &a, BinState<NB> &st, const float4 g, const float2 d,
                                            const float hds_p) {
+    const float SI = d.y * a.inv_chi_min;
 #pragma unroll
     for (int i = 0; i < NB; i++) {
         const float x = fmaf(-g.y, st.A1[i], st.aq[i]) * g.z;
-        const float chil = g.w * ex2f(-x * x);
-        const bool fl = chil < a.chi_min;
-        const float chi = fl ? a.chi_min : chil;
-        const float Sx = fl ? chil * S * a.inv_chi_min : S;
+        const float chil = d.x * ex2f(-x * x);
+        const float chi = fmaxf(chil, a.chi_min);
+        const float Sx = fminf(d.y, chil * SI);
         const float dt = fmaxf((st.chi_p[i] + chi) * hds_p, a.dtau_min);
         const float t = 0.5f * (st.dt_p[i] + dt);
         st.Phi[i] = fmaf(st.Phi[i], st.iota[i], t);
@@ -382,10 +386,10 @@ __device__ __forceinline__ void step_point(const MixArgs &a, BinState<NB> &st, c
 
 // Sweeps half-ray r from its far end to the origin; returns per bin (Phi iota, psi, dtau)
 // of the row next to the origin, or the empty-half values when the half has no point.
-template <int NB>
-__device__ __forceinline__ void sweep_half(const MixArgs &a, int64_t o, int l, int r, float nu_g, const float4 go,
-                                           const float So, RingPt *ring, BinState<NB> &st, float (&pi)[NB],
-                                           float (&ps)[NB], float (&dt)[NB]) {
+template <int G, int NB>
+__device__ __forceinline__ void sweep_half(const MixArgs &a, int64_t o, int l0, int grp, int r, float nu_g,
+                                           const float4 go, const float2 dlo, RingGeom *rg, float2 *rl,
+                                           BinState<NB> &st, float (&pi)[NB], float (&ps)[NB], float (&dt)[NB]) {
     const int lane = threadIdx.x & 31;
     const int64_t off = a.ray_off[o * a.R + r];
     const int len = (int)(a.ray_off[o * a.R + r + 1] - off);
@@ -399,6 +403,7 @@ __device__ __forceinline__ void sweep_half(const MixArgs &a, int64_t o, int l, i
         }
         return;
     }
+    const float2 *my = rl + grp * kRing;
     int anchor = len - 1;      // element holding the next point to stage
     int xnext = Kh - 1;        // next point to stage (descending towards the origin)
     float hds_p = 0.0f;
@@ -408,29 +413,31 @@ __device__ __forceinline__ void sweep_half(const MixArgs &a, int64_t o, int l, i
         __syncwarp();
         int e = anchor;
         if (lane < cnt) {
-            float4 g; float S;
-            stage_ring_point(a, o, l, off, xnext - lane, e, g, S);
-            ring[lane].g = g;
-            ring[lane].S = S;
+            float4 g;
+            float2 ln[G];
+            stage_ring_point<G>(a, o, l0, off, xnext - lane, e, g, ln);
+            rg[lane].g = g;
+#pragma unroll
+            for (int k = 0; k < G; k++) rl[k * kRing + lane] = ln[k];
         }
         anchor = __shfl_sync(0xffffffffu, e, cnt - 1);
         __syncwarp();
         int j = 0;
         if (first) {
-            const float4 g = ring[0].g;
-            first_point<NB>(a, st, g, ring[0].S, nu_g);
+            const float4 g = rg[0].g;
+            first_point<NB>(a, st, g, my[0], nu_g);
             hds_p = g.x;
             j = 1;
             first = false;
         }
         for (; j < cnt; j++) {
-            const float4 g = ring[j].g;
-            step_point<NB>(a, st, g, ring[j].S, hds_p);
+            const float4 g = rg[j].g;
+            step_point<NB>(a, st, g, my[j], hds_p);
             hds_p = g.x;
         }
         xnext -= cnt;
     }
-    step_point<NB>(a, st, go, So, hds_p);   // the origin
+    step_point<NB>(a, st, go, dlo, hds_p);   // the origin
 #pragma unroll
     for (int i = 0; i < NB; i++) {
         pi[i] = st.Phi[i] * st.iota[i];
@@ -439,46 +446,49 @@ __device__ __forceinline__ void sweep_half(const MixArgs &a, int64_t o, int l, i
     }
 }
 
-template <int NB>
-__global__ void __launch_bounds__(32 * kWarps2, NB == 1 ? 8 : 6) k_feautrier_warp(MixArgs a) {
-    __shared__ RingPt rings[kWarps2][kRing];
+template <int G, int NB, int MINB>
+__global__ void __launch_bounds__(32 * kWarps2, MINB) k_feautrier_warp(MixArgs a) {
+    __shared__ RingGeom rgs[kWarps2][kRing];
+    __shared__ float2 rls[kWarps2][G * kRing];
+    constexpr int LPG = 32 / G;   // lanes per line
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int ngroups = (a.L + G - 1) / G;
     const int64_t item = (int64_t)blockIdx.x * kWarps2 + warp;
-    if (item >= a.n * a.L) return;
-    const int64_t o = item / a.L;
-    const int l = (int)(item - o * a.L);
-    RingPt *ring = rings[warp];
+    if (item >= a.n * ngroups) return;
+    const int64_t o = item / ngroups;
+    const int l0 = (int)(item - o * ngroups) * G;
+    const int grp = lane / LPG, li = lane - grp * LPG;
+    const int l = l0 + grp;
+    const bool line_ok = l < a.L;
+    const int lc = line_ok ? l : a.L - 1;
     const int Q = a.Q;
     const float bo = a.b[o];
     const float ibo = 1.0f / bo;
-    const float2 dlo = reinterpret_cast<const float2 *>(a.line)[o * a.L + l];
-    const float4 go = make_float4(0.0f, 0.0f, kSqrtLog2e * ibo, dlo.y * a.kline[l] * ibo);
-    const float So = dlo.y > 0.0f ? dlo.x / dlo.y : 0.0f;
-    const float nu_g = a.nu_ghz[l];
+    const float2 dl = reinterpret_cast<const float2 *>(a.line)[o * a.L + lc];
+    const float4 go = make_float4(0.0f, 0.0f, kSqrtLog2e * ibo, 0.0f);
+    const float2 dlo = make_float2(fmaxf(dl.y, 0.0f) * a.kline[lc] * ibo, dl.y > 0.0f ? dl.x / dl.y : 0.0f);
+    const float nu_g = a.nu_ghz[lc];
     BinState<NB> st;
     float acc[NB][4];
-#pragma unroll
-    for (int i = 0; i < NB; i++) {
-        const int q = lane + 32 * i;
-        st.aq[i] = q < Q ? (float)(a.roots[q] * (double)bo) : 0.0f;
-        st.A1[i] = 1.0f + st.aq[i] * (float)(1.0 / kC);
-        acc[i][0] = acc[i][1] = acc[i][2] = acc[i][3] = 0.0f;
-    }
-    // the origin's own opacity per bin (v = 0 there)
     float chio[NB], Sov[NB], chilo[NB];
 #pragma unroll
     for (int i = 0; i < NB; i++) {
+        const int q = li + LPG * i;
+        st.aq[i] = q < Q ? (float)(a.roots[q] * (double)bo) : 0.0f;
+        st.A1[i] = 1.0f + st.aq[i] * (float)(1.0 / kC);
+        acc[i][0] = acc[i][1] = acc[i][2] = acc[i][3] = 0.0f;
         const float x = st.aq[i] * go.z;
-        const float chil = go.w * ex2f(-x * x);
-        const bool fl = chil < a.chi_min;
+        const float chil = dlo.x * ex2f(-x * x);
         chilo[i] = chil;
-        chio[i] = fl ? a.chi_min : chil;
-        Sov[i] = fl ? chil * So * a.inv_chi_min : So;
+        chio[i] = fmaxf(chil, a.chi_min);
+        Sov[i] = fminf(dlo.y, chil * dlo.y * a.inv_chi_min);
     }
+    RingGeom *rg = rgs[warp];
+    float2 *rl = rls[warp];
     for (int p = 0; p < a.P; p++) {
         float pib[NB], psb[NB], dtb[NB], pif[NB], psf[NB], dtf[NB];
-        sweep_half<NB>(a, o, l, a.pb[p], nu_g, go, So, ring, st, pib, psb, dtb);
-        sweep_half<NB>(a, o, l, a.pf[p], nu_g, go, So, ring, st, pif, psf, dtf);
+        sweep_half<G, NB>(a, o, l0, grp, a.pb[p], nu_g, go, dlo, rg, rl, st, pib, psb, dtb);
+        sweep_half<G, NB>(a, o, l0, grp, a.pf[p], nu_g, go, dlo, rg, rl, st, pif, psf, dtf);
 #pragma unroll
         for (int i = 0; i < NB; i++) {
             float u, lam, uml, oml;
@@ -497,30 +507,52 @@ __global__ void __launch_bounds__(32 * kWarps2, NB == 1 ? 8 : 6) k_feautrier_war
             const float ichi = 1.0f / chio[i];
             acc[i][0] += u;
             acc[i][1] += lam * chilo[i] * ichi;
-            acc[i][2] += uml + lam * (Sov[i] * chio[i] - chilo[i] * So) * ichi;
+            acc[i][2] += uml + lam * (Sov[i] * chio[i] - chilo[i] * dlo.y) * ichi;
             acc[i][3] += oml + lam * (chio[i] - chilo[i]) * ichi;
         }
     }
-    // weighted sums over bins: fixed shuffle tree in FP64
+    // weighted sums over each line's bins: fixed shuffle tree in FP64 within the lane group
     const double invP = 1.0 / a.P;
     double s[4] = {0.0, 0.0, 0.0, 0.0};
 #pragma unroll
     for (int i = 0; i < NB; i++) {
-        const int q = lane + 32 * i;
+        const int q = li + LPG * i;
         const double w = q < Q ? a.weights[q] : 0.0;
 #pragma unroll
         for (int k = 0; k < 4; k++) s[k] += w * (double)acc[i][k];
-        if (a.Jnu && q < Q) a.Jnu[(o * a.L + l) * Q + q] = (double)acc[i][0] * invP * (double)kI0;
+        if (a.Jnu && q < Q && line_ok) a.Jnu[(o * a.L + l) * Q + q] = (double)acc[i][0] * invP * (double)kI0;
     }
 #pragma unroll
     for (int k = 0; k < 4; k++)
-        for (int d = 16; d; d >>= 1) s[k] += __shfl_down_sync(0xffffffffu, s[k], d);
-    if (lane == 0) {
+        for (int d = LPG / 2; d; d >>= 1) s[k] += __shfl_down_sync(0xffffffffu, s[k], d);
+    if (li == 0 && line_ok) {
         a.J[o * a.L + l] = s[0] * invP * (double)kI0;
         a.Lout[o * a.L + l] = s[1] * invP;
         a.Jeff[o * a.L + l] = s[2] * invP * (double)kI0;
         a.Lc[o * a.L + l] = s[3] * invP;
     }
+}
+
+
+// Launch variants of the warp kernel: (lines per warp, bins per lane, min blocks per SM).
+struct WarpVariant {
+    int G, NB, MINB;
+    void (*fn)(MixArgs);
+};
+const WarpVariant kWarpVariants[] = {
+    {1, 1, 8, k_feautrier_warp<1, 1, 8>}, {1, 1, 10, k_feautrier_warp<1, 1, 10>},
+    {2, 2, 4, k_feautrier_warp<2, 2, 4>}, {2, 2, 5, k_feautrier_warp<2, 2, 5>},
+    {2, 2, 6, k_feautrier_warp<2, 2, 6>}, {1, 2, 4, k_feautrier_warp<1, 2, 4>},
+    {1, 2, 6, k_feautrier_warp<1, 2, 6>}, {1, 4, 3, k_feautrier_warp<1, 4, 3>},
+    {1, 4, 4, k_feautrier_warp<1, 4, 4>},
+};
+constexpr int kNumWarpVariants = sizeof(kWarpVariants) / sizeof(kWarpVariants[0]);
+
+bool variant_valid(int v, int L, int Q) {
+    if (v < 0 || v >= kNumWarpVariants) return false;
+    const WarpVariant &w = kWarpVariants[v];
+    if (w.G == 2 && L < 2) return false;
+    return Q <= w.NB * (32 / w.G) && Q > (w.NB == 1 ? 0 : (w.NB / 2) * (32 / w.G));
 }
 
 }  // namespace
@@ -535,7 +567,7 @@ int mg_launch_line_data_mixed(mg_ctx *ctx) {
     return MG_OK;
 }
 
-int mg_launch_feautrier_mixed(mg_ctx *ctx) {
+static int launch_mixed(mg_ctx *ctx, int variant) {
     const int L = ctx->n_lines, Q = ctx->Q;
     bool overlap = false;
     for (int l = 0; l < L; l++) overlap |= (ctx->h_ovl_off[l + 1] - ctx->h_ovl_off[l]) > 1;
@@ -555,26 +587,79 @@ int mg_launch_feautrier_mixed(mg_ctx *ctx) {
     a.overlap = overlap;
     a.err = ctx->d_err;
     size_t smem = (size_t)a.kmax * (16 + 8 * (size_t)L) + 16 * (size_t)L * Q;
-    if ((overlap || Q > 64) && smem > 227 * 1024) {
+    if ((overlap || Q > 128) && smem > 227 * 1024) {
         return mg_fail(ctx, MG_ERR_CAPACITY, "mixed formal solve: longest ray pair does not fit in shared memory");
     }
     int threads = 32 * std::min(L, 8);
+    if (overlap) variant = -1;
     MG_CUDA(cudaMemsetAsync(ctx->d_err, 0, 4, ctx->stream));
     if (overlap) {
         MG_CUDA(cudaFuncSetAttribute(k_feautrier_mixed<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         MgTimed t(ctx, "feautrier_mixed");
         k_feautrier_mixed<true><<<(unsigned)ctx->n, threads, smem, ctx->stream>>>(a);
-    } else if (Q <= 32 || Q <= 64) {
-        const int64_t items = ctx->n * L;
+    } else if (variant >= 0 && variant < kNumWarpVariants) {
+        const WarpVariant &wv = kWarpVariants[variant];
+        const int64_t items = ctx->n * ((L + wv.G - 1) / wv.G);
         const unsigned grid = (unsigned)((items + kWarps2 - 1) / kWarps2);
         MgTimed t(ctx, "feautrier_mixed");
-        if (Q <= 32) k_feautrier_warp<1><<<grid, 32 * kWarps2, 0, ctx->stream>>>(a);
-        else k_feautrier_warp<2><<<grid, 32 * kWarps2, 0, ctx->stream>>>(a);
+        wv.fn<<<grid, 32 * kWarps2, 0, ctx->stream>>>(a);
     } else {
         MG_CUDA(cudaFuncSetAttribute(k_feautrier_mixed<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         MgTimed t(ctx, "feautrier_mixed");
         k_feautrier_mixed<false><<<(unsigned)ctx->n, threads, smem, ctx->stream>>>(a);
     }
     MG_CUDA(cudaGetLastError());
+    return MG_OK;
+}
+
+// Default launch variant for a model: two lines per warp with two bins per lane when the
+// lines have <= 32 bins, otherwise one line per warp with as many bins per lane as needed.
+static int default_variant(int L, int Q) {
+    const int order[] = {3, 2, 4, 0, 1, 6, 5, 8, 7};
+    for (int v : order)
+        if (variant_valid(v, L, Q)) return v;
+    return -1;
+}
+
+int mg_launch_feautrier_mixed(mg_ctx *ctx) {
+    int v = ctx->mixed_variant;
+    if (!variant_valid(v, ctx->n_lines, ctx->Q)) v = default_variant(ctx->n_lines, ctx->Q);
+    return launch_mixed(ctx, v);
+}
+
+// Autotuner: times one formal-solve launch of every valid variant on the loaded model
+// (CUDA events on the context's stream, best of `reps`) and keeps the fastest.
+int mg_autotune_mixed(mg_ctx *ctx, int reps, int *best, double *best_ms, int *n_tried) {
+    const int L = ctx->n_lines, Q = ctx->Q;
+    cudaEvent_t e0, e1;
+    MG_CUDA(cudaEventCreate(&e0));
+    MG_CUDA(cudaEventCreate(&e1));
+    int bv = -1, tried = 0;
+    float bms = 1e30f;
+    const int saved_profile = ctx->opt.profile;
+    ctx->opt.profile = 0;
+    for (int v = 0; v < kNumWarpVariants; v++) {
+        if (!variant_valid(v, L, Q)) continue;
+        tried++;
+        float vbest = 1e30f;
+        for (int r = 0; r < reps + 1; r++) {
+            cudaEventRecord(e0, ctx->stream);
+            int rc = launch_mixed(ctx, v);
+            cudaEventRecord(e1, ctx->stream);
+            if (rc) { ctx->opt.profile = saved_profile; return rc; }
+            cudaEventSynchronize(e1);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (r > 0 && ms < vbest) vbest = ms;   // first launch warms up
+        }
+        if (vbest < bms) { bms = vbest; bv = v; }
+    }
+    ctx->opt.profile = saved_profile;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (bv >= 0) ctx->mixed_variant = bv;
+    if (best) *best = bv;
+    if (best_ms) *best_ms = bms;
+    if (n_tried) *n_tried = tried;
     return MG_OK;
 }

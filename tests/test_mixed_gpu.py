@@ -78,3 +78,27 @@ def test_mixed_ali_fixed_point(name):
     rep, rc = ctx.iterate()
     assert rep["converged"]
     assert np.max(rel_err(ctx.get_populations(), ref)) < TOL_MIX
+
+
+@pytest.mark.parametrize("Q,variants", [(31, [0, 1, 2, 3, 4]), (63, [5, 6]), (100, [7, 8])])
+def test_every_launch_variant_matches_oracle(Q, variants):
+    """Every launch variant of the warp kernel (lines per warp, bins per lane, blocks per
+    SM) gives the same radiation field within the mixed tolerance; the autotuner picks a
+    valid one."""
+    m = syn.model_clumpy_3d(n=1500, seed=6, n_q=Q)
+    o = Oracle(m, nthreads=16)
+    origins = np.sort(np.random.default_rng(3).choice(m.n, 40, replace=False))
+    Jo, Lo, Eo = o.formal_solve(o.lte(), origins)
+    ctx = gpu_context(m, oracle_dirs=o.dirs, precision=1)
+    ctx.trace_rays()
+    ctx.init_populations()
+    for v in variants:
+        ctx.set_variant(v)
+        ctx.formal_solve()
+        J, L, E = ctx.get_radiation()
+        assert np.max(rel_err(J[origins], Jo)) < TOL_MIX, v
+        assert np.max(rel_err(E[origins], Eo)) < TOL_MIX, v
+    best, ms, tried = ctx.autotune(reps=1)
+    assert best in variants and tried == len(variants)
+    J, L, E = ctx.get_radiation()
+    assert np.max(rel_err(J[origins], Jo)) < TOL_MIX
