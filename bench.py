@@ -297,6 +297,41 @@ def run_reference(args):
     }))
 
 
+# ------------------------------------------------------------------ ALI time to converge
+def run_ali(args):
+    """ALI time-to-converge on the workload: from LTE populations to a max relative change
+    below 1e-6, for each requested precision, with Ng off and on. Rays are traced once
+    beforehand (not timed); the timed region is the whole iteration loop."""
+    import torch
+    import paper_1912_08445_gb300 as mg
+    model = build_model(seed=0)
+    stream = torch.cuda.Stream()
+    out = {"metric": "ALI time to converge (max relative population change < 1e-6)", "unit": "s",
+           "higher_is_better": False, "data": "synthetic", "config": dict(WORKLOAD), "runs": []}
+    for prec_name in args.ali_precisions.split(","):
+        prec = mg.MG_MIXED if prec_name == "mixed" else mg.MG_FP64
+        for ng in (0, 4):
+            ctx = mg.Context(precision=prec, tol=1e-6, max_iter=args.ali_max_iter, ng_period=ng)
+            ctx.set_stream(stream.cuda_stream)
+            ctx.load_model(model)
+            ctx.trace_rays()
+            ctx.init_populations()
+            if prec == mg.MG_MIXED:
+                ctx.autotune(reps=1)
+                ctx.init_populations()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            rep, rc = ctx.iterate(allow_not_converged=True)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            out["runs"].append({"precision": prec_name, "ng_period": ng, "seconds": dt,
+                                "iterations": rep["iterations"], "ng_steps": rep["ng_steps"],
+                                "converged": bool(rep["converged"]), "last_change": rep["last_change"],
+                                "fallback_cells": rep["n_fallback"]})
+            ctx.close()
+    print(json.dumps(out))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -305,8 +340,13 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--ali", action="store_true", help="measure ALI time to converge instead")
+    ap.add_argument("--ali-precisions", default="mixed")
+    ap.add_argument("--ali-max-iter", type=int, default=300)
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.ali:
+        run_ali(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_gpu(args)

@@ -24,6 +24,8 @@ using namespace mg;
 namespace {
 
 constexpr float kSqrtLog2e = 1.2011224087864498f;
+constexpr float kSqrt2 = 1.4142135623730951f;
+constexpr float kInvSqrt8 = 0.35355339059327373f;   // 1/(2 sqrt 2)
 
 __device__ __forceinline__ float ex2f(float x) {
     float y;
@@ -310,7 +312,10 @@ constexpr int kRing = 32;
 constexpr int kWarps2 = 4;
 
 struct RingGeom {
-    float4 g;   // (ds/2 to the next point towards the origin, v, sqrt(log2 e)/b, unused)
+    // (ds / (2 sqrt 2) to the next point towards the origin, sqrt(log2 e) v/b,
+    //  sqrt(log2 e)(1 - v/c)/b, unused): the profile argument of bin a_q is then
+    //  x' = a_q g.z - g.y and the half-width interval factor yields delta = dtau/sqrt 2.
+    float4 g;
 };
 
 template <int G>
@@ -324,10 +329,11 @@ __device__ __forceinline__ void stage_ring_point(const MixArgs &a, int64_t o, in
     const int64_t prev = e ? a.cells[off + e - 1] : o;
     const float pv = e ? a.vpar[off + e - 1] : 0.0f;
     const float v = (1.0f - w) * pv + w * a.vpar[off + e];
-    const float hds = 0.5f * a.ds[off + e] / (float)(ns + 1);
+    const float qds = kInvSqrt8 * a.ds[off + e] / (float)(ns + 1);
     const float bb = (1.0f - w) * a.b[prev] + w * a.b[c];
     const float ib = 1.0f / bb;
-    g = make_float4(hds, v, kSqrtLog2e * ib, 0.0f);
+    const float pz = kSqrtLog2e * ib;
+    g = make_float4(qds, v * pz, (1.0f - v * (float)(1.0 / kC)) * pz, 0.0f);
 #pragma unroll
     for (int k = 0; k < G; k++) {
         const int l = l0 + k < a.L ? l0 + k : a.L - 1;
@@ -339,53 +345,60 @@ __device__ __forceinline__ void stage_ring_point(const MixArgs &a, int64_t o, in
     }
 }
 
+// Per-bin sweep state in the variables delta = dtau/sqrt 2, Phi^ = sqrt 2 Phi and
+// psi^ = sqrt 2 psi, in which the recursion carries no factor 1/2:
+//   s = delta_prev + delta,  Phi^ = s + Phi^_prev iota_prev,  iota = 1/(1 + delta Phi^),
+//   psi^ = (s S_prev + psi^_prev) iota.
 template <int NB>
 struct BinState {
-    float aq[NB], A1[NB];
-    float chi_p[NB], S_p[NB], dt_p[NB], Phi[NB], iota[NB], psi[NB];
+    float aq[NB];
+    float chi_p[NB], S_p[NB], d_p[NB], Phi[NB], iota[NB], psi[NB];
 };
 
+// The far end of a half: the boundary row is the interior update from the virtual state
+// Phi^ iota = sqrt 2, psi^ = sqrt 2 I, delta = 0.
 template <int NB>
 __device__ __forceinline__ void first_point(const MixArgs &a, BinState<NB> &st, const float4 g, const float2 d,
-                                            const float nu_g) {
+                                            const float nu_g, const float v) {
     const float SI = d.y * a.inv_chi_min;
 #pragma unroll
     for (int i = 0; i < NB; i++) {
-        const float x = fmaf(-g.y, st.A1[i], st.aq[i]) * g.z;
+        const float x = fmaf(st.aq[i], g.z, -g.y);
         const float chil = d.x * ex2f(-x * x);
         st.chi_p[i] = fmaxf(chil, a.chi_min);
         st.S_p[i] = fminf(d.y, chil * SI);
-        st.Phi[i] = 1.0f;
+        st.Phi[i] = kSqrt2;
         st.iota[i] = 1.0f;
-        st.dt_p[i] = 0.0f;
-        st.psi[i] = planck_f(a, nu_g * st.A1[i] * (1.0f - g.y * (float)(1.0 / kC)));
+        st.d_p[i] = 0.0f;
+        const float A1 = 1.0f + st.aq[i] * (float)(1.0 / kC);
+        st.psi[i] = kSqrt2 * planck_f(a, nu_g * A1 * (1.0f - v * (float)(1.0 / kC)));
     }
 }
 
-// Update with the interval (previous point, this point) of half length hds_p.
+// Update with the interval (previous point, this point), qds_p = ds/(2 sqrt 2).
 template <int NB>
 __device__ __forceinline__ void step_point(const MixArgs &a, BinState<NB> &st, const float4 g, const float2 d,
-                                           const float hds_p) {
+                                           const float qds_p) {
     const float SI = d.y * a.inv_chi_min;
 #pragma unroll
     for (int i = 0; i < NB; i++) {
-        const float x = fmaf(-g.y, st.A1[i], st.aq[i]) * g.z;
+        const float x = fmaf(st.aq[i], g.z, -g.y);
         const float chil = d.x * ex2f(-x * x);
         const float chi = fmaxf(chil, a.chi_min);
         const float Sx = fminf(d.y, chil * SI);
-        const float dt = fmaxf((st.chi_p[i] + chi) * hds_p, a.dtau_min);
-        const float t = 0.5f * (st.dt_p[i] + dt);
-        st.Phi[i] = fmaf(st.Phi[i], st.iota[i], t);
-        st.iota[i] = rcpf(fmaf(dt, st.Phi[i], 1.0f));
-        st.psi[i] = fmaf(t, st.S_p[i], st.psi[i]) * st.iota[i];
-        st.dt_p[i] = dt;
+        const float dl = fmaxf((st.chi_p[i] + chi) * qds_p, a.dtau_min);
+        const float sm = st.d_p[i] + dl;
+        st.Phi[i] = fmaf(st.Phi[i], st.iota[i], sm);
+        st.iota[i] = rcpf(fmaf(dl, st.Phi[i], 1.0f));
+        st.psi[i] = fmaf(sm, st.S_p[i], st.psi[i]) * st.iota[i];
+        st.d_p[i] = dl;
         st.chi_p[i] = chi;
         st.S_p[i] = Sx;
     }
 }
 
-// Sweeps half-ray r from its far end to the origin; returns per bin (Phi iota, psi, dtau)
-// of the row next to the origin, or the empty-half values when the half has no point.
+// Sweeps half-ray r from its far end to the origin; returns per bin (Phi^ iota, psi^,
+// delta) of the row next to the origin, or the empty-half values (sqrt 2, sqrt 2 I_o, 0).
 template <int G, int NB>
 __device__ __forceinline__ void sweep_half(const MixArgs &a, int64_t o, int l0, int grp, int r, float nu_g,
                                            const float4 go, const float2 dlo, RingGeom *rg, float2 *rl,
@@ -397,8 +410,8 @@ __device__ __forceinline__ void sweep_half(const MixArgs &a, int64_t o, int l0, 
     if (Kh == 0) {
 #pragma unroll
         for (int i = 0; i < NB; i++) {
-            pi[i] = 1.0f;
-            ps[i] = planck_f(a, nu_g * st.A1[i]);
+            pi[i] = kSqrt2;
+            ps[i] = kSqrt2 * planck_f(a, nu_g * (1.0f + st.aq[i] * (float)(1.0 / kC)));
             dt[i] = 0.0f;
         }
         return;
@@ -406,7 +419,7 @@ __device__ __forceinline__ void sweep_half(const MixArgs &a, int64_t o, int l0, 
     const float2 *my = rl + grp * kRing;
     int anchor = len - 1;      // element holding the next point to stage
     int xnext = Kh - 1;        // next point to stage (descending towards the origin)
-    float hds_p = 0.0f;
+    float qds_p = 0.0f;
     bool first = true;
     while (xnext >= 0) {
         const int cnt = min(kRing, xnext + 1);
@@ -425,24 +438,26 @@ __device__ __forceinline__ void sweep_half(const MixArgs &a, int64_t o, int l0, 
         int j = 0;
         if (first) {
             const float4 g = rg[0].g;
-            first_point<NB>(a, st, g, my[0], nu_g);
-            hds_p = g.x;
+            const float vfar = g.y / (g.z + g.y * (float)(1.0 / kC));   // v = (v pz)/pz
+            first_point<NB>(a, st, g, my[0], nu_g, vfar);
+            qds_p = g.x;
             j = 1;
             first = false;
         }
+#pragma unroll 4
         for (; j < cnt; j++) {
             const float4 g = rg[j].g;
-            step_point<NB>(a, st, g, my[j], hds_p);
-            hds_p = g.x;
+            step_point<NB>(a, st, g, my[j], qds_p);
+            qds_p = g.x;
         }
         xnext -= cnt;
     }
-    step_point<NB>(a, st, go, dlo, hds_p);   // the origin
+    step_point<NB>(a, st, go, dlo, qds_p);   // the origin
 #pragma unroll
     for (int i = 0; i < NB; i++) {
         pi[i] = st.Phi[i] * st.iota[i];
         ps[i] = st.psi[i];
-        dt[i] = st.dt_p[i];
+        dt[i] = st.d_p[i];
     }
 }
 
@@ -465,7 +480,7 @@ __global__ void __launch_bounds__(32 * kWarps2, MINB) k_feautrier_warp(MixArgs a
     const float bo = a.b[o];
     const float ibo = 1.0f / bo;
     const float2 dl = reinterpret_cast<const float2 *>(a.line)[o * a.L + lc];
-    const float4 go = make_float4(0.0f, 0.0f, kSqrtLog2e * ibo, 0.0f);
+    const float4 go = make_float4(0.0f, 0.0f, kSqrtLog2e * ibo, 0.0f);   // v = 0 at the origin
     const float2 dlo = make_float2(fmaxf(dl.y, 0.0f) * a.kline[lc] * ibo, dl.y > 0.0f ? dl.x / dl.y : 0.0f);
     const float nu_g = a.nu_ghz[lc];
     BinState<NB> st;
@@ -475,7 +490,6 @@ __global__ void __launch_bounds__(32 * kWarps2, MINB) k_feautrier_warp(MixArgs a
     for (int i = 0; i < NB; i++) {
         const int q = li + LPG * i;
         st.aq[i] = q < Q ? (float)(a.roots[q] * (double)bo) : 0.0f;
-        st.A1[i] = 1.0f + st.aq[i] * (float)(1.0 / kC);
         acc[i][0] = acc[i][1] = acc[i][2] = acc[i][3] = 0.0f;
         const float x = st.aq[i] * go.z;
         const float chil = dlo.x * ex2f(-x * x);
@@ -493,9 +507,10 @@ __global__ void __launch_bounds__(32 * kWarps2, MINB) k_feautrier_warp(MixArgs a
         for (int i = 0; i < NB; i++) {
             float u, lam, uml, oml;
             if (dtb[i] == 0.0f && dtf[i] == 0.0f) {   // isolated origin: both halves empty
-                u = psb[i]; lam = 0.0f; uml = psb[i]; oml = 1.0f;
+                u = psb[i] * (float)(1.0 / 1.4142135623730951); lam = 0.0f; uml = u; oml = 1.0f;
             } else {
-                const float sig = 2.0f / (dtb[i] + dtf[i]);
+                // sigma (Phi iota) = Phi^ iota / (delta_- + delta_+), sigma psi = psi^ / (delta_- + delta_+)
+                const float sig = 1.0f / (dtb[i] + dtf[i]);
                 const float pi2 = pib[i] + pif[i];
                 const float iD = 1.0f / fmaf(sig, pi2, 1.0f);
                 const float s2 = sig * (psb[i] + psf[i]);
