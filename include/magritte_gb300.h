@@ -43,6 +43,8 @@ extern "C" {
 #define MG_ERR_CAPACITY          (-7)  /* a ray pair exceeds the kernel's staging limit */
 #define MG_WARN_DEAD_END_RAYS      1   /* some rays ended at a cell with no farther neighbour */
 #define MG_WARN_NEG_POP_FALLBACK   2   /* some cells fell back to plain Lambda iteration    */
+#define MG_WARN_NEG_OPACITY        3   /* some line opacity integral was negative (population
+                                          inversion, a maser): the opacity floor was applied  */
 
 /* precision of the formal solve */
 #define MG_FP64   0   /* everything in FP64                                              */
@@ -179,7 +181,8 @@ int mg_get_spectrum(const mg_ctx *ctx, double *Jnu);
  * validity check (negative or non-finite populations -> the cell is solved again
  * without the ALO, Sec. 6.1) and the convergence measure: *max_rel_change = max over
  * cells and levels with n_i >= 1e-10 n of |n_new - n_old| / n_new (NULL allowed).
- * Returns MG_WARN_NEG_POP_FALLBACK when some cell fell back. Synchronises. */
+ * Returns MG_WARN_NEG_POP_FALLBACK when some cell fell back, else MG_WARN_NEG_OPACITY
+ * when the last formal solve met a negative line opacity integral. Synchronises. */
 int mg_update_populations(mg_ctx *ctx, double *max_rel_change);
 
 /* Allocation-free variant of mg_update_populations for callers that cannot allocate
@@ -199,6 +202,11 @@ int mg_update_populations(mg_ctx *ctx, double *max_rel_change);
  * overlap on the GPU (other streams, threads or contexts) race on the shared scratch. */
 int mg_update_populations_noalloc(mg_ctx *ctx, const double *d_pops_old, double *d_pops_new,
                                   double *max_rel_change, int64_t *n_fallback);
+
+/* Counts behind the warnings of the last mg_update_populations: cells that fell back
+ * without the ALO, and (point, line) pairs with a negative opacity integral in the last
+ * formal solve. Either pointer may be NULL. */
+int mg_status_counts(const mg_ctx *ctx, int64_t *fallback_cells, int64_t *negative_opacity);
 
 typedef struct {
     int32_t iterations;      /* regular iterations done                            */

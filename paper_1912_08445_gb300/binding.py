@@ -16,7 +16,7 @@ from . import build as _build
 MG_OK = 0
 MG_ERR_ARG, MG_ERR_STATE, MG_ERR_CUDA, MG_ERR_OOM = -1, -2, -3, -4
 MG_ERR_NOT_CONVERGED, MG_ERR_NUMERIC, MG_ERR_CAPACITY = -5, -6, -7
-MG_WARN_DEAD_END_RAYS, MG_WARN_NEG_POP_FALLBACK = 1, 2
+MG_WARN_DEAD_END_RAYS, MG_WARN_NEG_POP_FALLBACK, MG_WARN_NEG_OPACITY = 1, 2, 3
 MG_FP64, MG_MIXED = 0, 1
 MG_GEOM_3D, MG_GEOM_SPHERICAL_1D = 0, 1
 MG_INIT_LTE, MG_INIT_GIVEN = 0, 1
@@ -80,6 +80,7 @@ _SIGS = {
     "mg_reset_kernel_times": (C.c_int, [_P]),
     "mg_work_counts": (C.c_int, [_P, _P, _P]),
     "mg_autotune": (C.c_int, [_P, C.c_int32, _P, _P, _P]),
+    "mg_status_counts": (C.c_int, [_P, _P, _P]),
     "mg_set_variant": (C.c_int, [_P, C.c_int32]),
 }
 
@@ -290,6 +291,11 @@ class Context:
 
     def reset_kernel_times(self):
         self._chk(self.lib.mg_reset_kernel_times(self.h), "mg_reset_kernel_times")
+
+    def status_counts(self):
+        f = C.c_int64(0); n = C.c_int64(0)
+        self._chk(self.lib.mg_status_counts(self.h, C.byref(f), C.byref(n)), "mg_status_counts")
+        return f.value, n.value
 
     def autotune(self, reps=2):
         v = C.c_int32(0); ms = C.c_double(0); nt = C.c_int32(0)

@@ -129,7 +129,9 @@ struct mg_ctx {
     bool have_rad = false;
 
     // ---- scalars
-    unsigned long long *d_scal = nullptr;   // [0] max change bits, [1] fallbacks, [2] flags
+    unsigned long long *d_scal = nullptr;   // [0] max change bits, [1] fallbacks, [2] non-finite,
+                                            // [3] Ng flags, [4] negative line opacities
+    int64_t last_fallback = 0, last_neg_opacity = 0;
     unsigned long long *h_scal = nullptr;   // pinned
     int32_t *d_err = nullptr;               // kernel error word
 

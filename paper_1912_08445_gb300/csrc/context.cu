@@ -83,6 +83,7 @@ extern "C" int mg_create(mg_ctx **out, const mg_options *opt) {
         return MG_ERR_CUDA;
     }
     ctx->stream = ctx->own_stream;
+    cudaMemset(ctx->d_scal, 0, 8 * sizeof(unsigned long long));
     *out = ctx;
     return MG_OK;
 }
@@ -658,6 +659,7 @@ extern "C" int mg_formal_solve(mg_ctx *ctx) {
     if ((rc = ensure_state(ctx))) return rc;
     if (ctx->h_ovl_off.size() != (size_t)ctx->n_lines + 1)
         if ((rc = upload_overlaps(ctx))) return rc;
+    MG_CUDA(cudaMemsetAsync(ctx->d_scal + 4, 0, sizeof(unsigned long long), ctx->stream));
     if ((rc = mg_launch_line_data(ctx))) return rc;
     if ((rc = mg_launch_feautrier(ctx))) return rc;
     ctx->have_rad = true;
@@ -711,14 +713,24 @@ extern "C" int mg_update_populations(mg_ctx *ctx, double *max_rel_change) {
         ctx->coll_ready = true;
     }
     if ((rc = mg_launch_stateq(ctx))) return rc;
-    MG_CUDA(cudaMemcpyAsync(ctx->h_scal, ctx->d_scal, 3 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, ctx->stream));
+    MG_CUDA(cudaMemcpyAsync(ctx->h_scal, ctx->d_scal, 5 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, ctx->stream));
     MG_CUDA(cudaStreamSynchronize(ctx->stream));
     double ch;
     std::memcpy(&ch, &ctx->h_scal[0], 8);
     if (max_rel_change) *max_rel_change = ch;
     ctx->have_rad = false;
+    ctx->last_fallback = (int64_t)ctx->h_scal[1];
+    ctx->last_neg_opacity = (int64_t)ctx->h_scal[4];
     if (ctx->h_scal[2]) return mg_fail(ctx, MG_ERR_NUMERIC, "statistical equilibrium: non-finite populations after fallback");
-    return ctx->h_scal[1] ? MG_WARN_NEG_POP_FALLBACK : MG_OK;
+    if (ctx->h_scal[1]) return MG_WARN_NEG_POP_FALLBACK;
+    return ctx->h_scal[4] ? MG_WARN_NEG_OPACITY : MG_OK;
+}
+
+extern "C" int mg_status_counts(const mg_ctx *ctx, int64_t *fallback_cells, int64_t *negative_opacity) {
+    if (!ctx) return MG_ERR_ARG;
+    if (fallback_cells) *fallback_cells = ctx->last_fallback;
+    if (negative_opacity) *negative_opacity = ctx->last_neg_opacity;
+    return MG_OK;
 }
 
 // ------------------------------------------------------------------ ALI driver
@@ -735,7 +747,7 @@ extern "C" int mg_iterate(mg_ctx *ctx, mg_ali_report *rep) {
         double ch = 0;
         rc = mg_update_populations(ctx, &ch);
         if (rc < 0) return rc;
-        if (rc == MG_WARN_NEG_POP_FALLBACK) r.n_fallback += (int64_t)ctx->h_scal[1];
+        r.n_fallback += ctx->last_fallback;
         r.iterations = it + 1;
         r.last_change = ch;
         if (ch < ctx->opt.tol) { r.converged = 1; break; }

@@ -10,7 +10,7 @@ namespace {
 // eta_int = h nu/4pi n_u A_ul, chi_int = h nu/4pi (n_l B_lu - n_u B_ul) (eq. 'lines'),
 // stored per point as [L][2] so that one gather brings all lines of a point.
 __global__ void k_line_data(int64_t n, int L, int nlev, const double *__restrict__ pops,
-                            const LineConst *__restrict__ lc, double *__restrict__ line, float *__restrict__ linef) {
+                            const LineConst *__restrict__ lc, double *__restrict__ line, float *__restrict__ linef, unsigned long long *neg) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= n * L) return;
     const int64_t c = t / L;
@@ -21,6 +21,7 @@ __global__ void k_line_data(int64_t n, int L, int nlev, const double *__restrict
     const double chi = k.pre * (nl_ * k.Blu - nu_ * k.Bul);
     line[2 * t] = eta;
     line[2 * t + 1] = chi;
+    if (chi < 0.0) atomicAdd(neg, 1ull);
     if (linef) {
         linef[2 * t] = (float)eta;
         linef[2 * t + 1] = (float)chi;
@@ -250,7 +251,7 @@ int mg_launch_line_data(mg_ctx *ctx) {
     const int64_t m = ctx->n * ctx->n_lines;
     MgTimed t(ctx, "line_data");
     k_line_data<<<(unsigned)((m + 255) / 256), 256, 0, ctx->stream>>>(
-        ctx->n, ctx->n_lines, ctx->n_lev, ctx->d_pops, ctx->d_lines, ctx->d_line, nullptr);
+        ctx->n, ctx->n_lines, ctx->n_lev, ctx->d_pops, ctx->d_lines, ctx->d_line, nullptr, ctx->d_scal + 4);
     MG_CUDA(cudaGetLastError());
     return MG_OK;
 }

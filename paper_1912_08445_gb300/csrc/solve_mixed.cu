@@ -40,7 +40,7 @@ __device__ __forceinline__ float rcpf(float x) {
 
 __global__ void k_line_data_f32(int64_t n, int L, int nlev, const double *__restrict__ pops,
                                 const LineConst *__restrict__ lc, double *__restrict__ line,
-                                float *__restrict__ linef) {
+                                float *__restrict__ linef, unsigned long long *neg) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= n * L) return;
     const int64_t c = t / L;
@@ -51,6 +51,7 @@ __global__ void k_line_data_f32(int64_t n, int L, int nlev, const double *__rest
     const double chi = k.pre * (nl_ * k.Blu - nu_ * k.Bul);
     line[2 * t] = eta;
     line[2 * t + 1] = chi;
+    if (chi < 0.0) atomicAdd(neg, 1ull);
     linef[2 * t] = (float)(eta * kEtaScale);
     linef[2 * t + 1] = (float)(chi * kChiScale);
 }
@@ -577,7 +578,7 @@ int mg_launch_line_data_mixed(mg_ctx *ctx) {
     MgTimed t(ctx, "line_data");
     k_line_data_f32<<<(unsigned)((m + 255) / 256), 256, 0, ctx->stream>>>(ctx->n, ctx->n_lines, ctx->n_lev,
                                                                           ctx->d_pops, ctx->d_lines, ctx->d_line,
-                                                                          ctx->d_linef);
+                                                                          ctx->d_linef, ctx->d_scal + 4);
     MG_CUDA(cudaGetLastError());
     return MG_OK;
 }

@@ -201,13 +201,16 @@ def model_sphere_1d(seed=0, n=200, r_min=1e12, r_max=1e15, n_q=31, nside=1, A21=
 
 
 def model_clumpy_3d(seed=0, n=50_000, R=1e15, n_clumps=20, k=16, nside=2, n_q=31,
-                    n_lev=5, v_max=1.0e4, bdy_frac=None, n_h2_ref=1e10, abundance=1e-8,
+                    n_lev=5, v_max=1.0e4, bdy_frac=None, n_h2_ref=1e11, abundance=1e-6,
                     species=None):
     """3D clumpy cloud: points drawn from an r^-2 background plus seeded Gaussian clumps
     inside a sphere of radius R, about bdy_frac of them on the bounding sphere (convex
     hull), symmetric k-NN lists, T falling log-linearly from 100 K (centre) to 10 K
     (edge), radial outflow v = v_max r/R, 150 m/s turbulence, seeded linear rotor.
-    By default the boundary points get the spacing of the interior points at the edge."""
+    By default the boundary points get the spacing of the interior points at the edge.
+    The default density (n_H2 = 1e11 m^-3 (r/R)^-2 plus clumps) and abundance (1e-6) make
+    the lines optically thick without population inversion of the rotor's lowest line,
+    which sets in below ~1e10 m^-3 (a maser the method does not treat)."""
     rng = np.random.default_rng(seed)
     if bdy_frac is None:
         nb_est = 0.7 * n

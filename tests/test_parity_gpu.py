@@ -210,3 +210,28 @@ def test_isolated_and_boundary_points():
     assert np.max(rel_err(J, Jo)) < TOL64
     assert np.max(rel_err(E, Eo)) < TOL64
     assert np.all(L[0] == 0.0)
+
+
+def test_negative_opacity_is_reported():
+    """A population inversion (n_u/g_u > n_l/g_l: a maser, which the method does not
+    treat) makes the line opacity integral negative: the update reports
+    MG_WARN_NEG_OPACITY and counts the (point, line) pairs."""
+    import paper_1912_08445_gb300 as mg
+    m = syn.model_tiny_3d(seed=4, n=20)
+    o = Oracle(m, nthreads=4)
+    ctx = gpu_context(m, oracle_dirs=o.dirs)
+    ctx.trace_rays()
+    pops = o.lte()
+    sp = m.species
+    u, lo = int(sp.up[0]), int(sp.lo[0])
+    pops[3, u] = pops[3, lo] * sp.g[u] / sp.g[lo] * 1.5     # invert line 0 in point 3
+    ctx.set_populations(pops)
+    ctx.formal_solve()
+    ch, rc = ctx.update_populations()
+    fb, neg = ctx.status_counts()
+    assert neg == 1
+    assert rc in (mg.MG_WARN_NEG_OPACITY, mg.MG_WARN_NEG_POP_FALLBACK)
+    ctx.init_populations()
+    ctx.formal_solve()
+    ch, rc = ctx.update_populations()
+    assert ctx.status_counts()[1] == 0 and rc == 0
