@@ -234,6 +234,32 @@ int mg_autotune(mg_ctx *ctx, int32_t reps, int32_t *variant, double *ms, int32_t
  * to the default at launch. */
 int mg_set_variant(mg_ctx *ctx, int32_t variant);
 
+/* ---- Batches of independent models (uneven sizes) --------------------------------
+ * A batch runs the ALI of many contexts together: every iteration is one CUDA graph
+ * (line data of every model, one persistent formal-solve launch whose warps take work
+ * items from a queue ordered by decreasing ray length, statistical equilibrium of every
+ * model), and converged models drop out through device-side flags.
+ * The contexts must be traced and populated, on the same device, in MG_MIXED precision,
+ * with the same number of lines and bins and no overlapping lines. The batch keeps the
+ * context pointers but does not own the contexts: destroy the batch first. While a batch
+ * call runs, the contexts use the batch's stream. The batch ALI runs without Ng steps. */
+typedef struct mg_batch mg_batch;
+int mg_batch_create(mg_batch **out, int32_t n_models, mg_ctx *const *models);
+int mg_batch_destroy(mg_batch *batch);
+const char *mg_batch_last_error(const mg_batch *batch);
+/* Formal solve of every model (line data + one persistent launch). Synchronises. */
+int mg_batch_formal_solve(mg_batch *batch);
+/* ALI of every model to its own opt.tol / the first model's opt.max_iter; reps[n_models]
+ * (may be NULL) receives per-model reports. MG_ERR_NOT_CONVERGED if some model did not
+ * converge. */
+int mg_batch_iterate(mg_batch *batch, mg_ali_report *reps);
+/* Autotuner of the batched launch: times every valid kernel variant with the work queue
+ * in cost order and in natural order (CUDA events, best of reps after a warm-up) and keeps
+ * the fastest. Leaves a valid radiation field in every model. */
+int mg_batch_autotune(mg_batch *batch, int32_t reps, int32_t *variant, int32_t *sorted, double *ms);
+/* Sum of mg_work_counts over the batch's models. */
+int mg_batch_work_counts(const mg_batch *batch, int64_t *solves, int64_t *cell_freq_updates);
+
 /* Kernel timing (opt.profile = 1): total milliseconds and launch counts per kernel
  * since the last reset, for up to cap kernels; names[i] points to static strings. */
 int mg_kernel_times(const mg_ctx *ctx, int32_t cap, const char **names, double *ms,

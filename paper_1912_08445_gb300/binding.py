@@ -81,6 +81,13 @@ _SIGS = {
     "mg_work_counts": (C.c_int, [_P, _P, _P]),
     "mg_autotune": (C.c_int, [_P, C.c_int32, _P, _P, _P]),
     "mg_status_counts": (C.c_int, [_P, _P, _P]),
+    "mg_batch_create": (C.c_int, [_P, C.c_int32, _P]),
+    "mg_batch_destroy": (C.c_int, [_P]),
+    "mg_batch_last_error": (C.c_char_p, [_P]),
+    "mg_batch_formal_solve": (C.c_int, [_P]),
+    "mg_batch_iterate": (C.c_int, [_P, _P]),
+    "mg_batch_autotune": (C.c_int, [_P, C.c_int32, _P, _P, _P]),
+    "mg_batch_work_counts": (C.c_int, [_P, _P, _P]),
     "mg_set_variant": (C.c_int, [_P, C.c_int32]),
 }
 
@@ -324,3 +331,55 @@ class Context:
         else:
             self.set_directions(nside if nside is not None else m.nside)
         self.set_quadrature(n_q if n_q is not None else m.n_q)
+
+
+class Batch:
+    """Owns one mg_batch over existing Contexts (which must outlive it)."""
+
+    def __init__(self, contexts):
+        self.lib = load()
+        self.contexts = list(contexts)
+        arr = (C.c_void_p * len(self.contexts))(*[c.h.value for c in self.contexts])
+        h = C.c_void_p()
+        rc = self.lib.mg_batch_create(C.byref(h), len(self.contexts), arr)
+        if rc != MG_OK:
+            msg = self.lib.mg_last_error(self.contexts[0].h)
+            raise MagritteError(rc, f"mg_batch_create: {msg.decode() if msg else ''}")
+        self.h = h
+
+    def _chk(self, rc, what):
+        if rc < 0:
+            msg = self.lib.mg_batch_last_error(self.h)
+            raise MagritteError(rc, f"{what}: {msg.decode() if msg else ''}")
+        return rc
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.mg_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def formal_solve(self):
+        self._chk(self.lib.mg_batch_formal_solve(self.h), "mg_batch_formal_solve")
+
+    def iterate(self, allow_not_converged=False):
+        reps = (mg_ali_report * len(self.contexts))()
+        rc = self.lib.mg_batch_iterate(self.h, reps)
+        if rc < 0 and not (allow_not_converged and rc == MG_ERR_NOT_CONVERGED):
+            self._chk(rc, "mg_batch_iterate")
+        return [{k: getattr(r, k) for k, _ in r._fields_ if k != "pad"} for r in reps], rc
+
+    def autotune(self, reps=2):
+        v = C.c_int32(0); s = C.c_int32(0); ms = C.c_double(0)
+        self._chk(self.lib.mg_batch_autotune(self.h, int(reps), C.byref(v), C.byref(s), C.byref(ms)), "mg_batch_autotune")
+        return v.value, s.value, ms.value
+
+    def work_counts(self):
+        s = C.c_int64(0); u = C.c_int64(0)
+        self._chk(self.lib.mg_batch_work_counts(self.h, C.byref(s), C.byref(u)), "mg_batch_work_counts")
+        return s.value, u.value

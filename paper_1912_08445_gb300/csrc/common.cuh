@@ -188,3 +188,15 @@ int mg_launch_collision_rates(mg_ctx *ctx);
 int mg_launch_stateq(mg_ctx *ctx);
 int mg_launch_ng(mg_ctx *ctx, int *accepted);
 int mg_launch_push_history(mg_ctx *ctx);
+int mg_launch_stateq_into(mg_ctx *ctx, const double *pops_old, double *pops_new, const int32_t *active);
+int mg_ensure_solve_state(mg_ctx *ctx);   // state buffers, overlaps and collision rates ready
+// batch helpers (solve_mixed.cu)
+size_t mg_mixargs_size();
+int mg_fill_mixargs(mg_ctx *ctx, void *out);
+int mg_variant_count();
+int mg_variant_valid(int v, int L, int Q);
+int mg_variant_minb(int v);
+int mg_variant_g(int v);
+int mg_variant_default(int L, int Q);
+int mg_batch_launch(int v, int grid, const void *d_args, const void *d_items, int64_t n_items,
+                    unsigned long long *counter, const int32_t *active, cudaStream_t stream);

@@ -768,6 +768,19 @@ extern "C" int mg_iterate(mg_ctx *ctx, mg_ali_report *rep) {
     return r.converged ? MG_OK : mg_fail(ctx, MG_ERR_NOT_CONVERGED, "ALI did not reach the tolerance");
 }
 
+int mg_ensure_solve_state(mg_ctx *ctx) {
+    int rc;
+    if ((rc = check_solve_ready(ctx))) return rc;
+    if ((rc = ensure_state(ctx))) return rc;
+    if (ctx->h_ovl_off.size() != (size_t)ctx->n_lines + 1)
+        if ((rc = upload_overlaps(ctx))) return rc;
+    if (!ctx->coll_ready) {
+        if ((rc = mg_launch_collision_rates(ctx))) return rc;
+        ctx->coll_ready = true;
+    }
+    return MG_OK;
+}
+
 // ------------------------------------------------------------------ autotuning
 extern "C" int mg_autotune(mg_ctx *ctx, int32_t reps, int32_t *variant, double *ms, int32_t *n_tried) {
     if (!ctx) return MG_ERR_ARG;

@@ -17,6 +17,7 @@
 //   Phi = t + Phi iota,  iota = 1/(1 + dtau Phi),  psi = (t S + psi) iota,
 // the rescaled Rybicki-Hummer recursion described with the FP64 kernel.
 #include <cmath>
+#include <cstring>
 #include "common.cuh"
 
 using namespace mg;
@@ -312,6 +313,15 @@ __global__ void __launch_bounds__(256) k_feautrier_mixed(MixArgs a) {
 constexpr int kRing = 32;
 constexpr int kWarps2 = 4;
 
+// Scalars of the sweep, held in registers (not re-read from the argument block).
+struct SweepK {
+    float chi_min, inv_chi_min, dtau_min, planck_a, planck_b;
+};
+
+__device__ __forceinline__ float planck_k(const SweepK &k, float nu_g) {
+    return k.planck_a * nu_g * nu_g * nu_g / expm1f(k.planck_b * nu_g);
+}
+
 struct RingGeom {
     // (ds / (2 sqrt 2) to the next point towards the origin, sqrt(log2 e) v/b,
     //  sqrt(log2 e)(1 - v/c)/b, unused): the profile argument of bin a_q is then
@@ -359,7 +369,7 @@ struct BinState {
 // The far end of a half: the boundary row is the interior update from the virtual state
 // Phi^ iota = sqrt 2, psi^ = sqrt 2 I, delta = 0.
 template <int NB>
-__device__ __forceinline__ void first_point(const MixArgs &a, BinState<NB> &st, const float4 g, const float2 d,
+__device__ __forceinline__ void first_point(const SweepK &a, BinState<NB> &st, const float4 g, const float2 d,
                                             const float nu_g, const float v) {
     const float SI = d.y * a.inv_chi_min;
 #pragma unroll
@@ -372,13 +382,13 @@ __device__ __forceinline__ void first_point(const MixArgs &a, BinState<NB> &st, 
         st.iota[i] = 1.0f;
         st.d_p[i] = 0.0f;
         const float A1 = 1.0f + st.aq[i] * (float)(1.0 / kC);
-        st.psi[i] = kSqrt2 * planck_f(a, nu_g * A1 * (1.0f - v * (float)(1.0 / kC)));
+        st.psi[i] = kSqrt2 * planck_k(a, nu_g * A1 * (1.0f - v * (float)(1.0 / kC)));
     }
 }
 
 // Update with the interval (previous point, this point), qds_p = ds/(2 sqrt 2).
 template <int NB>
-__device__ __forceinline__ void step_point(const MixArgs &a, BinState<NB> &st, const float4 g, const float2 d,
+__device__ __forceinline__ void step_point(const SweepK &a, BinState<NB> &st, const float4 g, const float2 d,
                                            const float qds_p) {
     const float SI = d.y * a.inv_chi_min;
 #pragma unroll
@@ -401,8 +411,8 @@ __device__ __forceinline__ void step_point(const MixArgs &a, BinState<NB> &st, c
 // Sweeps half-ray r from its far end to the origin; returns per bin (Phi^ iota, psi^,
 // delta) of the row next to the origin, or the empty-half values (sqrt 2, sqrt 2 I_o, 0).
 template <int G, int NB>
-__device__ __forceinline__ void sweep_half(const MixArgs &a, int64_t o, int l0, int grp, int r, float nu_g,
-                                           const float4 go, const float2 dlo, RingGeom *rg, float2 *rl,
+__device__ __forceinline__ void sweep_half(const MixArgs &a, const SweepK &k, int64_t o, int l0, int grp, int r,
+                                           float nu_g, const float4 go, const float2 dlo, RingGeom *rg, float2 *rl,
                                            BinState<NB> &st, float (&pi)[NB], float (&ps)[NB], float (&dt)[NB]) {
     const int lane = threadIdx.x & 31;
     const int64_t off = a.ray_off[o * a.R + r];
@@ -412,7 +422,7 @@ __device__ __forceinline__ void sweep_half(const MixArgs &a, int64_t o, int l0, 
 #pragma unroll
         for (int i = 0; i < NB; i++) {
             pi[i] = kSqrt2;
-            ps[i] = kSqrt2 * planck_f(a, nu_g * (1.0f + st.aq[i] * (float)(1.0 / kC)));
+            ps[i] = kSqrt2 * planck_k(k, nu_g * (1.0f + st.aq[i] * (float)(1.0 / kC)));
             dt[i] = 0.0f;
         }
         return;
@@ -440,7 +450,7 @@ __device__ __forceinline__ void sweep_half(const MixArgs &a, int64_t o, int l0, 
         if (first) {
             const float4 g = rg[0].g;
             const float vfar = g.y / (g.z + g.y * (float)(1.0 / kC));   // v = (v pz)/pz
-            first_point<NB>(a, st, g, my[0], nu_g, vfar);
+            first_point<NB>(k, st, g, my[0], nu_g, vfar);
             qds_p = g.x;
             j = 1;
             first = false;
@@ -448,12 +458,12 @@ __device__ __forceinline__ void sweep_half(const MixArgs &a, int64_t o, int l0, 
 #pragma unroll 4
         for (; j < cnt; j++) {
             const float4 g = rg[j].g;
-            step_point<NB>(a, st, g, my[j], qds_p);
+            step_point<NB>(k, st, g, my[j], qds_p);
             qds_p = g.x;
         }
         xnext -= cnt;
     }
-    step_point<NB>(a, st, go, dlo, qds_p);   // the origin
+    step_point<NB>(k, st, go, dlo, qds_p);   // the origin
 #pragma unroll
     for (int i = 0; i < NB; i++) {
         pi[i] = st.Phi[i] * st.iota[i];
@@ -462,17 +472,11 @@ __device__ __forceinline__ void sweep_half(const MixArgs &a, int64_t o, int l0, 
     }
 }
 
-template <int G, int NB, int MINB>
-__global__ void __launch_bounds__(32 * kWarps2, MINB) k_feautrier_warp(MixArgs a) {
-    __shared__ RingGeom rgs[kWarps2][kRing];
-    __shared__ float2 rls[kWarps2][G * kRing];
+// One work item: origin o, lines l0 .. l0+G-1, all ray pairs, all bins (one warp).
+template <int G, int NB>
+__device__ __forceinline__ void solve_item(const MixArgs &a, int64_t o, int l0, RingGeom *rg, float2 *rl) {
     constexpr int LPG = 32 / G;   // lanes per line
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int ngroups = (a.L + G - 1) / G;
-    const int64_t item = (int64_t)blockIdx.x * kWarps2 + warp;
-    if (item >= a.n * ngroups) return;
-    const int64_t o = item / ngroups;
-    const int l0 = (int)(item - o * ngroups) * G;
+    const int lane = threadIdx.x & 31;
     const int grp = lane / LPG, li = lane - grp * LPG;
     const int l = l0 + grp;
     const bool line_ok = l < a.L;
@@ -484,6 +488,7 @@ __global__ void __launch_bounds__(32 * kWarps2, MINB) k_feautrier_warp(MixArgs a
     const float4 go = make_float4(0.0f, 0.0f, kSqrtLog2e * ibo, 0.0f);   // v = 0 at the origin
     const float2 dlo = make_float2(fmaxf(dl.y, 0.0f) * a.kline[lc] * ibo, dl.y > 0.0f ? dl.x / dl.y : 0.0f);
     const float nu_g = a.nu_ghz[lc];
+    const SweepK k{a.chi_min, a.inv_chi_min, a.dtau_min, a.planck_a, a.planck_b};
     BinState<NB> st;
     float acc[NB][4];
     float chio[NB], Sov[NB], chilo[NB];
@@ -498,12 +503,10 @@ __global__ void __launch_bounds__(32 * kWarps2, MINB) k_feautrier_warp(MixArgs a
         chio[i] = fmaxf(chil, a.chi_min);
         Sov[i] = fminf(dlo.y, chil * dlo.y * a.inv_chi_min);
     }
-    RingGeom *rg = rgs[warp];
-    float2 *rl = rls[warp];
     for (int p = 0; p < a.P; p++) {
         float pib[NB], psb[NB], dtb[NB], pif[NB], psf[NB], dtf[NB];
-        sweep_half<G, NB>(a, o, l0, grp, a.pb[p], nu_g, go, dlo, rg, rl, st, pib, psb, dtb);
-        sweep_half<G, NB>(a, o, l0, grp, a.pf[p], nu_g, go, dlo, rg, rl, st, pif, psf, dtf);
+        sweep_half<G, NB>(a, k, o, l0, grp, a.pb[p], nu_g, go, dlo, rg, rl, st, pib, psb, dtb);
+        sweep_half<G, NB>(a, k, o, l0, grp, a.pf[p], nu_g, go, dlo, rg, rl, st, pif, psf, dtf);
 #pragma unroll
         for (int i = 0; i < NB; i++) {
             float u, lam, uml, oml;
@@ -549,19 +552,64 @@ __global__ void __launch_bounds__(32 * kWarps2, MINB) k_feautrier_warp(MixArgs a
     }
 }
 
+template <int G, int NB, int MINB>
+__global__ void __launch_bounds__(32 * kWarps2, MINB) k_feautrier_warp(MixArgs a) {
+    __shared__ RingGeom rgs[kWarps2][kRing];
+    __shared__ float2 rls[kWarps2][G * kRing];
+    const int warp = threadIdx.x >> 5;
+    const int ngroups = (a.L + G - 1) / G;
+    const int64_t item = (int64_t)blockIdx.x * kWarps2 + warp;
+    if (item >= a.n * ngroups) return;
+    const int64_t o = item / ngroups;
+    const int l0 = (int)(item - o * ngroups) * G;
+    solve_item<G, NB>(a, o, l0, rgs[warp], rls[warp]);
+}
+
+// Persistent variant over a batch of models: every warp takes work items (model, origin,
+// line group) from a queue ordered by decreasing cost until the queue is empty. The
+// per-model arguments are copied once per item into the warp's shared-memory slot.
+struct BatchItem {
+    int32_t model;
+    int32_t local;   // origin * L + first line of the warp's line group
+};
+
+template <int G, int NB, int MINB>
+__global__ void __launch_bounds__(32 * kWarps2, MINB)
+k_feautrier_batch(const MixArgs *__restrict__ models, const BatchItem *__restrict__ items, int64_t n_items,
+                  unsigned long long *counter, const int32_t *__restrict__ active) {
+    __shared__ RingGeom rgs[kWarps2][kRing];
+    __shared__ float2 rls[kWarps2][G * kRing];
+    __shared__ MixArgs sa[kWarps2];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (;;) {
+        unsigned long long idx = 0;
+        if (lane == 0) idx = atomicAdd(counter, 1ull);
+        idx = __shfl_sync(0xffffffffu, idx, 0);
+        if (idx >= (unsigned long long)n_items) break;
+        const BatchItem it = items[idx];
+        if (!active[it.model]) continue;
+        __syncwarp();
+        if (lane == 0) sa[warp] = models[it.model];
+        __syncwarp();
+        const MixArgs &a = sa[warp];
+        const int64_t o = it.local / a.L;
+        const int l0 = (int)(it.local - o * a.L);
+        solve_item<G, NB>(a, o, l0, rgs[warp], rls[warp]);
+    }
+}
 
 // Launch variants of the warp kernel: (lines per warp, bins per lane, min blocks per SM).
 struct WarpVariant {
     int G, NB, MINB;
     void (*fn)(MixArgs);
+    void (*batch)(const MixArgs *, const BatchItem *, int64_t, unsigned long long *, const int32_t *);
 };
+#define MG_VARIANT(G, NB, M) {G, NB, M, k_feautrier_warp<G, NB, M>, k_feautrier_batch<G, NB, M>}
 const WarpVariant kWarpVariants[] = {
-    {1, 1, 8, k_feautrier_warp<1, 1, 8>}, {1, 1, 10, k_feautrier_warp<1, 1, 10>},
-    {2, 2, 4, k_feautrier_warp<2, 2, 4>}, {2, 2, 5, k_feautrier_warp<2, 2, 5>},
-    {2, 2, 6, k_feautrier_warp<2, 2, 6>}, {1, 2, 4, k_feautrier_warp<1, 2, 4>},
-    {1, 2, 6, k_feautrier_warp<1, 2, 6>}, {1, 4, 3, k_feautrier_warp<1, 4, 3>},
-    {1, 4, 4, k_feautrier_warp<1, 4, 4>},
+    MG_VARIANT(1, 1, 8), MG_VARIANT(1, 1, 10), MG_VARIANT(2, 2, 4), MG_VARIANT(2, 2, 5), MG_VARIANT(2, 2, 6),
+    MG_VARIANT(1, 2, 4), MG_VARIANT(1, 2, 6), MG_VARIANT(1, 4, 3), MG_VARIANT(1, 4, 4),
 };
+#undef MG_VARIANT
 constexpr int kNumWarpVariants = sizeof(kWarpVariants) / sizeof(kWarpVariants[0]);
 
 bool variant_valid(int v, int L, int Q) {
@@ -583,11 +631,9 @@ int mg_launch_line_data_mixed(mg_ctx *ctx) {
     return MG_OK;
 }
 
-static int launch_mixed(mg_ctx *ctx, int variant) {
+
+static void fill_args(mg_ctx *ctx, MixArgs &a) {
     const int L = ctx->n_lines, Q = ctx->Q;
-    bool overlap = false;
-    for (int l = 0; l < L; l++) overlap |= (ctx->h_ovl_off[l + 1] - ctx->h_ovl_off[l]) > 1;
-    MixArgs a{};
     a.n = ctx->n; a.R = ctx->R; a.P = ctx->P; a.L = L; a.Q = Q;
     a.pf = ctx->d_pf; a.pb = ctx->d_pb; a.ray_off = ctx->d_ray_off; a.cells = ctx->d_cells; a.xcum = ctx->d_xcum;
     a.ds = ctx->d_dsf; a.vpar = ctx->d_vparf; a.b = ctx->d_bf; a.line = ctx->d_linef;
@@ -599,6 +645,19 @@ static int launch_mixed(mg_ctx *ctx, int variant) {
     a.planck_b = (float)(kH * 1e9 / (kKB * ctx->opt.T_cmb));
     a.J = ctx->d_J; a.Lout = ctx->d_L; a.Jeff = ctx->d_Jeff; a.Lc = ctx->d_Lc;
     a.Jnu = ctx->opt.spectrum ? ctx->d_Jnu : nullptr;
+    a.kmax = (int32_t)ctx->max_pair_len;
+    a.err = ctx->d_err;
+    bool overlap = false;
+    for (int l = 0; l < L; l++) overlap |= (ctx->h_ovl_off[l + 1] - ctx->h_ovl_off[l]) > 1;
+    a.overlap = overlap;
+}
+
+static int launch_mixed(mg_ctx *ctx, int variant) {
+    const int L = ctx->n_lines, Q = ctx->Q;
+    bool overlap = false;
+    for (int l = 0; l < L; l++) overlap |= (ctx->h_ovl_off[l + 1] - ctx->h_ovl_off[l]) > 1;
+    MixArgs a{};
+    fill_args(ctx, a);
     a.kmax = (int32_t)ctx->max_pair_len;
     a.overlap = overlap;
     a.err = ctx->d_err;
@@ -678,4 +737,30 @@ int mg_autotune_mixed(mg_ctx *ctx, int reps, int *best, double *best_ms, int *n_
     if (best_ms) *best_ms = bms;
     if (n_tried) *n_tried = tried;
     return MG_OK;
+}
+
+// ---------------------------------------------------------------- batch helpers
+size_t mg_mixargs_size() { return sizeof(MixArgs); }
+
+int mg_fill_mixargs(mg_ctx *ctx, void *out) {
+    MixArgs a{};
+    fill_args(ctx, a);
+    if (a.overlap) return mg_fail(ctx, MG_ERR_ARG, "batch: models with overlapping lines are not batched");
+    std::memcpy(out, &a, sizeof(a));
+    return MG_OK;
+}
+
+int mg_variant_count() { return kNumWarpVariants; }
+int mg_variant_valid(int v, int L, int Q) { return variant_valid(v, L, Q) ? 1 : 0; }
+int mg_variant_minb(int v) { return (v >= 0 && v < kNumWarpVariants) ? kWarpVariants[v].MINB : 0; }
+int mg_variant_g(int v) { return (v >= 0 && v < kNumWarpVariants) ? kWarpVariants[v].G : 1; }
+int mg_variant_default(int L, int Q) { return default_variant(L, Q); }
+
+int mg_batch_launch(int v, int grid, const void *d_args, const void *d_items, int64_t n_items,
+                    unsigned long long *counter, const int32_t *active, cudaStream_t stream) {
+    if (v < 0 || v >= kNumWarpVariants) return MG_ERR_ARG;
+    kWarpVariants[v].batch<<<grid, 32 * kWarps2, 0, stream>>>(static_cast<const MixArgs *>(d_args),
+                                                               static_cast<const BatchItem *>(d_items), n_items,
+                                                               counter, active);
+    return cudaGetLastError() == cudaSuccess ? MG_OK : MG_ERR_CUDA;
 }

@@ -90,6 +90,7 @@ struct StateqArgs {
     const double *coll;      // [n][npairs][2]
     const double *nspec;
     unsigned long long *scal;   // [0] max change bits, [1] fallback count, [2] non-finite count
+    const int32_t *active;      // optional: skip the whole launch when *active == 0
 };
 
 // Rates u->l = A (1 - L) + B_ul Jeff + C_ul, l->u = B_lu Jeff + C_lu (eq. 'ourALI');
@@ -118,6 +119,7 @@ __device__ void build_rates(const StateqArgs &a, int64_t c, bool plain, double (
 
 template <int MAXLEV>
 __global__ void k_stateq(StateqArgs a) {
+    if (a.active && !*a.active) return;
     const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     double change = 0.0;
     unsigned long long fb = 0, bad = 0;
@@ -258,6 +260,21 @@ int mg_launch_stateq(mg_ctx *ctx) {
     }
     MG_CUDA(cudaGetLastError());
     std::swap(ctx->d_pops, ctx->d_pops_new);
+    return MG_OK;
+}
+
+// Statistical equilibrium from pops_old into pops_new with explicit buffers (no pointer
+// swap), skipped when *active == 0; used by the batch graph.
+int mg_launch_stateq_into(mg_ctx *ctx, const double *pops_old, double *pops_new, const int32_t *active) {
+    StateqArgs a{};
+    a.n = ctx->n; a.nlev = ctx->n_lev; a.L = ctx->n_lines; a.lc = ctx->d_lines;
+    a.pops = pops_old; a.pops_new = pops_new; a.J = ctx->d_J; a.Lc = ctx->d_Lc; a.Jeff = ctx->d_Jeff;
+    a.coll = ctx->d_coll; a.nspec = ctx->d_nspec; a.scal = ctx->d_scal; a.active = active;
+    const unsigned grid = (unsigned)((ctx->n + 127) / 128);
+    if (ctx->n_lev <= 8) k_stateq<8><<<grid, 128, 0, ctx->stream>>>(a);
+    else if (ctx->n_lev <= 24) k_stateq<24><<<grid, 128, 0, ctx->stream>>>(a);
+    else k_stateq<64><<<grid, 128, 0, ctx->stream>>>(a);
+    MG_CUDA(cudaGetLastError());
     return MG_OK;
 }
 

@@ -258,22 +258,28 @@ def model_clumpy_3d(seed=0, n=50_000, R=1e15, n_clumps=20, k=16, nside=2, n_q=31
 
 
 def model_disc(seed=0, n=200_000, r_in_au=10.0, r_out_au=200.0, k=16, nside=4, n_q=63,
-               n_lev=20, bdy_frac=0.02, n_h2_in=1e13, abundance=1e-4, T_in=100.0):
+               n_lev=20, bdy_frac=0.02, env_frac=0.1, n_h2_in=1e13, abundance=1e-4, T_in=100.0):
     """Flared Keplerian disc: n ~ r^-1 exp(-z^2/2H^2) with H = 0.1 r, T ~ r^-0.5,
     v = sqrt(G M_sun / r) phi_hat, boundary points on the bounding sphere, 20-level rotor."""
     rng = np.random.default_rng(seed)
     r_in, r_out = r_in_au * AU, r_out_au * AU
     n_b = max(12, int(round(bdy_frac * n)))
-    n_i = n - n_b
+    n_env = int(round(env_frac * n))
+    n_i = n - n_b - n_env
     # surface density ~ r^-1 * H ~ r^0 -> radius uniform in area weighting r dr: p(r) ~ r
     rr = np.sqrt(rng.uniform(r_in ** 2, (0.97 * r_out) ** 2, n_i))
     ph = rng.uniform(0, 2 * np.pi, n_i)
     z = rng.normal(size=n_i) * 0.1 * rr
     z = np.clip(z, -0.4 * rr, 0.4 * rr)
     pos_i = np.stack([rr * np.cos(ph), rr * np.sin(ph), z], 1)
-    pos = np.concatenate([pos_i, _fibonacci_sphere(n_b, r_out)])
+    # a sparse envelope filling the bounding sphere (the floor density), so that rays
+    # leaving the disc reach the boundary instead of ending at a dead end
+    d = rng.normal(size=(n_env, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    pos_e = d * (0.97 * r_out * rng.uniform(0, 1, (n_env, 1)) ** (1.0 / 3.0))
+    pos = np.concatenate([pos_i, pos_e, _fibonacci_sphere(n_b, r_out)])
     is_bdy = np.zeros(n, np.uint8)
-    is_bdy[n_i:] = 1
+    is_bdy[n_i + n_env:] = 1
     rc = np.maximum(np.hypot(pos[:, 0], pos[:, 1]), r_in)
     H = 0.1 * rc
     n_h2 = n_h2_in * (rc / r_in) ** -1 * np.exp(-0.5 * (pos[:, 2] / H) ** 2)

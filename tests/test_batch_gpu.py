@@ -1,0 +1,74 @@
+"""Batched models (uneven sizes, one persistent launch per iteration, CUDA graphs):
+identical to solving each model on its own, and within the mixed tolerance of the
+oracle."""
+import numpy as np
+import pytest
+
+import synthetic as syn
+from oracle import Oracle
+from helpers import rel_err, gpu_context
+
+pytestmark = pytest.mark.gpu
+
+
+def _models(k=6, seed=11):
+    rng = np.random.default_rng(seed)
+    sizes = np.exp(rng.uniform(np.log(600), np.log(4000), k)).astype(int)
+    return [syn.model_clumpy_3d(n=int(s), seed=seed * 100 + i, v_max=float(rng.uniform(2e3, 2e4)))
+            for i, s in enumerate(sizes)]
+
+
+def test_batch_formal_solve_matches_single_models():
+    import paper_1912_08445_gb300 as mg
+    ms = _models()
+    ctxs = []
+    for m in ms:
+        c = gpu_context(m, precision=1)
+        c.trace_rays()
+        c.init_populations()
+        ctxs.append(c)
+    refs = []
+    for c in ctxs:
+        c.formal_solve()
+        refs.append(c.get_radiation())
+    b = mg.Batch(ctxs)
+    b.formal_solve()
+    for c, (J, L, E) in zip(ctxs, refs):
+        J2, L2, E2 = c.get_radiation()
+        assert np.max(rel_err(J2, J)) < 1e-12
+        assert np.max(rel_err(E2, E)) < 1e-12
+        assert np.max(np.abs(L2 - L)) < 1e-12
+    v, srt, ms_ = b.autotune(reps=1)
+    assert v >= 0
+    # every model still within the mixed tolerance of the oracle after autotuning
+    o = Oracle(ms[1], nthreads=16)
+    origins = np.sort(np.random.default_rng(0).choice(ms[1].n, 20, replace=False))
+    Jo, Lo, Eo = o.formal_solve(o.lte(), origins)
+    J2, L2, E2 = ctxs[1].get_radiation()
+    assert np.max(rel_err(J2[origins], Jo)) < 1e-4
+    b.close()
+
+
+def test_batch_ali_matches_single_model_ali():
+    import paper_1912_08445_gb300 as mg
+    ms = _models(k=5, seed=12)
+    singles, batched = [], []
+    for m in ms:
+        c = gpu_context(m, precision=1, tol=1e-6, max_iter=100, ng_period=0)
+        c.trace_rays()
+        c.init_populations()
+        rep, rc = c.iterate()
+        singles.append((rep, c.get_populations()))
+    ctxs = []
+    for m in ms:
+        c = gpu_context(m, precision=1, tol=1e-6, max_iter=100, ng_period=0)
+        c.trace_rays()
+        c.init_populations()
+        ctxs.append(c)
+    b = mg.Batch(ctxs)
+    reps, rc = b.iterate()
+    assert rc == 0
+    for (rep, pops), r2, c in zip(singles, reps, ctxs):
+        assert r2["converged"] and r2["iterations"] == rep["iterations"]
+        assert np.max(rel_err(c.get_populations(), pops)) < 1e-12
+    b.close()
