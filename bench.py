@@ -332,6 +332,95 @@ def run_ali(args):
     print(json.dumps(out))
 
 
+# ------------------------------------------------------------------ other configurations
+def run_batch(args):
+    """Batched models: 64 independent clumpy clouds of 2k-40k points (seeded log-uniform
+    sizes, per-model outflow speeds so that ray lengths span ~10-400 points), mixed
+    precision. Reports the batched formal solve (one persistent launch after the line data
+    of every model) against a loop of per-model launches, and the batched ALI to 1e-6."""
+    import torch
+    import paper_1912_08445_gb300 as mg
+    import synthetic as syn
+    t0 = time.perf_counter()
+    models = syn.model_batch(seed=3, n_models=args.batch_models)
+    gen_s = time.perf_counter() - t0
+    ctxs = []
+    for m in models:
+        c = mg.Context(precision=mg.MG_MIXED, tol=1e-6, max_iter=100, ng_period=0)
+        c.load_model(m)
+        c.trace_rays()
+        c.init_populations()
+        ctxs.append(c)
+    b = mg.Batch(ctxs)
+    v, srt, tune_ms = b.autotune(reps=2)
+    solves, updates = b.work_counts()
+    torch.cuda.synchronize()
+    for _ in range(args.warmup):
+        b.formal_solve()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        b.formal_solve()
+    torch.cuda.synchronize()
+    batched = (time.perf_counter() - t0) / args.steps
+    for c in ctxs:
+        c.set_variant(v)
+    for _ in range(args.warmup):
+        for c in ctxs:
+            c.formal_solve()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        for c in ctxs:
+            c.formal_solve()
+    torch.cuda.synchronize()
+    looped = (time.perf_counter() - t0) / args.steps
+    for c in ctxs:
+        c.init_populations()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    reps, rc = b.iterate(allow_not_converged=True)
+    ali_s = time.perf_counter() - t0
+    its = [r["iterations"] for r in reps]
+    print(json.dumps({
+        "metric": METRIC, "unit": UNIT, "workload": f"{len(models)} clumpy clouds, "
+        f"{min(m.n for m in models)}-{max(m.n for m in models)} points, 48 rays, 4 lines x 31 bins",
+        "points_total": int(sum(m.n for m in models)), "solves_per_formal_solve": solves,
+        "cell_freq_updates": updates, "batched_value": solves / batched, "batched_ms": batched * 1e3,
+        "looped_value": solves / looped, "looped_ms": looped * 1e3, "variant": v, "queue_sorted": srt,
+        "ali_seconds": ali_s, "ali_iterations_min_max": [min(its), max(its)],
+        "ali_converged": int(sum(r["converged"] for r in reps)), "generation_s": gen_s}))
+
+
+def run_disc(args):
+    """Keplerian disc (200k points, 192 rays, 20-level rotor, 19 lines x 63 bins), mixed
+    precision: one ALI iteration per step."""
+    import torch
+    import paper_1912_08445_gb300 as mg
+    import synthetic as syn
+    m = syn.model_disc(n=args.disc_points, seed=0)
+    ctx = mg.Context(precision=mg.MG_MIXED, profile=1)
+    ctx.load_model(m)
+    t0 = time.perf_counter()
+    st, _ = ctx.trace_rays()
+    trace_s = time.perf_counter() - t0
+    ctx.init_populations()
+    v, tms, nt = ctx.autotune(reps=1)
+    solves, updates = ctx.work_counts()
+    ctx.reset_kernel_times()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        ctx.formal_solve()
+        ctx.update_populations()
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t0) / args.steps
+    kt = ctx.kernel_times()
+    print(json.dumps({"metric": METRIC, "unit": UNIT, "workload": "Keplerian disc, "
+                      f"{m.n} points, 192 rays, 20 levels, 19 lines x 63 bins", "value": solves / dt,
+                      "ms_per_step": dt * 1e3, "cell_freq_updates": updates, "variant": v,
+                      "trace_s": trace_s, "ray_stats": st, "kernel_ms": {k: v2[0] / max(v2[1], 1) for k, v2 in kt.items()}}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -341,10 +430,17 @@ def main():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--ali", action="store_true", help="measure ALI time to converge instead")
+    ap.add_argument("--workload", default="clumpy", choices=["clumpy", "batch", "disc"])
+    ap.add_argument("--batch-models", type=int, default=64)
+    ap.add_argument("--disc-points", type=int, default=200_000)
     ap.add_argument("--ali-precisions", default="mixed")
     ap.add_argument("--ali-max-iter", type=int, default=300)
     args = ap.parse_args()
-    if args.ali:
+    if args.workload == "batch":
+        run_batch(args)
+    elif args.workload == "disc":
+        run_disc(args)
+    elif args.ali:
         run_ali(args)
     elif args.impl == "reference":
         run_reference(args)
