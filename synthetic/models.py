@@ -221,7 +221,9 @@ def model_clumpy_3d(seed=0, n=50_000, R=1e15, n_clumps=20, k=16, nside=2, n_q=31
     else:
         n_b = max(12, int(round(bdy_frac * n)))
     n_i = n - n_b
-    cc = rng.uniform(-0.7, 0.7, (n_clumps, 3)) * R
+    cdir = rng.normal(size=(n_clumps, 3))
+    cdir /= np.linalg.norm(cdir, axis=1, keepdims=True)
+    cc = cdir * rng.uniform(0.0, 0.7, (n_clumps, 1)) * R
     cs = rng.uniform(0.02, 0.10, n_clumps) * R
     ca = np.exp(rng.uniform(np.log(1.0), np.log(100.0), n_clumps))
     n_clump_pts = int(0.3 * n_i)
@@ -236,10 +238,17 @@ def model_clumpy_3d(seed=0, n=50_000, R=1e15, n_clumps=20, k=16, nside=2, n_q=31
     cl = cc[which] + rng.normal(size=(n_clump_pts, 3)) * cs[which, None]
     rc = np.linalg.norm(cl, axis=1)
     bad = rc > 0.98 * R
-    while bad.any():
+    for _ in range(50):
+        if not bad.any():
+            break
         cl[bad] = cc[which[bad]] + rng.normal(size=(bad.sum(), 3)) * cs[which[bad], None]
         rc = np.linalg.norm(cl, axis=1)
         bad = rc > 0.98 * R
+    if bad.any():   # leftovers come from the background distribution
+        nb = int(bad.sum())
+        db = rng.normal(size=(nb, 3))
+        db /= np.linalg.norm(db, axis=1, keepdims=True)
+        cl[bad] = rng.uniform(0.01 * R, 0.98 * R, (nb, 1)) * db
     pos = np.concatenate([bg, cl, _fibonacci_sphere(n_b, R)])
     is_bdy = np.zeros(n, np.uint8)
     is_bdy[n_i:] = 1
