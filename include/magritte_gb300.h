@@ -260,6 +260,53 @@ int mg_batch_autotune(mg_batch *batch, int32_t reps, int32_t *variant, int32_t *
 /* Sum of mg_work_counts over the batch's models. */
 int mg_batch_work_counts(const mg_batch *batch, int64_t *solves, int64_t *cell_freq_updates);
 
+/* ---- Learned initial populations (an addition to the paper's method) ---------------
+ * A network maps four features of a cell -- log10 n_coll, log10 T, log10 |grad v| (the
+ * least-squares velocity gradient over the neighbours) and log10 of the Sobolev optical
+ * depth of line 0 at LTE -- to its log fractional level populations: 4 -> 128 -> 128 ->
+ * 128 -> n_out, ReLU, log-softmax. Inference and training run in hand-written kernels:
+ * BF16 tensor-core products (FP32 accumulation) for the 128-wide layers and the
+ * back-propagated deltas, FP32 weight gradients, Adam on FP32 master weights. The ALI
+ * from such a start converges to the same fixed point as from LTE. */
+typedef struct mg_mlp mg_mlp;
+typedef struct {
+    int32_t epochs;      /* passes over the rows                   */
+    int32_t batch;       /* rows per Adam step (>= 64)             */
+    float   lr;          /* Adam learning rate                     */
+    int32_t pad;
+    uint64_t seed;       /* row shuffling                          */
+} mg_train_opts;
+typedef struct {
+    double  first_loss;  /* mean loss of the first epoch           */
+    double  last_loss;   /* mean loss of the last epoch            */
+    int64_t steps;       /* Adam steps                             */
+    double  seconds;
+} mg_train_report;
+/* Creates a network with n_out outputs (2 <= n_out <= 32) on a device, He-uniform weights
+ * from seed. Parameters are one flat float vector: W1 [4][128], b1, W2 [128][128], b2,
+ * W3, b3, W4 [128][n_out], b4 (weights stored [in][out]). */
+int mg_mlp_create(mg_mlp **out, int32_t n_out, uint64_t seed, int32_t device);
+int mg_mlp_destroy(mg_mlp *mlp);
+const char *mg_mlp_last_error(const mg_mlp *mlp);
+int mg_mlp_param_count(const mg_mlp *mlp, int64_t *count);
+int mg_mlp_set_params(mg_mlp *mlp, const float *theta, int64_t count);   /* resets Adam */
+int mg_mlp_get_params(const mg_mlp *mlp, float *theta, int64_t count);
+/* Input normalisation f' = (f - mean)/std, mean[4], std[4] > 0. */
+int mg_mlp_set_normalisation(mg_mlp *mlp, const float *mean, const float *std);
+/* Host rows: X [rows][4] raw features -> logp [rows][n_out] log fractions. */
+int mg_mlp_forward(mg_mlp *mlp, int64_t rows, const float *X, float *logp);
+/* Loss (mean squared error of log fractions over targets Y >= 1e-12, Y [rows][n_out]
+ * fractions) and its gradient [param_count] (either may be NULL). */
+int mg_mlp_loss_grad(mg_mlp *mlp, int64_t rows, const float *X, const float *Y, double *loss, float *grad);
+/* Adam training on host rows (copied to the device once). */
+int mg_mlp_train(mg_mlp *mlp, int64_t rows, const float *X, const float *Y, const mg_train_opts *opts,
+                 mg_train_report *report);
+/* Features of every cell of a context, out [n][4]. */
+int mg_features(mg_ctx *ctx, float *out);
+/* Initial populations from the network (n_out must equal n_lev); cells whose output is
+ * not finite keep LTE populations (their count: mg_status_counts' fallback_cells). */
+int mg_init_populations_mlp(mg_ctx *ctx, mg_mlp *mlp);
+
 /* Kernel timing (opt.profile = 1): total milliseconds and launch counts per kernel
  * since the last reset, for up to cap kernels; names[i] points to static strings. */
 int mg_kernel_times(const mg_ctx *ctx, int32_t cap, const char **names, double *ms,

@@ -30,6 +30,16 @@ class mg_options(C.Structure):
                 ("spectrum", C.c_int32)]
 
 
+class mg_train_opts(C.Structure):
+    _fields_ = [("epochs", C.c_int32), ("batch", C.c_int32), ("lr", C.c_float), ("pad", C.c_int32),
+                ("seed", C.c_uint64)]
+
+
+class mg_train_report(C.Structure):
+    _fields_ = [("first_loss", C.c_double), ("last_loss", C.c_double), ("steps", C.c_int64),
+                ("seconds", C.c_double)]
+
+
 class mg_ray_stats(C.Structure):
     _fields_ = [("n_rays", C.c_int64), ("n_elements", C.c_int64), ("n_expanded", C.c_int64),
                 ("max_pair_len", C.c_int64), ("n_dead_end", C.c_int64), ("mean_pair_len", C.c_double)]
@@ -81,6 +91,18 @@ _SIGS = {
     "mg_work_counts": (C.c_int, [_P, _P, _P]),
     "mg_autotune": (C.c_int, [_P, C.c_int32, _P, _P, _P]),
     "mg_status_counts": (C.c_int, [_P, _P, _P]),
+    "mg_mlp_create": (C.c_int, [_P, C.c_int32, C.c_uint64, C.c_int32]),
+    "mg_mlp_destroy": (C.c_int, [_P]),
+    "mg_mlp_last_error": (C.c_char_p, [_P]),
+    "mg_mlp_param_count": (C.c_int, [_P, _P]),
+    "mg_mlp_set_params": (C.c_int, [_P, _P, C.c_int64]),
+    "mg_mlp_get_params": (C.c_int, [_P, _P, C.c_int64]),
+    "mg_mlp_set_normalisation": (C.c_int, [_P, _P, _P]),
+    "mg_mlp_forward": (C.c_int, [_P, C.c_int64, _P, _P]),
+    "mg_mlp_loss_grad": (C.c_int, [_P, C.c_int64, _P, _P, _P, _P]),
+    "mg_mlp_train": (C.c_int, [_P, C.c_int64, _P, _P, _P, _P]),
+    "mg_features": (C.c_int, [_P, _P]),
+    "mg_init_populations_mlp": (C.c_int, [_P, _P]),
     "mg_batch_create": (C.c_int, [_P, C.c_int32, _P]),
     "mg_batch_destroy": (C.c_int, [_P]),
     "mg_batch_last_error": (C.c_char_p, [_P]),
@@ -304,6 +326,14 @@ class Context:
         self._chk(self.lib.mg_status_counts(self.h, C.byref(f), C.byref(n)), "mg_status_counts")
         return f.value, n.value
 
+    def features(self):
+        out = np.empty((self.n, 4), np.float32)
+        self._chk(self.lib.mg_features(self.h, _ptr(out)), "mg_features")
+        return out
+
+    def init_populations_mlp(self, mlp):
+        self._chk(self.lib.mg_init_populations_mlp(self.h, mlp.h), "mg_init_populations_mlp")
+
     def autotune(self, reps=2):
         v = C.c_int32(0); ms = C.c_double(0); nt = C.c_int32(0)
         self._chk(self.lib.mg_autotune(self.h, int(reps), C.byref(v), C.byref(ms), C.byref(nt)), "mg_autotune")
@@ -383,3 +413,82 @@ class Batch:
         s = C.c_int64(0); u = C.c_int64(0)
         self._chk(self.lib.mg_batch_work_counts(self.h, C.byref(s), C.byref(u)), "mg_batch_work_counts")
         return s.value, u.value
+
+
+class MLP:
+    """Owns one mg_mlp (learned initial populations)."""
+
+    def __init__(self, n_out, seed=0, device=0):
+        self.lib = load()
+        h = C.c_void_p()
+        rc = self.lib.mg_mlp_create(C.byref(h), int(n_out), int(seed), int(device))
+        if rc != MG_OK:
+            raise MagritteError(rc, "mg_mlp_create failed")
+        self.h = h
+        self.n_out = int(n_out)
+        c = C.c_int64(0)
+        self.lib.mg_mlp_param_count(self.h, C.byref(c))
+        self.n_params = c.value
+
+    def _chk(self, rc, what):
+        if rc < 0:
+            msg = self.lib.mg_mlp_last_error(self.h)
+            raise MagritteError(rc, f"{what}: {msg.decode() if msg else ''}")
+        return rc
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.mg_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def get_params(self):
+        t = np.empty(self.n_params, np.float32)
+        self._chk(self.lib.mg_mlp_get_params(self.h, _ptr(t), self.n_params), "mg_mlp_get_params")
+        return t
+
+    def set_params(self, theta):
+        t = _c(theta, np.float32)
+        self._chk(self.lib.mg_mlp_set_params(self.h, _ptr(t), t.size), "mg_mlp_set_params")
+
+    def set_normalisation(self, mean, std):
+        m, s = _c(mean, np.float32), _c(std, np.float32)
+        self.mean, self.std = m, s
+        self._chk(self.lib.mg_mlp_set_normalisation(self.h, _ptr(m), _ptr(s)), "mg_mlp_set_normalisation")
+
+    def forward(self, X):
+        X = _c(X, np.float32)
+        out = np.empty((X.shape[0], self.n_out), np.float32)
+        self._chk(self.lib.mg_mlp_forward(self.h, X.shape[0], _ptr(X), _ptr(out)), "mg_mlp_forward")
+        return out
+
+    def loss_grad(self, X, Y):
+        X, Y = _c(X, np.float32), _c(Y, np.float32)
+        loss = C.c_double(0)
+        g = np.empty(self.n_params, np.float32)
+        self._chk(self.lib.mg_mlp_loss_grad(self.h, X.shape[0], _ptr(X), _ptr(Y), C.byref(loss), _ptr(g)),
+                  "mg_mlp_loss_grad")
+        return loss.value, g
+
+    def train(self, X, Y, epochs=10, batch=4096, lr=1e-3, seed=0):
+        X, Y = _c(X, np.float32), _c(Y, np.float32)
+        o = mg_train_opts(epochs=epochs, batch=batch, lr=lr, seed=seed)
+        r = mg_train_report()
+        self._chk(self.lib.mg_mlp_train(self.h, X.shape[0], _ptr(X), _ptr(Y), C.byref(o), C.byref(r)), "mg_mlp_train")
+        return {k: getattr(r, k) for k, _ in r._fields_}
+
+    def save(self, path):
+        np.savez(path, theta=self.get_params(), mean=self.mean, std=self.std, n_out=self.n_out)
+
+    @classmethod
+    def load(cls, path, device=0):
+        d = np.load(path)
+        m = cls(int(d["n_out"]), device=device)
+        m.set_params(d["theta"])
+        m.set_normalisation(d["mean"], d["std"])
+        return m
