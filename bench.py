@@ -421,6 +421,57 @@ def run_disc(args):
                       "trace_s": trace_s, "ray_stats": st, "kernel_ms": {k: v2[0] / max(v2[1], 1) for k, v2 in kt.items()}}))
 
 
+def run_learned(args):
+    """Learned initial populations (20-level rotor): trains the network on converged
+    populations of seeded cloud/disc models, then compares on held-out seeds the ALI to
+    1e-6 from the network's start (mixed precision) with the LTE start (mixed) and with
+    the plain FP64 ALI from LTE, on the same GPU (Ng off and on)."""
+    import numpy as np
+    import torch
+    import paper_1912_08445_gb300 as mg
+    import synthetic as syn
+    from paper_1912_08445_gb300 import learned
+    sp = syn.species_rotor(20, np.random.default_rng(77))
+    t0 = time.perf_counter()
+    train = learned.corpus_models(args.corpus, 1000, n_points=args.corpus_points, species=sp)
+    X, Y, reps = learned.build_corpus(train, ng_period=4)
+    corpus_s = time.perf_counter() - t0
+    net, trep = learned.train_network(X, Y, 20, epochs=args.epochs, batch=4096, lr=2e-3)
+    held = learned.corpus_models(10, 5000, n_points=args.corpus_points, species=sp)
+    rows = []
+    for m in held:
+        for ng in (0, 4):
+            rec = {"n": m.n, "shape": m.name, "ng_period": ng}
+            for name, prec, start in (("fp64_lte", mg.MG_FP64, "lte"), ("mixed_lte", mg.MG_MIXED, "lte"),
+                                      ("mixed_mlp", mg.MG_MIXED, "mlp")):
+                ctx = mg.Context(precision=prec, tol=1e-6, max_iter=400, ng_period=ng)
+                ctx.load_model(m)
+                ctx.trace_rays()
+                torch.cuda.synchronize()
+                t1 = time.perf_counter()
+                if start == "lte":
+                    ctx.init_populations()
+                else:
+                    ctx.init_populations_mlp(net)
+                rep, rc = ctx.iterate(allow_not_converged=True)
+                torch.cuda.synchronize()
+                rec[name] = {"seconds": time.perf_counter() - t1, "iterations": rep["iterations"],
+                             "converged": bool(rep["converged"])}
+                ctx.close()
+            rows.append(rec)
+    summ = {}
+    for ng in (0, 4):
+        sel = [r for r in rows if r["ng_period"] == ng]
+        for name in ("fp64_lte", "mixed_lte", "mixed_mlp"):
+            summ[f"{name}_ng{ng}"] = {"mean_seconds": float(np.mean([r[name]["seconds"] for r in sel])),
+                                      "mean_iterations": float(np.mean([r[name]["iterations"] for r in sel])),
+                                      "all_converged": all(r[name]["converged"] for r in sel)}
+    print(json.dumps({"metric": "ALI time to converge (1e-6), held-out seeds", "unit": "s", "higher_is_better": False,
+                      "workload": f"20-level rotor, cloud/disc models of {args.corpus_points} points, 48 rays, 19 lines x 31 bins",
+                      "corpus_models": len(train), "corpus_rows": int(X.shape[0]), "corpus_seconds": corpus_s,
+                      "training": trep, "summary": summ, "runs": rows}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -430,7 +481,10 @@ def main():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--ali", action="store_true", help="measure ALI time to converge instead")
-    ap.add_argument("--workload", default="clumpy", choices=["clumpy", "batch", "disc"])
+    ap.add_argument("--workload", default="clumpy", choices=["clumpy", "batch", "disc", "learned"])
+    ap.add_argument("--corpus", type=int, default=200)
+    ap.add_argument("--corpus-points", type=int, default=3000)
+    ap.add_argument("--epochs", type=int, default=30)
     ap.add_argument("--batch-models", type=int, default=64)
     ap.add_argument("--disc-points", type=int, default=200_000)
     ap.add_argument("--ali-precisions", default="mixed")
@@ -440,6 +494,8 @@ def main():
         run_batch(args)
     elif args.workload == "disc":
         run_disc(args)
+    elif args.workload == "learned":
+        run_learned(args)
     elif args.ali:
         run_ali(args)
     elif args.impl == "reference":

@@ -41,3 +41,23 @@ def train_network(X, Y, n_lev, epochs=30, batch=4096, lr=2e-3, seed=0, device=0)
     net.set_normalisation(mean, std)
     rep = net.train(X, Y, epochs=epochs, batch=batch, lr=lr, seed=seed)
     return net, rep
+
+
+def corpus_models(n_models, seed0, n_points=3000, species=None):
+    """Seeded cloud/disc models of the given species (alternating shapes of the clumpy
+    cloud and the Keplerian disc, scaled down), densities and abundances log-uniform."""
+    import synthetic as syn
+    out = []
+    for k in range(n_models):
+        rng = np.random.default_rng(seed0 + k)
+        dens = float(np.exp(rng.uniform(np.log(1e8), np.log(1e11))))
+        X = float(np.exp(rng.uniform(np.log(1e-7), np.log(1e-5))))
+        if k % 2 == 0:
+            m = syn.model_clumpy_3d(n=n_points, seed=seed0 + k, n_h2_ref=dens, abundance=X, species=species,
+                                    v_max=float(rng.uniform(2e3, 2e4)))
+        else:
+            m = syn.model_disc(n=n_points, seed=seed0 + k, nside=2, n_q=31, n_lev=species.n_lev,
+                               n_h2_in=dens * 100, abundance=X)
+            m.species = species
+        out.append(m)
+    return out

@@ -88,10 +88,12 @@ def species_two_level(A21=1.0e-4, K21=2.0e-16, dE_cm=6.0, g_ratio=3.0, mass_amu=
 
 
 def species_rotor(n_lev, rng, mass_amu=28.0, B_range=(40e9, 60e9), A1_scale=1e-7,
-                  a_range=(1e-17, 1e-16), b_range=(0.0, 0.5)):
+                  a_range=(1e-17, 1e-16), b_range=(0.0, 0.5), dj_decay=10.0):
     """Seeded linear-rotor ladder: E_J = h B J(J+1), g_J = 2J+1, radiative lines
     J -> J-1 with A_J = A_1 J^3, and de-excitation coefficients for every pair J > J'
-    K(T) = a (T / 100 K)^b / (J - J') tabulated on a temperature grid."""
+    K(T) = a (T / 100 K)^b / dj_decay^(J - J' - 1) tabulated on a temperature grid.
+    Collisions are dominated by Delta J = 1: with strong Delta J >= 2 excitation the fast
+    radiative cascade (A ~ J^3) inverts the lowest line at low density (a maser)."""
     h = CODATA["h"]
     B = rng.uniform(*B_range)
     J = np.arange(n_lev, dtype=np.float64)
@@ -107,7 +109,7 @@ def species_rotor(n_lev, rng, mass_amu=28.0, B_range=(40e9, 60e9), A1_scale=1e-7
     rows = []
     for i in range(1, n_lev):
         for j in range(i):
-            rows.append(a * (T_grid / 100.0) ** b / (i - j))
+            rows.append(a * (T_grid / 100.0) ** b / dj_decay ** (i - j - 1))
     return Species(E=E, g=g, mass=mass_amu * CODATA["amu"], up=up, lo=lo, A=A,
                    T_grid=T_grid, K_down=np.array(rows))
 
