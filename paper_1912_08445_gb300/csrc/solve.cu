@@ -51,30 +51,36 @@ __device__ __forceinline__ double planck_d(double nu, double T) {
     return 2.0 * kH * nu * nu * nu / (kC * kC) / expm1(kH * nu / (kKB * T));
 }
 
-// Stages the expanded points of half-ray (o, r) into the pair arrays. Point x of the
-// half (0 = nearest the origin) sits at pair index base + dir * x; its path length to the
-// neighbouring point towards the origin goes to ds slot (dir < 0 ? idx : idx - 1).
-__device__ void stage_half64(const SolveArgs &a, int64_t o, int r, int base, int dir, double *s_ds, double *s_v,
-                             double *s_b, double *s_line) {
-    const int L = a.L;
+// Stages the expanded points of half-ray (o, r) into the pair arrays: per point the path
+// length to the neighbouring point towards the origin, the line-of-sight velocity, the
+// width, and the two cells and weight that interpolate its line data (read from global
+// memory during the sweep). Point x of the half (0 = nearest the origin) sits at pair
+// index base + dir x; its path length goes to ds slot (dir < 0 ? idx : idx - 1).
+struct PairSmem64 {
+    double *ds, *v, *b, *w;
+    int32_t *ca, *cb;
+};
+
+__device__ void stage_half64(const SolveArgs &a, int64_t o, int r, int base, int dir, const PairSmem64 &S) {
     const int64_t off = a.ray_off[o * a.R + r];
     const int len = (int)(a.ray_off[o * a.R + r + 1] - off);
     for (int e = threadIdx.x; e < len; e += blockDim.x) {
-        const int64_t c = a.cells[off + e];
-        const int64_t prev = e ? a.cells[off + e - 1] : o;
+        const int32_t c = a.cells[off + e];
+        const int32_t prev = e ? a.cells[off + e - 1] : (int32_t)o;
         const int x0 = e ? a.xcum[off + e - 1] : 0;
         const int ns = a.xcum[off + e] - x0 - 1;
         const double pv = e ? a.vpar[off + e - 1] : 0.0;
         const double ve = a.vpar[off + e], dse = a.ds[off + e];
         const double bp = a.b[prev], bc = a.b[c];
-        const double *lp = a.line + prev * 2 * L, *lcur = a.line + c * 2 * L;
         for (int j = 1; j <= ns + 1; j++) {
             const double w = (double)j / (double)(ns + 1);
             const int idx = base + dir * (x0 + j - 1);
-            s_ds[dir < 0 ? idx : idx - 1] = dse / (double)(ns + 1);
-            s_v[idx] = (1.0 - w) * pv + w * ve;
-            s_b[idx] = (1.0 - w) * bp + w * bc;
-            for (int k = 0; k < 2 * L; k++) s_line[idx * 2 * L + k] = (1.0 - w) * lp[k] + w * lcur[k];
+            S.ds[dir < 0 ? idx : idx - 1] = dse / (double)(ns + 1);
+            S.v[idx] = (1.0 - w) * pv + w * ve;
+            S.b[idx] = (1.0 - w) * bp + w * bc;
+            S.w[idx] = w;
+            S.ca[idx] = prev;
+            S.cb[idx] = c;
         }
     }
 }
@@ -84,9 +90,9 @@ struct Pt64 {
     double chi, eta, chil, etal;
 };
 
-__device__ __forceinline__ Pt64 point64(const SolveArgs &a, int l, double aq, int k, const double *s_v,
-                                        const double *s_b, const double *s_line) {
-    const double v = s_v[k], bk = s_b[k];
+__device__ __forceinline__ Pt64 point64(const SolveArgs &a, int l, double aq, int k, const PairSmem64 &S) {
+    const double v = S.v[k], bk = S.b[k], w = S.w[k];
+    const double *pa = a.line + (int64_t)S.ca[k] * 2 * a.L, *pb = a.line + (int64_t)S.cb[k] * 2 * a.L;
     const double ibk = 1.0 / bk;
     Pt64 p{0.0, 0.0, 0.0, 0.0};
     const int o0 = a.ovl_off[l], o1 = a.ovl_off[l + 1];
@@ -95,8 +101,8 @@ __device__ __forceinline__ Pt64 point64(const SolveArgs &a, int l, double aq, in
         const Overlap ov = a.ovl[i];
         const double x = (ov.dnl + ov.rat * base) * ibk;
         const double phi = exp(-x * x) * kC * ov.inv_nu2 * ibk / kSqrtPi;
-        const double et = s_line[k * 2 * a.L + 2 * ov.l2] * phi;
-        const double ch = s_line[k * 2 * a.L + 2 * ov.l2 + 1] * phi;
+        const double et = ((1.0 - w) * pa[2 * ov.l2] + w * pb[2 * ov.l2]) * phi;
+        const double ch = ((1.0 - w) * pa[2 * ov.l2 + 1] + w * pb[2 * ov.l2 + 1]) * phi;
         p.eta += et;
         p.chi += ch;
         if (i == o0) { p.etal = et; p.chil = ch; }
@@ -122,20 +128,19 @@ struct Side64 {
 };
 
 __device__ __forceinline__ Side64 sweep64(const SolveArgs &a, int l, double aq, double nu_o, int kstart, int kend,
-                                          int step, const double *s_ds, const double *s_v, const double *s_b,
-                                          const double *s_line, Pt64 &po) {
+                                          int step, const PairSmem64 &S, Pt64 &po) {
     // kstart: far end, kend: origin; step = +1 (backward half) or -1 (forward half)
-    Pt64 p = point64(a, l, aq, kstart, s_v, s_b, s_line);
+    Pt64 p = point64(a, l, aq, kstart, S);
     double chi_prev = fmax(p.chi, a.chi_min);
     double S_prev = p.eta / chi_prev;
-    const double I = planck_d(nu_o * (1.0 - s_v[kstart] / kC), a.T_cmb);
+    const double I = planck_d(nu_o * (1.0 - S.v[kstart] / kC), a.T_cmb);
     double Phi = 0.0, iota = 0.0, psi = 0.0, dt_prev = 0.0;
     int row = 0;
     for (int k = kstart + step;; k += step) {
-        Pt64 q = point64(a, l, aq, k, s_v, s_b, s_line);
+        Pt64 q = point64(a, l, aq, k, S);
         const double chi = fmax(q.chi, a.chi_min);
-        const double S = q.eta / chi;
-        const double dsk = s_ds[step > 0 ? k - 1 : k];
+        const double Sk = q.eta / chi;
+        const double dsk = S.ds[step > 0 ? k - 1 : k];
         const double dt = fmax(0.5 * (chi_prev + chi) * dsk, a.dtau_min);
         if (row == 0) {
             Phi = 0.5 * dt + 1.0;
@@ -150,7 +155,7 @@ __device__ __forceinline__ Side64 sweep64(const SolveArgs &a, int l, double aq, 
         row++;
         dt_prev = dt;
         chi_prev = chi;
-        S_prev = S;
+        S_prev = Sk;
         if (k == kend) {
             q.chi = chi;
             po = q;
@@ -164,11 +169,14 @@ __global__ void k_feautrier64(SolveArgs a) {
     extern __shared__ double smem[];
     const int L = a.L, Q = a.Q, F = L * Q;
     const int kmax = a.kmax;
-    double *s_ds = smem;
-    double *s_v = s_ds + kmax;
-    double *s_b = s_v + kmax;
-    double *s_line = s_b + kmax;
-    double *acc = s_line + (size_t)kmax * 2 * L;   // [F][4]
+    PairSmem64 S;
+    S.ds = smem;
+    S.v = S.ds + kmax;
+    S.b = S.v + kmax;
+    S.w = S.b + kmax;
+    double *acc = S.w + kmax;   // [F][4]
+    S.ca = reinterpret_cast<int32_t *>(acc + 4 * F);
+    S.cb = S.ca + kmax;
     const int64_t o = blockIdx.x;
     for (int f = threadIdx.x; f < 4 * F; f += blockDim.x) acc[f] = 0.0;
     const double bo = a.b[o];
@@ -185,13 +193,15 @@ __global__ void k_feautrier64(SolveArgs a) {
             continue;
         }
         __syncthreads();
-        stage_half64(a, o, rb, Kb - 1, -1, s_ds, s_v, s_b, s_line);
-        stage_half64(a, o, rf, Kb + 1, +1, s_ds, s_v, s_b, s_line);
+        stage_half64(a, o, rb, Kb - 1, -1, S);
+        stage_half64(a, o, rf, Kb + 1, +1, S);
         if (threadIdx.x == 0) {
-            s_v[Kb] = 0.0;
-            s_b[Kb] = bo;
+            S.v[Kb] = 0.0;
+            S.b[Kb] = bo;
+            S.w[Kb] = 0.0;
+            S.ca[Kb] = (int32_t)o;
+            S.cb[Kb] = (int32_t)o;
         }
-        for (int k = threadIdx.x; k < 2 * L; k += blockDim.x) s_line[Kb * 2 * L + k] = a.line[o * 2 * L + k];
         __syncthreads();
         for (int f = threadIdx.x; f < F; f += blockDim.x) {
             const int l = f / Q, q = f - l * Q;
@@ -203,11 +213,11 @@ __global__ void k_feautrier64(SolveArgs a) {
             if (K == 1) {
                 const double I = planck_d(nu_o, a.T_cmb);
                 u = I; lam = 0.0; uml = I; oml = 1.0;
-                po = point64(a, l, aq, Kb, s_v, s_b, s_line);
+                po = point64(a, l, aq, Kb, S);
                 po.chi = fmax(po.chi, a.chi_min);
             } else {
-                if (Kb > 0) sb = sweep64(a, l, aq, nu_o, 0, Kb, +1, s_ds, s_v, s_b, s_line, po);
-                if (Kf > 0) sf = sweep64(a, l, aq, nu_o, K - 1, Kb, -1, s_ds, s_v, s_b, s_line, po);
+                if (Kb > 0) sb = sweep64(a, l, aq, nu_o, 0, Kb, +1, S, po);
+                if (Kf > 0) sf = sweep64(a, l, aq, nu_o, K - 1, Kb, -1, S, po);
                 if (Kb == 0 || Kf == 0) {
                     const double Io = planck_d(nu_o, a.T_cmb);
                     if (Kb == 0) sb = Side64{1.0, Io, 0.0};
@@ -271,7 +281,7 @@ int mg_launch_feautrier(mg_ctx *ctx) {
     a.kmax = (int32_t)ctx->max_pair_len;
     a.err = ctx->d_err;
     const int F = a.L * a.Q;
-    size_t smem = sizeof(double) * ((size_t)a.kmax * (3 + 2 * a.L) + 4 * (size_t)F);
+    size_t smem = sizeof(double) * ((size_t)a.kmax * 4 + 4 * (size_t)F) + sizeof(int32_t) * 2 * (size_t)a.kmax;
     if (smem > 227 * 1024)
         return mg_fail(ctx, MG_ERR_CAPACITY, "FP64 formal solve: longest ray pair does not fit in shared memory");
     MG_CUDA(cudaFuncSetAttribute(k_feautrier64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
