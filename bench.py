@@ -100,6 +100,22 @@ class Clocks:
         return out
 
 
+def reduce_max(values, device="cpu"):
+    """Element-wise maximum of per-rank timings over all ranks (identity for one rank)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor(list(values), dtype=torch.float64, device=device)
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t.tolist()]
+
+
+def whole_job_rate(units_per_rank, steps, world_size, ms_max):
+    """Units processed by all ranks divided by the slowest rank's time (weak scaling:
+    every rank solves its own model)."""
+    return world_size * units_per_rank * steps / (ms_max * 1e-3)
+
+
 def build_model(seed):
     import synthetic as syn
     return syn.model_clumpy_3d(n=WORKLOAD["n_points"], seed=seed)
@@ -210,11 +226,9 @@ def run_gpu(args):
         torch.cuda.synchronize()
         e2e_s = time.perf_counter() - t0
 
-    t = torch.tensor([ms, e2e_s * 1e3], dtype=torch.float64, device=f"cuda:{local}")
+    ms_max, e2e_ms_max = reduce_max([ms, e2e_s * 1e3], device=f"cuda:{local}")
     if ws > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
         dist.barrier()
-    ms_max, e2e_ms_max = float(t[0]), float(t[1])
 
     if rank == 0:
         pk, pk_kind = peaks()
@@ -238,7 +252,7 @@ def run_gpu(args):
                 "cell_freq_updates_per_launch": updates,
                 "hbm_algorithmic_frac_of_measured": None}
         cpu_v, cores, sample = time_oracle(model) if args.cpu_baseline else (None, None, None)
-        value = ws * solves * args.steps / (ms_max * 1e-3)
+        value = whole_job_rate(solves, args.steps, ws, ms_max)
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
@@ -249,7 +263,7 @@ def run_gpu(args):
                            parallelism=f"replicas x{ws}", solves_per_step=solves,
                            cell_freq_updates_per_step=updates, mean_pair_len=round(st["mean_pair_len"], 1),
                            launch_variant=tuned[0], variants_tried=tuned[2]),
-            "e2e": {"value": ws * solves * args.steps / (e2e_ms_max * 1e-3), "unit": UNIT,
+            "e2e": {"value": whole_job_rate(solves, args.steps, ws, e2e_ms_max), "unit": UNIT,
                     "h2d_bytes_per_step": n * lev * 8, "d2h_bytes_per_step": n * lev * 8},
             "gpu_launches": 3 * args.steps,
             "clocks": clk,
