@@ -79,7 +79,7 @@ typedef struct {
 } mg_options;
 
 /* Fills *opt with defaults: MG_FP64, device 0, tol 1e-6, max_iter 300, ng_period 4,
- * dshift_frac 1/3, chi_min 1e-30, dtau_min 1e-12, T_cmb 2.725, line_cut 7.5,
+ * dshift_frac 1/3, chi_min 1e-30, dtau_min 1e-30, T_cmb 2.725, line_cut 7.5,
  * max_steps 100000, profile 0, spectrum 0. */
 void mg_default_options(mg_options *opt);
 

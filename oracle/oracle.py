@@ -177,7 +177,7 @@ class Oracle:
     """FP64 oracle bound to one synthetic model (``synthetic.Model``)."""
 
     def __init__(self, model, dirs=None, Q=None, dshift_frac=1.0 / 3.0, chi_min=1e-30,
-                 dtau_min=1e-12, T_cmb=2.725, max_steps=100000, nthreads=0):
+                 dtau_min=1e-30, T_cmb=2.725, max_steps=100000, nthreads=0):
         self.model = model
         sp = model.species
         if dirs is None:

@@ -49,7 +49,7 @@ extern "C" void mg_default_options(mg_options *o) {
     o->ng_period = 4;
     o->dshift_frac = 1.0 / 3.0;
     o->chi_min = 1e-30;
-    o->dtau_min = 1e-12;
+    o->dtau_min = 1e-30;
     o->T_cmb = 2.725;
     o->line_cut = 7.5;
     o->max_steps = 100000;
