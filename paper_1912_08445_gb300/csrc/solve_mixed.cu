@@ -329,9 +329,13 @@ struct RingGeom {
     float4 g;
 };
 
+// A point is "far" for the warp when every bin of the warp lies so far in the wings of
+// every line of its group that the opacity is floored there: X 2^(-x'^2) < chi_min with
+// x' = a_q g.z - g.y over the warp's range of a_q (monotonic in a_q, so the smallest
+// |x'| is at an end of the range or zero). Flagged in g.w.
 template <int G>
 __device__ __forceinline__ void stage_ring_point(const MixArgs &a, int64_t o, int l0, int64_t off, int x, int &e,
-                                                 float4 &g, float2 (&ln)[G]) {
+                                                 float4 &g, float2 (&ln)[G], float aq_lo, float aq_hi) {
     while (e > 0 && a.xcum[off + e - 1] > x) e--;
     const int x0 = e ? a.xcum[off + e - 1] : 0;
     const int ns = a.xcum[off + e] - x0 - 1;
@@ -345,6 +349,10 @@ __device__ __forceinline__ void stage_ring_point(const MixArgs &a, int64_t o, in
     const float ib = 1.0f / bb;
     const float pz = kSqrtLog2e * ib;
     g = make_float4(qds, v * pz, (1.0f - v * (float)(1.0 / kC)) * pz, 0.0f);
+    const float xlo = aq_lo * g.z - g.y, xhi = aq_hi * g.z - g.y;
+    const float xm = xlo > 0.0f ? xlo : (xhi < 0.0f ? -xhi : 0.0f);
+    const float wing = ex2f(-xm * xm);
+    bool far = true;
 #pragma unroll
     for (int k = 0; k < G; k++) {
         const int l = l0 + k < a.L ? l0 + k : a.L - 1;
@@ -353,7 +361,9 @@ __device__ __forceinline__ void stage_ring_point(const MixArgs &a, int64_t o, in
         const float et = (1.0f - w) * p0.x + w * p1.x;
         const float ch = (1.0f - w) * p0.y + w * p1.y;
         ln[k] = make_float2(fmaxf(ch, 0.0f) * a.kline[l] * ib, ch > 0.0f ? et / ch : 0.0f);
+        far = far && (ln[k].x * wing < a.chi_min);
     }
+    g.w = far ? 1.0f : 0.0f;
 }
 
 // Per-bin sweep state in the variables delta = dtau/sqrt 2, Phi^ = sqrt 2 Phi and
@@ -410,10 +420,11 @@ __device__ __forceinline__ void step_point(const SweepK &a, BinState<NB> &st, co
 
 // Sweeps half-ray r from its far end to the origin; returns per bin (Phi^ iota, psi^,
 // delta) of the row next to the origin, or the empty-half values (sqrt 2, sqrt 2 I_o, 0).
-template <int G, int NB>
+template <int G, int NB, bool SKIP>
 __device__ __forceinline__ void sweep_half(const MixArgs &a, const SweepK &k, int64_t o, int l0, int grp, int r,
                                            float nu_g, const float4 go, const float2 dlo, RingGeom *rg, float2 *rl,
-                                           BinState<NB> &st, float (&pi)[NB], float (&ps)[NB], float (&dt)[NB]) {
+                                           BinState<NB> &st, float (&pi)[NB], float (&ps)[NB], float (&dt)[NB],
+                                           float aq_lo, float aq_hi) {
     const int lane = threadIdx.x & 31;
     const int64_t off = a.ray_off[o * a.R + r];
     const int len = (int)(a.ray_off[o * a.R + r + 1] - off);
@@ -431,7 +442,7 @@ __device__ __forceinline__ void sweep_half(const MixArgs &a, const SweepK &k, in
     int anchor = len - 1;      // element holding the next point to stage
     int xnext = Kh - 1;        // next point to stage (descending towards the origin)
     float qds_p = 0.0f;
-    bool first = true;
+    bool first = true, far1 = false, far2 = false;
     while (xnext >= 0) {
         const int cnt = min(kRing, xnext + 1);
         __syncwarp();
@@ -439,7 +450,7 @@ __device__ __forceinline__ void sweep_half(const MixArgs &a, const SweepK &k, in
         if (lane < cnt) {
             float4 g;
             float2 ln[G];
-            stage_ring_point<G>(a, o, l0, off, xnext - lane, e, g, ln);
+            stage_ring_point<G>(a, o, l0, off, xnext - lane, e, g, ln, aq_lo, aq_hi);
             rg[lane].g = g;
 #pragma unroll
             for (int k = 0; k < G; k++) rl[k * kRing + lane] = ln[k];
@@ -452,14 +463,30 @@ __device__ __forceinline__ void sweep_half(const MixArgs &a, const SweepK &k, in
             const float vfar = g.y / (g.z + g.y * (float)(1.0 / kC));   // v = (v pz)/pz
             first_point<NB>(k, st, g, my[0], nu_g, vfar);
             qds_p = g.x;
+            far1 = false;
+            far2 = false;
             j = 1;
             first = false;
         }
+        if (SKIP) {
+            // A point whose own and two previous points are all far changes the state by
+            // O(chi_min ds) only (no-ops in FP32): rows that involve a non-floored interval
+            // are still computed exactly.
+            for (; j < cnt; j++) {
+                const float4 g = rg[j].g;
+                const bool far = g.w != 0.0f;
+                if (!(far && far1 && far2)) step_point<NB>(k, st, g, my[j], qds_p);
+                qds_p = g.x;
+                far2 = far1;
+                far1 = far;
+            }
+        } else {
 #pragma unroll 4
-        for (; j < cnt; j++) {
-            const float4 g = rg[j].g;
-            step_point<NB>(k, st, g, my[j], qds_p);
-            qds_p = g.x;
+            for (; j < cnt; j++) {
+                const float4 g = rg[j].g;
+                step_point<NB>(k, st, g, my[j], qds_p);
+                qds_p = g.x;
+            }
         }
         xnext -= cnt;
     }
@@ -473,7 +500,7 @@ __device__ __forceinline__ void sweep_half(const MixArgs &a, const SweepK &k, in
 }
 
 // One work item: origin o, lines l0 .. l0+G-1, all ray pairs, all bins (one warp).
-template <int G, int NB>
+template <int G, int NB, bool SKIP>
 __device__ __forceinline__ void solve_item(const MixArgs &a, int64_t o, int l0, RingGeom *rg, float2 *rl) {
     constexpr int LPG = 32 / G;   // lanes per line
     const int lane = threadIdx.x & 31;
@@ -503,10 +530,21 @@ __device__ __forceinline__ void solve_item(const MixArgs &a, int64_t o, int l0, 
         chio[i] = fmaxf(chil, a.chi_min);
         Sov[i] = fminf(dlo.y, chil * dlo.y * a.inv_chi_min);
     }
+    // range of a_q over the whole warp (all lanes, all bins)
+    float aq_lo = 1e30f, aq_hi = -1e30f;
+#pragma unroll
+    for (int i = 0; i < NB; i++) {
+        const int q = li + LPG * i;
+        if (q < Q) { aq_lo = fminf(aq_lo, st.aq[i]); aq_hi = fmaxf(aq_hi, st.aq[i]); }
+    }
+    for (int d = 16; d; d >>= 1) {
+        aq_lo = fminf(aq_lo, __shfl_xor_sync(0xffffffffu, aq_lo, d));
+        aq_hi = fmaxf(aq_hi, __shfl_xor_sync(0xffffffffu, aq_hi, d));
+    }
     for (int p = 0; p < a.P; p++) {
         float pib[NB], psb[NB], dtb[NB], pif[NB], psf[NB], dtf[NB];
-        sweep_half<G, NB>(a, k, o, l0, grp, a.pb[p], nu_g, go, dlo, rg, rl, st, pib, psb, dtb);
-        sweep_half<G, NB>(a, k, o, l0, grp, a.pf[p], nu_g, go, dlo, rg, rl, st, pif, psf, dtf);
+        sweep_half<G, NB, SKIP>(a, k, o, l0, grp, a.pb[p], nu_g, go, dlo, rg, rl, st, pib, psb, dtb, aq_lo, aq_hi);
+        sweep_half<G, NB, SKIP>(a, k, o, l0, grp, a.pf[p], nu_g, go, dlo, rg, rl, st, pif, psf, dtf, aq_lo, aq_hi);
 #pragma unroll
         for (int i = 0; i < NB; i++) {
             float u, lam, uml, oml;
@@ -552,7 +590,7 @@ __device__ __forceinline__ void solve_item(const MixArgs &a, int64_t o, int l0, 
     }
 }
 
-template <int G, int NB, int MINB>
+template <int G, int NB, int MINB, bool SKIP>
 __global__ void __launch_bounds__(32 * kWarps2, MINB) k_feautrier_warp(MixArgs a) {
     __shared__ RingGeom rgs[kWarps2][kRing];
     __shared__ float2 rls[kWarps2][G * kRing];
@@ -562,7 +600,7 @@ __global__ void __launch_bounds__(32 * kWarps2, MINB) k_feautrier_warp(MixArgs a
     if (item >= a.n * ngroups) return;
     const int64_t o = item / ngroups;
     const int l0 = (int)(item - o * ngroups) * G;
-    solve_item<G, NB>(a, o, l0, rgs[warp], rls[warp]);
+    solve_item<G, NB, SKIP>(a, o, l0, rgs[warp], rls[warp]);
 }
 
 // Persistent variant over a batch of models: every warp takes work items (model, origin,
@@ -573,7 +611,7 @@ struct BatchItem {
     int32_t local;   // origin * L + first line of the warp's line group
 };
 
-template <int G, int NB, int MINB>
+template <int G, int NB, int MINB, bool SKIP>
 __global__ void __launch_bounds__(32 * kWarps2, MINB)
 k_feautrier_batch(const MixArgs *__restrict__ models, const BatchItem *__restrict__ items, int64_t n_items,
                   unsigned long long *counter, const int32_t *__restrict__ active) {
@@ -594,20 +632,24 @@ k_feautrier_batch(const MixArgs *__restrict__ models, const BatchItem *__restric
         const MixArgs &a = sa[warp];
         const int64_t o = it.local / a.L;
         const int l0 = (int)(it.local - o * a.L);
-        solve_item<G, NB>(a, o, l0, rgs[warp], rls[warp]);
+        solve_item<G, NB, SKIP>(a, o, l0, rgs[warp], rls[warp]);
     }
 }
 
 // Launch variants of the warp kernel: (lines per warp, bins per lane, min blocks per SM).
 struct WarpVariant {
     int G, NB, MINB;
+    bool skip;
     void (*fn)(MixArgs);
     void (*batch)(const MixArgs *, const BatchItem *, int64_t, unsigned long long *, const int32_t *);
 };
-#define MG_VARIANT(G, NB, M) {G, NB, M, k_feautrier_warp<G, NB, M>, k_feautrier_batch<G, NB, M>}
+#define MG_VARIANT(G, NB, M, S) {G, NB, M, S, k_feautrier_warp<G, NB, M, S>, k_feautrier_batch<G, NB, M, S>}
 const WarpVariant kWarpVariants[] = {
-    MG_VARIANT(1, 1, 8), MG_VARIANT(1, 1, 10), MG_VARIANT(2, 2, 4), MG_VARIANT(2, 2, 5), MG_VARIANT(2, 2, 6),
-    MG_VARIANT(1, 2, 4), MG_VARIANT(1, 2, 6), MG_VARIANT(1, 4, 3), MG_VARIANT(1, 4, 4),
+    MG_VARIANT(1, 1, 8, true), MG_VARIANT(1, 1, 10, true), MG_VARIANT(2, 2, 4, true), MG_VARIANT(2, 2, 5, true),
+    MG_VARIANT(2, 2, 6, true), MG_VARIANT(1, 2, 4, true), MG_VARIANT(1, 2, 6, true), MG_VARIANT(1, 4, 3, true),
+    MG_VARIANT(1, 4, 4, true),
+    // without far-wing skipping (every point swept)
+    MG_VARIANT(1, 1, 8, false), MG_VARIANT(2, 2, 5, false), MG_VARIANT(1, 2, 4, false), MG_VARIANT(1, 4, 3, false),
 };
 #undef MG_VARIANT
 constexpr int kNumWarpVariants = sizeof(kWarpVariants) / sizeof(kWarpVariants[0]);
@@ -690,7 +732,7 @@ static int launch_mixed(mg_ctx *ctx, int variant) {
 // Default launch variant for a model: two lines per warp with two bins per lane when the
 // lines have <= 32 bins, otherwise one line per warp with as many bins per lane as needed.
 static int default_variant(int L, int Q) {
-    const int order[] = {3, 2, 4, 0, 1, 6, 5, 8, 7};
+    const int order[] = {3, 2, 4, 0, 1, 6, 5, 8, 7, 10, 9, 11, 12};
     for (int v : order)
         if (variant_valid(v, L, Q)) return v;
     return -1;

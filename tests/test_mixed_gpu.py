@@ -80,11 +80,11 @@ def test_mixed_ali_fixed_point(name):
     assert np.max(rel_err(ctx.get_populations(), ref)) < TOL_MIX
 
 
-@pytest.mark.parametrize("Q,variants", [(31, [0, 1, 2, 3, 4]), (63, [5, 6]), (100, [7, 8])])
+@pytest.mark.parametrize("Q,variants", [(31, [0, 1, 2, 3, 4, 9, 10]), (63, [5, 6, 11]), (100, [7, 8, 12])])
 def test_every_launch_variant_matches_oracle(Q, variants):
     """Every launch variant of the warp kernel (lines per warp, bins per lane, blocks per
-    SM) gives the same radiation field within the mixed tolerance; the autotuner picks a
-    valid one."""
+    SM, with and without skipping far-wing points) gives the same radiation field within
+    the mixed tolerance; the autotuner picks a valid one."""
     m = syn.model_clumpy_3d(n=1500, seed=6, n_q=Q)
     o = Oracle(m, nthreads=16)
     origins = np.sort(np.random.default_rng(3).choice(m.n, 40, replace=False))
