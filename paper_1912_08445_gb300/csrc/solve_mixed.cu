@@ -447,14 +447,17 @@ __device__ __forceinline__ void sweep_half(const MixArgs &a, const SweepK &k, in
         const int cnt = min(kRing, xnext + 1);
         __syncwarp();
         int e = anchor;
+        bool my_far = false;
         if (lane < cnt) {
             float4 g;
             float2 ln[G];
             stage_ring_point<G>(a, o, l0, off, xnext - lane, e, g, ln, aq_lo, aq_hi);
             rg[lane].g = g;
+            my_far = g.w != 0.0f;
 #pragma unroll
             for (int k = 0; k < G; k++) rl[k * kRing + lane] = ln[k];
         }
+        const unsigned farmask = SKIP ? __ballot_sync(0xffffffffu, my_far) : 0u;
         anchor = __shfl_sync(0xffffffffu, e, cnt - 1);
         __syncwarp();
         int j = 0;
@@ -471,14 +474,25 @@ __device__ __forceinline__ void sweep_half(const MixArgs &a, const SweepK &k, in
         if (SKIP) {
             // A point whose own and two previous points are all far changes the state by
             // O(chi_min ds) only (no-ops in FP32): rows that involve a non-floored interval
-            // are still computed exactly.
-            for (; j < cnt; j++) {
-                const float4 g = rg[j].g;
-                const bool far = g.w != 0.0f;
-                if (!(far && far1 && far2)) step_point<NB>(k, st, g, my[j], qds_p);
-                qds_p = g.x;
+            // are still computed exactly. The points to process come from the chunk's
+            // ballot of far points (bit j = point j), so skipped points cost nothing.
+            const unsigned f1 = (farmask << 1) | (far1 ? 1u : 0u);                 // far(j-1)
+            const unsigned f2 = (farmask << 2) | (far1 ? 2u : 0u) | (far2 ? 1u : 0u);   // far(j-2)
+            unsigned proc = ~(farmask & f1 & f2) & (cnt == 32 ? 0xffffffffu : ((1u << cnt) - 1u));
+            if (j) proc &= ~1u;   // point 0 of the first chunk is the far end, done above
+            while (proc) {
+                const int jj = __ffs(proc) - 1;
+                proc &= proc - 1u;
+                const float qprev = jj ? rg[jj - 1].g.x : qds_p;
+                step_point<NB>(k, st, rg[jj].g, my[jj], qprev);
+            }
+            qds_p = rg[cnt - 1].g.x;
+            if (cnt >= 2) {
+                far1 = (farmask >> (cnt - 1)) & 1u;
+                far2 = (farmask >> (cnt - 2)) & 1u;
+            } else {
                 far2 = far1;
-                far1 = far;
+                far1 = farmask & 1u;
             }
         } else {
 #pragma unroll 4
