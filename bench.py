@@ -132,7 +132,7 @@ def recorded_traffic(kernel_variant):
     src = os.path.join(ROOT, rec["source"])
     if not os.path.exists(src) or hashlib.sha256(open(src, "rb").read()).hexdigest() != rec["source_sha256"]:
         return None
-    if kernel_variant != 3:      # the record is for the (2 lines, 2 bins, 5 blocks) variant
+    if kernel_variant != rec.get("variant"):      # the record belongs to one launch variant
         return None
     return rec["dram_bytes_read_per_launch"] + rec["dram_bytes_write_per_launch"]
 

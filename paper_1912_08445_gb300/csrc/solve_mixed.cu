@@ -659,11 +659,14 @@ struct WarpVariant {
 };
 #define MG_VARIANT(G, NB, M, S) {G, NB, M, S, k_feautrier_warp<G, NB, M, S>, k_feautrier_batch<G, NB, M, S>}
 const WarpVariant kWarpVariants[] = {
+    // with far-wing skipping
     MG_VARIANT(1, 1, 8, true), MG_VARIANT(1, 1, 10, true), MG_VARIANT(2, 2, 4, true), MG_VARIANT(2, 2, 5, true),
     MG_VARIANT(2, 2, 6, true), MG_VARIANT(1, 2, 4, true), MG_VARIANT(1, 2, 6, true), MG_VARIANT(1, 4, 3, true),
     MG_VARIANT(1, 4, 4, true),
-    // without far-wing skipping (every point swept)
-    MG_VARIANT(1, 1, 8, false), MG_VARIANT(2, 2, 5, false), MG_VARIANT(1, 2, 4, false), MG_VARIANT(1, 4, 3, false),
+    // the same shapes without skipping (every point swept)
+    MG_VARIANT(1, 1, 8, false), MG_VARIANT(1, 1, 10, false), MG_VARIANT(2, 2, 4, false), MG_VARIANT(2, 2, 5, false),
+    MG_VARIANT(2, 2, 6, false), MG_VARIANT(1, 2, 4, false), MG_VARIANT(1, 2, 6, false), MG_VARIANT(1, 4, 3, false),
+    MG_VARIANT(1, 4, 4, false),
 };
 #undef MG_VARIANT
 constexpr int kNumWarpVariants = sizeof(kWarpVariants) / sizeof(kWarpVariants[0]);
@@ -746,7 +749,7 @@ static int launch_mixed(mg_ctx *ctx, int variant) {
 // Default launch variant for a model: two lines per warp with two bins per lane when the
 // lines have <= 32 bins, otherwise one line per warp with as many bins per lane as needed.
 static int default_variant(int L, int Q) {
-    const int order[] = {3, 2, 4, 0, 1, 6, 5, 8, 7, 10, 9, 11, 12};
+    const int order[] = {4, 3, 2, 0, 1, 6, 5, 8, 7, 13, 12, 11, 9, 10, 15, 14, 17, 16};
     for (int v : order)
         if (variant_valid(v, L, Q)) return v;
     return -1;
