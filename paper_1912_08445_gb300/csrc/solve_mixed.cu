@@ -478,13 +478,23 @@ __device__ __forceinline__ void sweep_half(const MixArgs &a, const SweepK &k, in
             // ballot of far points (bit j = point j), so skipped points cost nothing.
             const unsigned f1 = (farmask << 1) | (far1 ? 1u : 0u);                 // far(j-1)
             const unsigned f2 = (farmask << 2) | (far1 ? 2u : 0u) | (far2 ? 1u : 0u);   // far(j-2)
-            unsigned proc = ~(farmask & f1 & f2) & (cnt == 32 ? 0xffffffffu : ((1u << cnt) - 1u));
-            if (j) proc &= ~1u;   // point 0 of the first chunk is the far end, done above
-            while (proc) {
-                const int jj = __ffs(proc) - 1;
-                proc &= proc - 1u;
-                const float qprev = jj ? rg[jj - 1].g.x : qds_p;
-                step_point<NB>(k, st, rg[jj].g, my[jj], qprev);
+            const unsigned all = cnt == 32 ? 0xffffffffu : ((1u << cnt) - 1u);
+            unsigned proc = ~(farmask & f1 & f2) & all;
+            if (proc == all) {   // nothing to skip in this chunk: the unrolled sweep
+#pragma unroll 4
+                for (; j < cnt; j++) {
+                    const float4 g = rg[j].g;
+                    step_point<NB>(k, st, g, my[j], qds_p);
+                    qds_p = g.x;
+                }
+            } else {
+                if (j) proc &= ~1u;   // point 0 of the first chunk is the far end, done above
+                while (proc) {
+                    const int jj = __ffs(proc) - 1;
+                    proc &= proc - 1u;
+                    const float qprev = jj ? rg[jj - 1].g.x : qds_p;
+                    step_point<NB>(k, st, rg[jj].g, my[jj], qprev);
+                }
             }
             qds_p = rg[cnt - 1].g.x;
             if (cnt >= 2) {
