@@ -25,6 +25,9 @@ struct TraceArgs {
     int32_t *cells, *xcum;
     double *ds, *vpar;
     int32_t *err;
+    // cells of each half-ray recorded by the count pass: tmp[k * n R + t] for k < cap_tmp
+    int32_t *tmp;
+    int32_t cap_tmp;
 };
 
 // Points inserted between two consecutive points by the velocity-step rule: when the
@@ -50,6 +53,8 @@ __device__ __forceinline__ bool emit(const TraceArgs &a, int64_t base, int32_t &
         a.xcum[base + len] = x;
         a.ds[base + len] = ds;
         a.vpar[base + len] = vp;
+    } else if (a.tmp && len < a.cap_tmp) {
+        a.tmp[(int64_t)len * a.n * a.R + base] = cell;   // base = thread index in the count pass
     }
     len++;
     va = vp;
@@ -96,6 +101,27 @@ __device__ void walk_3d(const TraceArgs &a, int64_t o, int r, int64_t base, int3
         s_cur = bs;
         cur = best;
         if (a.bdy[best]) return;
+    }
+}
+
+// Fill pass of a half-ray whose cells the count pass recorded: the same projections,
+// path lengths, line-of-sight velocities and velocity steps as the walk, without the
+// neighbour search.
+__device__ void replay_3d(const TraceArgs &a, int64_t o, int r, int64_t t, int64_t base, int32_t n_cells) {
+    const double n0 = a.dirs[3 * r], n1 = a.dirs[3 * r + 1], n2 = a.dirs[3 * r + 2];
+    const double xo0 = a.pos[3 * o], xo1 = a.pos[3 * o + 1], xo2 = a.pos[3 * o + 2];
+    const double vo0 = a.vel[3 * o], vo1 = a.vel[3 * o + 1], vo2 = a.vel[3 * o + 2];
+    double s_cur = 0.0, va = 0.0, ba = a.b[o];
+    int32_t len = 0, x = 0;
+    for (int32_t k = 0; k < n_cells; k++) {
+        const int64_t c = a.tmp[(int64_t)k * a.n * a.R + t];
+        const double dx = a.pos[3 * c] - xo0;
+        const double dy = a.pos[3 * c + 1] - xo1;
+        const double dz = a.pos[3 * c + 2] - xo2;
+        const double s = dx * n0 + dy * n1 + dz * n2;
+        const double vp = n0 * (a.vel[3 * c] - vo0) + n1 * (a.vel[3 * c + 1] - vo1) + n2 * (a.vel[3 * c + 2] - vo2);
+        emit<true>(a, base, len, x, (int32_t)c, s - s_cur, vp, va, ba);
+        s_cur = s;
     }
 }
 
@@ -164,9 +190,16 @@ __global__ void k_trace(TraceArgs a) {
     const int r = (int)(t / a.n);
     const int64_t o = t - (int64_t)r * a.n;
     const int64_t ray = o * a.R + r;
-    const int64_t base = FILL ? a.ray_off[ray] : 0;
+    const int64_t base = FILL ? a.ray_off[ray] : t;
     int32_t len = 0, x = 0;
     bool dead = false, overflow = false;
+    if (FILL && a.tmp && a.geometry == MG_GEOM_3D) {
+        const int32_t n_cells = a.len[ray];
+        if (n_cells <= a.cap_tmp) {
+            replay_3d(a, o, r, t, base, n_cells);
+            return;
+        }
+    }
     if (a.geometry == MG_GEOM_SPHERICAL_1D) walk_sph1d<FILL>(a, o, r, base, len, x, overflow);
     else walk_3d<FILL>(a, o, r, base, len, x, dead, overflow);
     if (overflow) atomicOr(a.err, 1);
@@ -308,6 +341,16 @@ int mg_launch_trace(mg_ctx *ctx) {
     a.nbr_off = ctx->d_nbr_off; a.nbr_idx = ctx->d_nbr_idx; a.bdy = ctx->d_bdy;
     a.dshift_frac = ctx->opt.dshift_frac; a.max_steps = ctx->opt.max_steps;
     a.len = d_len; a.xlen = d_xlen; a.err = ctx->d_err;
+    // record up to cap_tmp cells per half-ray in the count pass (capped at 8 GiB)
+    int32_t *d_tmp = nullptr;
+    int32_t cap_tmp = 32;
+    while (cap_tmp > 0 && (double)nr * cap_tmp * 4.0 > 8.0 * (1 << 30)) cap_tmp /= 2;
+    if (ctx->geometry == MG_GEOM_3D && cap_tmp > 0 && cudaMalloc(&d_tmp, (size_t)nr * cap_tmp * 4) != cudaSuccess) {
+        cudaGetLastError();
+        d_tmp = nullptr;
+    }
+    a.tmp = d_tmp;
+    a.cap_tmp = d_tmp ? cap_tmp : 0;
     const int bs = 128;
     const unsigned grid = (unsigned)((nr + bs - 1) / bs);
     {
@@ -321,7 +364,7 @@ int mg_launch_trace(mg_ctx *ctx) {
     MG_CUDA(cudaMemcpy(&total, ctx->d_ray_off + nr, 8, cudaMemcpyDeviceToHost));
     MG_CUDA(cudaMemcpy(&kerr, ctx->d_err, 4, cudaMemcpyDeviceToHost));
     if (kerr) {
-        cudaFree(d_len); cudaFree(d_xlen);
+        cudaFree(d_len); cudaFree(d_xlen); cudaFree(d_tmp);
         return mg_fail(ctx, MG_ERR_CAPACITY, "ray tracing: a half-ray exceeded max_steps");
     }
     if ((rc = mg_alloc(ctx, &ctx->d_cells, total)) || (rc = mg_alloc(ctx, &ctx->d_xcum, total)) ||
@@ -348,6 +391,7 @@ int mg_launch_trace(mg_ctx *ctx) {
     MG_CUDA(cudaStreamSynchronize(ctx->stream));
     cudaFree(d_len);
     cudaFree(d_xlen);
+    cudaFree(d_tmp);
     ctx->n_elements = (int64_t)st[0];
     ctx->n_expanded = (int64_t)st[1];
     ctx->max_pair_len = (int64_t)st[2];
