@@ -341,10 +341,10 @@ int mg_launch_trace(mg_ctx *ctx) {
     a.nbr_off = ctx->d_nbr_off; a.nbr_idx = ctx->d_nbr_idx; a.bdy = ctx->d_bdy;
     a.dshift_frac = ctx->opt.dshift_frac; a.max_steps = ctx->opt.max_steps;
     a.len = d_len; a.xlen = d_xlen; a.err = ctx->d_err;
-    // record up to cap_tmp cells per half-ray in the count pass (capped at 8 GiB)
+    // record up to cap_tmp cells per half-ray in the count pass (at most 32 GiB of scratch)
     int32_t *d_tmp = nullptr;
-    int32_t cap_tmp = 32;
-    while (cap_tmp > 0 && (double)nr * cap_tmp * 4.0 > 8.0 * (1 << 30)) cap_tmp /= 2;
+    int32_t cap_tmp = 128;
+    while (cap_tmp > 0 && (double)nr * cap_tmp * 4.0 > 32.0 * (1 << 30)) cap_tmp /= 2;
     if (ctx->geometry == MG_GEOM_3D && cap_tmp > 0 && cudaMalloc(&d_tmp, (size_t)nr * cap_tmp * 4) != cudaSuccess) {
         cudaGetLastError();
         d_tmp = nullptr;
