@@ -76,11 +76,15 @@ typedef struct {
     int64_t max_steps;     /* cap on traced cells per half-ray                            */
     int32_t profile;       /* 1: time each kernel launch with CUDA events                 */
     int32_t spectrum;      /* 1: keep the per-bin mean intensity for mg_get_spectrum      */
+    int32_t pad;
+    double  tau_fp64;      /* MG_MIXED only: cells whose largest diagonal ALO weight L is
+                              >= 1 - 1/tau_fp64 (optically thick lines) are solved again in
+                              FP64 after the FP32 pass; 0 = off                            */
 } mg_options;
 
 /* Fills *opt with defaults: MG_FP64, device 0, tol 1e-6, max_iter 300, ng_period 4,
  * dshift_frac 1/3, chi_min 1e-30, dtau_min 1e-30, T_cmb 2.725, line_cut 7.5,
- * max_steps 100000, profile 0, spectrum 0. */
+ * max_steps 100000, profile 0, spectrum 0, tau_fp64 0 (off). */
 void mg_default_options(mg_options *opt);
 
 /* Creates a context on opt->device (NULL opt = defaults). *out receives the handle.
@@ -207,6 +211,9 @@ int mg_update_populations_noalloc(mg_ctx *ctx, const double *d_pops_old, double 
  * without the ALO, and (point, line) pairs with a negative opacity integral in the last
  * formal solve. Either pointer may be NULL. */
 int mg_status_counts(const mg_ctx *ctx, int64_t *fallback_cells, int64_t *negative_opacity);
+/* Number of cells the last mixed-precision formal solve solved again in FP64
+ * (opt.tau_fp64 > 0). Synchronises. */
+int mg_promoted_cells(const mg_ctx *ctx, int64_t *count);
 
 typedef struct {
     int32_t iterations;      /* regular iterations done                            */

@@ -27,7 +27,7 @@ class mg_options(C.Structure):
                 ("max_iter", C.c_int32), ("ng_period", C.c_int32), ("dshift_frac", C.c_double),
                 ("chi_min", C.c_double), ("dtau_min", C.c_double), ("T_cmb", C.c_double),
                 ("line_cut", C.c_double), ("max_steps", C.c_int64), ("profile", C.c_int32),
-                ("spectrum", C.c_int32)]
+                ("spectrum", C.c_int32), ("pad", C.c_int32), ("tau_fp64", C.c_double)]
 
 
 class mg_train_opts(C.Structure):
@@ -91,6 +91,7 @@ _SIGS = {
     "mg_work_counts": (C.c_int, [_P, _P, _P]),
     "mg_autotune": (C.c_int, [_P, C.c_int32, _P, _P, _P]),
     "mg_status_counts": (C.c_int, [_P, _P, _P]),
+    "mg_promoted_cells": (C.c_int, [_P, _P]),
     "mg_mlp_create": (C.c_int, [_P, C.c_int32, C.c_uint64, C.c_int32]),
     "mg_mlp_destroy": (C.c_int, [_P]),
     "mg_mlp_last_error": (C.c_char_p, [_P]),
@@ -320,6 +321,11 @@ class Context:
 
     def reset_kernel_times(self):
         self._chk(self.lib.mg_reset_kernel_times(self.h), "mg_reset_kernel_times")
+
+    def promoted_cells(self):
+        c = C.c_int64(0)
+        self._chk(self.lib.mg_promoted_cells(self.h, C.byref(c)), "mg_promoted_cells")
+        return c.value
 
     def status_counts(self):
         f = C.c_int64(0); n = C.c_int64(0)

@@ -135,6 +135,9 @@ struct mg_ctx {
     unsigned long long *h_scal = nullptr;   // pinned
     int32_t *d_err = nullptr;               // kernel error word
 
+    // ---- FP64 promotion of optically thick cells (mixed precision)
+    int32_t *d_promo = nullptr;   // [n] origin list, then [n] count in d_promo[n]
+
     // ---- launch variant of the mixed formal solve (-1: default for the model)
     int mixed_variant = -1;
 
@@ -182,6 +185,7 @@ int mg_launch_trace(mg_ctx *ctx);
 int mg_launch_line_data(mg_ctx *ctx);
 int mg_launch_line_data_mixed(mg_ctx *ctx);
 int mg_launch_feautrier(mg_ctx *ctx);
+int mg_launch_feautrier_fp64_list(mg_ctx *ctx, const int32_t *olist, const int32_t *ocount);
 int mg_autotune_mixed(mg_ctx *ctx, int reps, int *best, double *best_ms, int *n_tried);
 int mg_launch_lte(mg_ctx *ctx);
 int mg_launch_collision_rates(mg_ctx *ctx);

@@ -55,6 +55,7 @@ extern "C" void mg_default_options(mg_options *o) {
     o->max_steps = 100000;
     o->profile = 0;
     o->spectrum = 0;
+    o->tau_fp64 = 0.0;
 }
 
 extern "C" int mg_create(mg_ctx **out, const mg_options *opt) {
@@ -66,7 +67,8 @@ extern "C" int mg_create(mg_ctx **out, const mg_options *opt) {
     const mg_options &o = ctx->opt;
     if ((o.precision != MG_FP64 && o.precision != MG_MIXED) || !(o.tol > 0) || o.max_iter < 1 ||
         o.ng_period < 0 || !(o.dshift_frac > 0) || !(o.chi_min > 0) || !(o.dtau_min > 0) ||
-        !(o.T_cmb > 0) || !(o.line_cut > 0) || o.max_steps < 1) {
+        !(o.T_cmb > 0) || !(o.line_cut > 0) || o.max_steps < 1 || !(o.tau_fp64 >= 0) ||
+        (o.tau_fp64 > 0 && o.tau_fp64 <= 1)) {
         delete ctx;
         return MG_ERR_ARG;
     }
@@ -98,7 +100,7 @@ static void drop_state(mg_ctx *ctx) {
     mg_free(ctx->d_pops); mg_free(ctx->d_pops_new); mg_free(ctx->d_line); mg_free(ctx->d_linef);
     mg_free(ctx->d_J); mg_free(ctx->d_L); mg_free(ctx->d_Jeff); mg_free(ctx->d_Lc); mg_free(ctx->d_Jnu);
     for (auto &h : ctx->d_hist) mg_free(h);
-    mg_free(ctx->d_ng_tmp); mg_free(ctx->d_ng_part);
+    mg_free(ctx->d_ng_tmp); mg_free(ctx->d_ng_part); mg_free(ctx->d_promo);
 }
 
 extern "C" int mg_destroy(mg_ctx *ctx) {
@@ -113,7 +115,7 @@ extern "C" int mg_destroy(mg_ctx *ctx) {
     mg_free(ctx->d_ovl); mg_free(ctx->d_dirs); mg_free(ctx->d_pf); mg_free(ctx->d_pb);
     mg_free(ctx->d_roots); mg_free(ctx->d_weights); mg_free(ctx->d_pops); mg_free(ctx->d_pops_new);
     for (auto &h : ctx->d_hist) mg_free(h);
-    mg_free(ctx->d_ng_tmp); mg_free(ctx->d_ng_part);
+    mg_free(ctx->d_ng_tmp); mg_free(ctx->d_ng_part); mg_free(ctx->d_promo);
     mg_free(ctx->d_line); mg_free(ctx->d_linef); mg_free(ctx->d_J); mg_free(ctx->d_L);
     mg_free(ctx->d_Jeff); mg_free(ctx->d_Lc); mg_free(ctx->d_Jnu); mg_free(ctx->d_scal);
     mg_free(ctx->d_err);
@@ -724,6 +726,18 @@ extern "C" int mg_update_populations(mg_ctx *ctx, double *max_rel_change) {
     if (ctx->h_scal[2]) return mg_fail(ctx, MG_ERR_NUMERIC, "statistical equilibrium: non-finite populations after fallback");
     if (ctx->h_scal[1]) return MG_WARN_NEG_POP_FALLBACK;
     return ctx->h_scal[4] ? MG_WARN_NEG_OPACITY : MG_OK;
+}
+
+extern "C" int mg_promoted_cells(const mg_ctx *cctx, int64_t *count) {
+    mg_ctx *ctx = const_cast<mg_ctx *>(cctx);
+    if (!ctx || !count) return MG_ERR_ARG;
+    *count = 0;
+    if (!ctx->d_promo) return MG_OK;
+    int32_t c = 0;
+    MG_CUDA(cudaMemcpyAsync(&c, ctx->d_promo + ctx->n, 4, cudaMemcpyDeviceToHost, ctx->stream));
+    MG_CUDA(cudaStreamSynchronize(ctx->stream));
+    *count = c;
+    return MG_OK;
 }
 
 extern "C" int mg_status_counts(const mg_ctx *ctx, int64_t *fallback_cells, int64_t *negative_opacity) {

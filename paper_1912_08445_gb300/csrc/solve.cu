@@ -45,6 +45,8 @@ struct SolveArgs {
     double *J, *Lout, *Jeff, *Lc, *Jnu;
     int32_t kmax;
     int32_t *err;
+    const int32_t *olist;    // optional list of origins (FP64 promotion), count in *ocount
+    const int32_t *ocount;
 };
 
 __device__ __forceinline__ double planck_d(double nu, double T) {
@@ -177,7 +179,11 @@ __global__ void k_feautrier64(SolveArgs a) {
     double *acc = S.w + kmax;   // [F][4]
     S.ca = reinterpret_cast<int32_t *>(acc + 4 * F);
     S.cb = S.ca + kmax;
-    const int64_t o = blockIdx.x;
+    int64_t o = blockIdx.x;
+    if (a.olist) {
+        if ((int)blockIdx.x >= *a.ocount) return;
+        o = a.olist[blockIdx.x];
+    }
     for (int f = threadIdx.x; f < 4 * F; f += blockDim.x) acc[f] = 0.0;
     const double bo = a.b[o];
     for (int p = 0; p < a.P; p++) {
@@ -268,8 +274,37 @@ int mg_launch_line_data(mg_ctx *ctx) {
 
 int mg_launch_feautrier_mixed(mg_ctx *ctx);
 
+// Cells whose largest diagonal ALO weight over the lines is >= lmin go to the list.
+__global__ void k_mark_thick(int64_t n, int L, const double *Lw, double lmin, int32_t *list, int32_t *count) {
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n) return;
+    double mx = 0.0;
+    for (int l = 0; l < L; l++) mx = fmax(mx, Lw[c * L + l]);
+    if (mx >= lmin) list[atomicAdd(count, 1)] = (int32_t)c;
+}
+
+static int launch_fp64(mg_ctx *ctx, const int32_t *olist, const int32_t *ocount, unsigned grid);
+
+int mg_launch_feautrier_fp64_list(mg_ctx *ctx, const int32_t *olist, const int32_t *ocount) {
+    return launch_fp64(ctx, olist, ocount, (unsigned)ctx->n);
+}
+
 int mg_launch_feautrier(mg_ctx *ctx) {
-    if (ctx->opt.precision == MG_MIXED) return mg_launch_feautrier_mixed(ctx);
+    if (ctx->opt.precision == MG_MIXED) {
+        int rc = mg_launch_feautrier_mixed(ctx);
+        if (rc || !(ctx->opt.tau_fp64 > 0.0)) return rc;
+        // FP64 promotion of optically thick cells: list them, then solve them again in FP64
+        if (!ctx->d_promo && (rc = mg_alloc(ctx, &ctx->d_promo, ctx->n + 1))) return rc;
+        MG_CUDA(cudaMemsetAsync(ctx->d_promo + ctx->n, 0, sizeof(int32_t), ctx->stream));
+        k_mark_thick<<<(unsigned)((ctx->n + 255) / 256), 256, 0, ctx->stream>>>(
+            ctx->n, ctx->n_lines, ctx->d_L, 1.0 - 1.0 / ctx->opt.tau_fp64, ctx->d_promo, ctx->d_promo + ctx->n);
+        MG_CUDA(cudaGetLastError());
+        return launch_fp64(ctx, ctx->d_promo, ctx->d_promo + ctx->n, (unsigned)ctx->n);
+    }
+    return launch_fp64(ctx, nullptr, nullptr, (unsigned)ctx->n);
+}
+
+static int launch_fp64(mg_ctx *ctx, const int32_t *olist, const int32_t *ocount, unsigned grid) {
     SolveArgs a{};
     a.n = ctx->n; a.R = ctx->R; a.P = ctx->P; a.L = ctx->n_lines; a.Q = ctx->Q;
     a.pf = ctx->d_pf; a.pb = ctx->d_pb; a.ray_off = ctx->d_ray_off; a.cells = ctx->d_cells; a.xcum = ctx->d_xcum;
@@ -280,6 +315,8 @@ int mg_launch_feautrier(mg_ctx *ctx) {
     a.Jnu = ctx->opt.spectrum ? ctx->d_Jnu : nullptr;
     a.kmax = (int32_t)ctx->max_pair_len;
     a.err = ctx->d_err;
+    a.olist = olist;
+    a.ocount = ocount;
     const int F = a.L * a.Q;
     size_t smem = sizeof(double) * ((size_t)a.kmax * 4 + 4 * (size_t)F) + sizeof(int32_t) * 2 * (size_t)a.kmax;
     if (smem > 227 * 1024)
@@ -287,10 +324,10 @@ int mg_launch_feautrier(mg_ctx *ctx) {
     MG_CUDA(cudaFuncSetAttribute(k_feautrier64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int threads = ((F + 31) / 32) * 32;
     if (threads > 256) threads = 256;
-    MG_CUDA(cudaMemsetAsync(ctx->d_err, 0, 4, ctx->stream));
+    if (!olist) MG_CUDA(cudaMemsetAsync(ctx->d_err, 0, 4, ctx->stream));
     {
-        MgTimed t(ctx, "feautrier_fp64");
-        k_feautrier64<<<(unsigned)ctx->n, threads, smem, ctx->stream>>>(a);
+        MgTimed t(ctx, olist ? "feautrier_fp64_promoted" : "feautrier_fp64");
+        k_feautrier64<<<grid, threads, smem, ctx->stream>>>(a);
     }
     MG_CUDA(cudaGetLastError());
     return MG_OK;

@@ -130,3 +130,26 @@ def test_mixed_at_high_optical_depth():
         rep, rc = c.iterate()
         assert rep["converged"]
     assert np.max(rel_err(ctx32.get_populations(), ctx64.get_populations())) < TOL_MIX
+
+
+def test_fp64_promotion_of_thick_cells():
+    """With opt.tau_fp64 the cells whose largest diagonal ALO weight L is >= 1 - 1/tau are
+    solved again in FP64 after the FP32 pass: their J, L, J_eff then equal the FP64 path
+    within 1e-10, the other cells keep the FP32 results."""
+    m = syn.model_disc(n=3000, seed=4, nside=1, n_q=31, n_h2_in=1e16, abundance=1e-4)
+    c64 = gpu_context(m, precision=0)
+    c32 = gpu_context(m, precision=1)
+    cp = gpu_context(m, precision=1, tau_fp64=20.0)
+    for c in (c64, c32, cp):
+        c.trace_rays()
+        c.init_populations()
+        c.formal_solve()
+    J64, L64, E64 = c64.get_radiation()
+    J32, L32, E32 = c32.get_radiation()
+    Jp, Lp, Ep = cp.get_radiation()
+    n_prom = cp.promoted_cells()
+    thick = L32.max(1) >= 1 - 1 / 20.0
+    assert n_prom == int(thick.sum()) and 0 < n_prom < m.n
+    assert np.max(rel_err(Jp[thick], J64[thick])) < 1e-10
+    assert np.max(rel_err(Ep[thick], E64[thick])) < 1e-10
+    assert np.array_equal(Jp[~thick], J32[~thick])
