@@ -310,8 +310,86 @@ __global__ void __launch_bounds__(256) k_feautrier_mixed(MixArgs a) {
 // interior update started from the virtual state (Phi iota = 1, psi = I, dtau = 0).
 // The opacity floor costs three instructions: chi = max(chi_l, chi_min) and
 // S = min(S_l, chi_l S_l / chi_min), which is eta/chi with chi floored.
+//
+// The ray elements behind each ring refill come from an element window in shared memory
+// that is filled asynchronously (cp.async) one refill ahead: while the warp sweeps the
+// points of one refill, the records (xcum, cell, v, ds) of the next window stream in, and
+// half-way through the sweep the gathers through the cell index (b and the line data)
+// are issued, so a refill normally finds its window complete. The last refill of a
+// half-ray prefetches the first window of the next half-ray.
 constexpr int kRing = 32;
 constexpr int kWarps2 = 4;
+constexpr int kWin = 33;   // elements top, top-1, ..., top-32 of a half-ray
+
+// Element window of one warp, double-buffered. Element e of the half-ray sits at slot
+// top - e; element -1 (reached when top < 32) is the origin itself: xcum 0, cell o, v 0.
+template <int G>
+struct ElemWin {
+    int32_t x1[2][kWin];      // xcum[e]: the element's expanded points are xcum[e-1] .. xcum[e]-1
+    int32_t cell[2][kWin];
+    float v[2][kWin], ds[2][kWin], b[2][kWin];
+    float2 ln[2][G][kWin];    // scaled (eta, chi) of the warp's lines at the element's cell
+};
+
+__device__ __forceinline__ void cp_async4(void *dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+                 "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async8(void *dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+                 "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// Issues the copies of the records of elements top .. top-32 of the half-ray at `off`
+// into buffer bf (lane i: slot i; lane 0 also slot 32).
+template <int G>
+__device__ __forceinline__ void win_records(const MixArgs &a, int64_t off, int top, int32_t o, ElemWin<G> &w,
+                                            int bf) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int t = 0; t < 2; t++) {
+        if (t == 1 && lane != 0) break;
+        const int i = lane + 32 * t;
+        const int e = top - i;
+        if (e >= 0) {
+            cp_async4(&w.x1[bf][i], a.xcum + off + e);
+            cp_async4(&w.cell[bf][i], a.cells + off + e);
+            cp_async4(&w.v[bf][i], a.vpar + off + e);
+            cp_async4(&w.ds[bf][i], a.ds + off + e);
+        } else {
+            w.x1[bf][i] = 0;
+            w.cell[bf][i] = o;
+            w.v[bf][i] = 0.0f;
+            w.ds[bf][i] = 0.0f;
+        }
+    }
+    cp_async_commit();
+}
+
+// Issues the gathers through the cell index of buffer bf; the records must have landed
+// (each lane reads only the slots it copied itself).
+template <int G>
+__device__ __forceinline__ void win_gathers(const MixArgs &a, int l0, ElemWin<G> &w, int bf) {
+    const int lane = threadIdx.x & 31;
+    const float2 *line2 = reinterpret_cast<const float2 *>(a.line);
+#pragma unroll
+    for (int t = 0; t < 2; t++) {
+        if (t == 1 && lane != 0) break;
+        const int i = lane + 32 * t;
+        const int64_t c = w.cell[bf][i];
+        cp_async4(&w.b[bf][i], a.b + c);
+#pragma unroll
+        for (int k = 0; k < G; k++) {
+            const int l = l0 + k < a.L ? l0 + k : a.L - 1;
+            cp_async8(&w.ln[bf][k][i], line2 + c * a.L + l);
+        }
+    }
+    cp_async_commit();
+}
 
 // Scalars of the sweep, held in registers (not re-read from the argument block).
 struct SweepK {
@@ -329,24 +407,25 @@ struct RingGeom {
     float4 g;
 };
 
+// Expanded point x of the element in window slot i (sub-point (x - x0 + 1)/(ns + 1) of the
+// interval from the element's predecessor towards the origin to its own cell).
 // A point is "far" for the warp when every bin of the warp lies so far in the wings of
 // every line of its group that the opacity is floored there: X 2^(-x'^2) < chi_min with
 // x' = a_q g.z - g.y over the warp's range of a_q (monotonic in a_q, so the smallest
-// |x'| is at an end of the range or zero). Flagged in g.w.
+// |x'| is at an end of the range or zero). Flagged in g.w. The divisions here use the
+// approximate reciprocal (the path computes in FP32).
 template <int G>
-__device__ __forceinline__ void stage_ring_point(const MixArgs &a, int64_t o, int l0, int64_t off, int x, int &e,
+__device__ __forceinline__ void stage_ring_point(const MixArgs &a, const ElemWin<G> &w, int bf, int i, int l0, int x,
                                                  float4 &g, float2 (&ln)[G], float aq_lo, float aq_hi) {
-    while (e > 0 && a.xcum[off + e - 1] > x) e--;
-    const int x0 = e ? a.xcum[off + e - 1] : 0;
-    const int ns = a.xcum[off + e] - x0 - 1;
-    const float w = (float)(x - x0 + 1) / (float)(ns + 1);
-    const int64_t c = a.cells[off + e];
-    const int64_t prev = e ? a.cells[off + e - 1] : o;
-    const float pv = e ? a.vpar[off + e - 1] : 0.0f;
-    const float v = (1.0f - w) * pv + w * a.vpar[off + e];
-    const float qds = kInvSqrt8 * a.ds[off + e] / (float)(ns + 1);
-    const float bb = (1.0f - w) * a.b[prev] + w * a.b[c];
-    const float ib = 1.0f / bb;
+    const int x0 = w.x1[bf][i + 1];
+    const int ns = w.x1[bf][i] - x0 - 1;
+    const float rn = rcpf((float)(ns + 1));
+    // exactly 1 at the element's own cell, so that a thick neighbour cannot leak into it
+    const float wt = x - x0 == ns ? 1.0f : (float)(x - x0 + 1) * rn;
+    const float v = (1.0f - wt) * w.v[bf][i + 1] + wt * w.v[bf][i];
+    const float qds = kInvSqrt8 * w.ds[bf][i] * rn;
+    const float bb = (1.0f - wt) * w.b[bf][i + 1] + wt * w.b[bf][i];
+    const float ib = rcpf(bb);
     const float pz = kSqrtLog2e * ib;
     g = make_float4(qds, v * pz, (1.0f - v * (float)(1.0 / kC)) * pz, 0.0f);
     const float xlo = aq_lo * g.z - g.y, xhi = aq_hi * g.z - g.y;
@@ -356,11 +435,11 @@ __device__ __forceinline__ void stage_ring_point(const MixArgs &a, int64_t o, in
 #pragma unroll
     for (int k = 0; k < G; k++) {
         const int l = l0 + k < a.L ? l0 + k : a.L - 1;
-        const float2 p0 = reinterpret_cast<const float2 *>(a.line)[prev * a.L + l];
-        const float2 p1 = reinterpret_cast<const float2 *>(a.line)[c * a.L + l];
-        const float et = (1.0f - w) * p0.x + w * p1.x;
-        const float ch = (1.0f - w) * p0.y + w * p1.y;
-        ln[k] = make_float2(fmaxf(ch, 0.0f) * a.kline[l] * ib, ch > 0.0f ? et / ch : 0.0f);
+        const float2 p0 = w.ln[bf][k][i + 1];
+        const float2 p1 = w.ln[bf][k][i];
+        const float et = (1.0f - wt) * p0.x + wt * p1.x;
+        const float ch = (1.0f - wt) * p0.y + wt * p1.y;
+        ln[k] = make_float2(fmaxf(ch, 0.0f) * a.kline[l] * ib, ch > 0.0f ? et * rcpf(ch) : 0.0f);
         far = far && (ln[k].x * wing < a.chi_min);
     }
     g.w = far ? 1.0f : 0.0f;
@@ -420,16 +499,24 @@ __device__ __forceinline__ void step_point(const SweepK &a, BinState<NB> &st, co
 
 // Sweeps half-ray r from its far end to the origin; returns per bin (Phi^ iota, psi^,
 // delta) of the row next to the origin, or the empty-half values (sqrt 2, sqrt 2 I_o, 0).
+// `pre` says that buffer bf already holds (or is receiving) the first window of r; on
+// return it says the same of rnext (the half-ray swept next, -1 for none).
 template <int G, int NB, bool SKIP>
 __device__ __forceinline__ void sweep_half(const MixArgs &a, const SweepK &k, int64_t o, int l0, int grp, int r,
-                                           float nu_g, const float4 go, const float2 dlo, RingGeom *rg, float2 *rl,
-                                           BinState<NB> &st, float (&pi)[NB], float (&ps)[NB], float (&dt)[NB],
-                                           float aq_lo, float aq_hi) {
+                                           int rnext, float nu_g, const float4 go, const float2 dlo, RingGeom *rg,
+                                           float2 *rl, ElemWin<G> &w, int &bf, bool &pre, BinState<NB> &st,
+                                           float (&pi)[NB], float (&ps)[NB], float (&dt)[NB], float aq_lo,
+                                           float aq_hi) {
     const int lane = threadIdx.x & 31;
     const int64_t off = a.ray_off[o * a.R + r];
     const int len = (int)(a.ray_off[o * a.R + r + 1] - off);
-    const int Kh = len ? a.xcum[off + len - 1] : 0;
-    if (Kh == 0) {
+    int64_t offn = 0;
+    int lenn = 0;
+    if (rnext >= 0) {
+        offn = a.ray_off[o * a.R + rnext];
+        lenn = (int)(a.ray_off[o * a.R + rnext + 1] - offn);
+    }
+    if (len == 0) {   // an empty half is never prefetched, so `pre` is false here
 #pragma unroll
         for (int i = 0; i < NB; i++) {
             pi[i] = kSqrt2;
@@ -438,28 +525,58 @@ __device__ __forceinline__ void sweep_half(const MixArgs &a, const SweepK &k, in
         }
         return;
     }
+    if (!pre) {
+        win_records<G>(a, off, len - 1, (int32_t)o, w, bf);
+        cp_async_wait_all();
+        win_gathers<G>(a, l0, w, bf);
+    }
+    pre = false;
     const float2 *my = rl + grp * kRing;
-    int anchor = len - 1;      // element holding the next point to stage
-    int xnext = Kh - 1;        // next point to stage (descending towards the origin)
+    int top = len - 1;         // element in window slot 0; it holds point xnext
+    int xnext = -1;            // next point to stage (descending towards the origin)
     float qds_p = 0.0f;
     bool first = true, far1 = false, far2 = false;
-    while (xnext >= 0) {
-        const int cnt = min(kRing, xnext + 1);
+    do {
+        cp_async_wait_all();
         __syncwarp();
-        int e = anchor;
+        if (first) xnext = w.x1[bf][0] - 1;
+        // Owner slot of the point of each lane: slot i's element starts at chunk position
+        // xnext - xcum + 1 (<= 0 for slot 0); the owner of position j is the last slot
+        // starting at or before j.
+        const int pos = xnext - w.x1[bf][lane] + 1;
+        const unsigned bit = (top - lane >= 0 && pos < 32) ? (1u << (pos > 0 ? pos : 0)) : 0u;
+        const unsigned starts = __reduce_or_sync(0xffffffffu, bit);
+        const int own = __popc(starts & (0xffffffffu >> (31 - lane))) - 1;
+        const int cnt = min(kRing, xnext + 1);
         bool my_far = false;
+        int top_next = 0;
         if (lane < cnt) {
             float4 g;
             float2 ln[G];
-            stage_ring_point<G>(a, o, l0, off, xnext - lane, e, g, ln, aq_lo, aq_hi);
+            const int x = xnext - lane;
+            stage_ring_point<G>(a, w, bf, own, l0, x, g, ln, aq_lo, aq_hi);
             rg[lane].g = g;
             my_far = g.w != 0.0f;
 #pragma unroll
-            for (int k = 0; k < G; k++) rl[k * kRing + lane] = ln[k];
+            for (int kk = 0; kk < G; kk++) rl[kk * kRing + lane] = ln[kk];
+            // element of point x - 1: this point's own, or the next one if x opens it
+            top_next = top - own - (w.x1[bf][own + 1] == x ? 1 : 0);
         }
         const unsigned farmask = SKIP ? __ballot_sync(0xffffffffu, my_far) : 0u;
-        anchor = __shfl_sync(0xffffffffu, e, cnt - 1);
+        top_next = __shfl_sync(0xffffffffu, top_next, cnt - 1);
         __syncwarp();
+        // the next window: the rest of this half-ray, else the start of the next one
+        const bool more = xnext - cnt >= 0;
+        const bool issue = more || lenn > 0;
+        if (more) win_records<G>(a, off, top_next, (int32_t)o, w, bf ^ 1);
+        else if (lenn > 0) win_records<G>(a, offn, lenn - 1, (int32_t)o, w, bf ^ 1);
+        const int nb = bf ^ 1;
+        auto gathers = [&]() {
+            if (issue) {
+                cp_async_wait_all();
+                win_gathers<G>(a, l0, w, nb);
+            }
+        };
         int j = 0;
         if (first) {
             const float4 g = rg[0].g;
@@ -471,30 +588,40 @@ __device__ __forceinline__ void sweep_half(const MixArgs &a, const SweepK &k, in
             j = 1;
             first = false;
         }
+        // The chunk is swept in two segments, points [0, 16) and [16, cnt), with the
+        // gathers of the next window issued between them (one copy of each loop body).
+        const int mid = cnt < 16 ? cnt : 16;
         if (SKIP) {
             // A point whose own and two previous points are all far changes the state by
             // O(chi_min ds) only (no-ops in FP32): rows that involve a non-floored interval
             // are still computed exactly. The points to process come from the chunk's
             // ballot of far points (bit j = point j), so skipped points cost nothing.
-            const unsigned f1 = (farmask << 1) | (far1 ? 1u : 0u);                 // far(j-1)
+            const unsigned f1 = (farmask << 1) | (far1 ? 1u : 0u);                     // far(j-1)
             const unsigned f2 = (farmask << 2) | (far1 ? 2u : 0u) | (far2 ? 1u : 0u);   // far(j-2)
             const unsigned all = cnt == 32 ? 0xffffffffu : ((1u << cnt) - 1u);
             unsigned proc = ~(farmask & f1 & f2) & all;
-            if (proc == all) {   // nothing to skip in this chunk: the unrolled sweep
+            if (j) proc &= ~1u;   // point 0 of the first chunk is the far end, done above
+            const bool dense = (proc | (j ? 1u : 0u)) == all;
+#pragma unroll 1
+            for (int seg = 0; seg < 2; seg++) {
+                if (dense) {   // nothing to skip in this chunk: the unrolled sweep
+                    const int jend = seg ? cnt : mid;
 #pragma unroll 4
-                for (; j < cnt; j++) {
-                    const float4 g = rg[j].g;
-                    step_point<NB>(k, st, g, my[j], qds_p);
-                    qds_p = g.x;
+                    for (; j < jend; j++) {
+                        const float4 g = rg[j].g;
+                        step_point<NB>(k, st, g, my[j], qds_p);
+                        qds_p = g.x;
+                    }
+                } else {
+                    unsigned bits = proc & (seg ? 0xffff0000u : 0x0000ffffu);
+                    while (bits) {
+                        const int jj = __ffs(bits) - 1;
+                        bits &= bits - 1u;
+                        const float qprev = jj ? rg[jj - 1].g.x : qds_p;
+                        step_point<NB>(k, st, rg[jj].g, my[jj], qprev);
+                    }
                 }
-            } else {
-                if (j) proc &= ~1u;   // point 0 of the first chunk is the far end, done above
-                while (proc) {
-                    const int jj = __ffs(proc) - 1;
-                    proc &= proc - 1u;
-                    const float qprev = jj ? rg[jj - 1].g.x : qds_p;
-                    step_point<NB>(k, st, rg[jj].g, my[jj], qprev);
-                }
+                if (seg == 0) gathers();
             }
             qds_p = rg[cnt - 1].g.x;
             if (cnt >= 2) {
@@ -505,15 +632,23 @@ __device__ __forceinline__ void sweep_half(const MixArgs &a, const SweepK &k, in
                 far1 = farmask & 1u;
             }
         } else {
+#pragma unroll 1
+            for (int seg = 0; seg < 2; seg++) {
+                const int jend = seg ? cnt : mid;
 #pragma unroll 4
-            for (; j < cnt; j++) {
-                const float4 g = rg[j].g;
-                step_point<NB>(k, st, g, my[j], qds_p);
-                qds_p = g.x;
+                for (; j < jend; j++) {
+                    const float4 g = rg[j].g;
+                    step_point<NB>(k, st, g, my[j], qds_p);
+                    qds_p = g.x;
+                }
+                if (seg == 0) gathers();
             }
         }
+        bf = nb;
+        top = top_next;
         xnext -= cnt;
-    }
+        if (!more) pre = issue;
+    } while (xnext >= 0);
     step_point<NB>(k, st, go, dlo, qds_p);   // the origin
 #pragma unroll
     for (int i = 0; i < NB; i++) {
@@ -523,9 +658,19 @@ __device__ __forceinline__ void sweep_half(const MixArgs &a, const SweepK &k, in
     }
 }
 
+// Per-lane, per-bin values that live across the ray pairs (slot [.][i][lane]): the pair
+// sums and the backward half's result while the forward half is swept. Held in shared
+// memory so that the sweeps keep their registers for the recursion.
+template <int NB>
+struct PairSmem {
+    float acc[4][NB][32];
+    float pi[NB][32], ps[NB][32], dt[NB][32];   // backward half: (Phi^ iota, psi^, delta)
+};
+
 // One work item: origin o, lines l0 .. l0+G-1, all ray pairs, all bins (one warp).
 template <int G, int NB, bool SKIP>
-__device__ __forceinline__ void solve_item(const MixArgs &a, int64_t o, int l0, RingGeom *rg, float2 *rl) {
+__device__ __forceinline__ void solve_item(const MixArgs &a, int64_t o, int l0, RingGeom *rg, float2 *rl,
+                                           ElemWin<G> &w, PairSmem<NB> &ps) {
     constexpr int LPG = 32 / G;   // lanes per line
     const int lane = threadIdx.x & 31;
     const int grp = lane / LPG, li = lane - grp * LPG;
@@ -541,18 +686,11 @@ __device__ __forceinline__ void solve_item(const MixArgs &a, int64_t o, int l0, 
     const float nu_g = a.nu_ghz[lc];
     const SweepK k{a.chi_min, a.inv_chi_min, a.dtau_min, a.planck_a, a.planck_b};
     BinState<NB> st;
-    float acc[NB][4];
-    float chio[NB], Sov[NB], chilo[NB];
 #pragma unroll
     for (int i = 0; i < NB; i++) {
         const int q = li + LPG * i;
         st.aq[i] = q < Q ? (float)(a.roots[q] * (double)bo) : 0.0f;
-        acc[i][0] = acc[i][1] = acc[i][2] = acc[i][3] = 0.0f;
-        const float x = st.aq[i] * go.z;
-        const float chil = dlo.x * ex2f(-x * x);
-        chilo[i] = chil;
-        chio[i] = fmaxf(chil, a.chi_min);
-        Sov[i] = fminf(dlo.y, chil * dlo.y * a.inv_chi_min);
+        ps.acc[0][i][lane] = ps.acc[1][i][lane] = ps.acc[2][i][lane] = ps.acc[3][i][lane] = 0.0f;
     }
     // range of a_q over the whole warp (all lanes, all bins)
     float aq_lo = 1e30f, aq_hi = -1e30f;
@@ -565,47 +703,70 @@ __device__ __forceinline__ void solve_item(const MixArgs &a, int64_t o, int l0, 
         aq_lo = fminf(aq_lo, __shfl_xor_sync(0xffffffffu, aq_lo, d));
         aq_hi = fmaxf(aq_hi, __shfl_xor_sync(0xffffffffu, aq_hi, d));
     }
+    int bf = 0;
+    bool pre = false;
     for (int p = 0; p < a.P; p++) {
-        float pib[NB], psb[NB], dtb[NB], pif[NB], psf[NB], dtf[NB];
-        sweep_half<G, NB, SKIP>(a, k, o, l0, grp, a.pb[p], nu_g, go, dlo, rg, rl, st, pib, psb, dtb, aq_lo, aq_hi);
-        sweep_half<G, NB, SKIP>(a, k, o, l0, grp, a.pf[p], nu_g, go, dlo, rg, rl, st, pif, psf, dtf, aq_lo, aq_hi);
+        const int rb = a.pb[p], rf = a.pf[p];
+        const int rn = p + 1 < a.P ? a.pb[p + 1] : -1;
+        float pif[NB], psf[NB], dtf[NB];
+#pragma unroll 1
+        for (int h = 0; h < 2; h++) {   // backward half, then forward half (one code copy)
+            sweep_half<G, NB, SKIP>(a, k, o, l0, grp, h ? rf : rb, h ? rn : rf, nu_g, go, dlo, rg, rl, w, bf, pre,
+                                    st, pif, psf, dtf, aq_lo, aq_hi);
+            if (h == 0) {
+#pragma unroll
+                for (int i = 0; i < NB; i++) {
+                    ps.pi[i][lane] = pif[i];
+                    ps.ps[i][lane] = psf[i];
+                    ps.dt[i][lane] = dtf[i];
+                }
+            }
+        }
 #pragma unroll
         for (int i = 0; i < NB; i++) {
+            const float pib = ps.pi[i][lane], psb = ps.ps[i][lane], dtb = ps.dt[i][lane];
+            // the origin's line opacity, floored opacity and floored source in this bin
+            const float xo = st.aq[i] * go.z;
+            const float chilo = dlo.x * ex2f(-xo * xo);
+            const float chio = fmaxf(chilo, k.chi_min);
+            const float Sov = fminf(dlo.y, chilo * dlo.y * k.inv_chi_min);
             float u, lam, uml, oml;
-            if (dtb[i] == 0.0f && dtf[i] == 0.0f) {   // isolated origin: both halves empty
-                u = psb[i] * (float)(1.0 / 1.4142135623730951); lam = 0.0f; uml = u; oml = 1.0f;
+            if (dtb == 0.0f && dtf[i] == 0.0f) {   // isolated origin: both halves empty
+                u = psb * (float)(1.0 / 1.4142135623730951); lam = 0.0f; uml = u; oml = 1.0f;
             } else {
                 // sigma (Phi iota) = Phi^ iota / (delta_- + delta_+), sigma psi = psi^ / (delta_- + delta_+)
-                const float sig = 1.0f / (dtb[i] + dtf[i]);
-                const float pi2 = pib[i] + pif[i];
+                const float sig = 1.0f / (dtb + dtf[i]);
+                const float pi2 = pib + pif[i];
                 const float iD = 1.0f / fmaf(sig, pi2, 1.0f);
-                const float s2 = sig * (psb[i] + psf[i]);
-                u = (Sov[i] + s2) * iD;
+                const float s2 = sig * (psb + psf[i]);
+                u = (Sov + s2) * iD;
                 lam = iD;
                 uml = s2 * iD;
                 oml = sig * pi2 * iD;
             }
-            const float ichi = 1.0f / chio[i];
-            acc[i][0] += u;
-            acc[i][1] += lam * chilo[i] * ichi;
-            acc[i][2] += uml + lam * (Sov[i] * chio[i] - chilo[i] * dlo.y) * ichi;
-            acc[i][3] += oml + lam * (chio[i] - chilo[i]) * ichi;
+            const float ichi = 1.0f / chio;
+            ps.acc[0][i][lane] += u;
+            ps.acc[1][i][lane] += lam * chilo * ichi;
+            ps.acc[2][i][lane] += uml + lam * (Sov * chio - chilo * dlo.y) * ichi;
+            ps.acc[3][i][lane] += oml + lam * (chio - chilo) * ichi;
         }
     }
+    cp_async_wait_all();
     // weighted sums over each line's bins: fixed shuffle tree in FP64 within the lane group
     const double invP = 1.0 / a.P;
     double s[4] = {0.0, 0.0, 0.0, 0.0};
 #pragma unroll
     for (int i = 0; i < NB; i++) {
         const int q = li + LPG * i;
-        const double w = q < Q ? a.weights[q] : 0.0;
+        const double wq = q < Q ? a.weights[q] : 0.0;
 #pragma unroll
-        for (int k = 0; k < 4; k++) s[k] += w * (double)acc[i][k];
-        if (a.Jnu && q < Q && line_ok) a.Jnu[(o * a.L + l) * Q + q] = (double)acc[i][0] * invP * (double)kI0;
+        for (int kk = 0; kk < 4; kk++) s[kk] += wq * (double)ps.acc[kk][i][lane];
+        if (a.Jnu && q < Q && line_ok)
+            a.Jnu[(o * a.L + l) * Q + q] = (double)ps.acc[0][i][lane] * invP * (double)kI0;
     }
 #pragma unroll
-    for (int k = 0; k < 4; k++)
-        for (int d = LPG / 2; d; d >>= 1) s[k] += __shfl_down_sync(0xffffffffu, s[k], d);
+    for (int kk = 0; kk < 4; kk++)
+        for (int d = LPG / 2; d; d >>= 1) s[kk] += __shfl_down_sync(0xffffffffu, s[kk], d);
     if (li == 0 && line_ok) {
         a.J[o * a.L + l] = s[0] * invP * (double)kI0;
         a.Lout[o * a.L + l] = s[1] * invP;
@@ -618,13 +779,15 @@ template <int G, int NB, int MINB, bool SKIP>
 __global__ void __launch_bounds__(32 * kWarps2, MINB) k_feautrier_warp(MixArgs a) {
     __shared__ RingGeom rgs[kWarps2][kRing];
     __shared__ float2 rls[kWarps2][G * kRing];
+    __shared__ ElemWin<G> ews[kWarps2];
+    __shared__ PairSmem<NB> pss[kWarps2];
     const int warp = threadIdx.x >> 5;
     const int ngroups = (a.L + G - 1) / G;
     const int64_t item = (int64_t)blockIdx.x * kWarps2 + warp;
     if (item >= a.n * ngroups) return;
     const int64_t o = item / ngroups;
     const int l0 = (int)(item - o * ngroups) * G;
-    solve_item<G, NB, SKIP>(a, o, l0, rgs[warp], rls[warp]);
+    solve_item<G, NB, SKIP>(a, o, l0, rgs[warp], rls[warp], ews[warp], pss[warp]);
 }
 
 // Persistent variant over a batch of models: every warp takes work items (model, origin,
@@ -641,6 +804,8 @@ k_feautrier_batch(const MixArgs *__restrict__ models, const BatchItem *__restric
                   unsigned long long *counter, const int32_t *__restrict__ active) {
     __shared__ RingGeom rgs[kWarps2][kRing];
     __shared__ float2 rls[kWarps2][G * kRing];
+    __shared__ ElemWin<G> ews[kWarps2];
+    __shared__ PairSmem<NB> pss[kWarps2];
     __shared__ MixArgs sa[kWarps2];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (;;) {
@@ -656,7 +821,7 @@ k_feautrier_batch(const MixArgs *__restrict__ models, const BatchItem *__restric
         const MixArgs &a = sa[warp];
         const int64_t o = it.local / a.L;
         const int l0 = (int)(it.local - o * a.L);
-        solve_item<G, NB, SKIP>(a, o, l0, rgs[warp], rls[warp]);
+        solve_item<G, NB, SKIP>(a, o, l0, rgs[warp], rls[warp], ews[warp], pss[warp]);
     }
 }
 
@@ -672,11 +837,13 @@ const WarpVariant kWarpVariants[] = {
     // with far-wing skipping
     MG_VARIANT(1, 1, 8, true), MG_VARIANT(1, 1, 10, true), MG_VARIANT(2, 2, 4, true), MG_VARIANT(2, 2, 5, true),
     MG_VARIANT(2, 2, 6, true), MG_VARIANT(1, 2, 4, true), MG_VARIANT(1, 2, 6, true), MG_VARIANT(1, 4, 3, true),
-    MG_VARIANT(1, 4, 4, true),
+    MG_VARIANT(1, 4, 4, true), MG_VARIANT(2, 4, 3, true), MG_VARIANT(2, 4, 4, true), MG_VARIANT(4, 4, 3, true),
+    MG_VARIANT(4, 4, 4, true),
     // the same shapes without skipping (every point swept)
     MG_VARIANT(1, 1, 8, false), MG_VARIANT(1, 1, 10, false), MG_VARIANT(2, 2, 4, false), MG_VARIANT(2, 2, 5, false),
     MG_VARIANT(2, 2, 6, false), MG_VARIANT(1, 2, 4, false), MG_VARIANT(1, 2, 6, false), MG_VARIANT(1, 4, 3, false),
-    MG_VARIANT(1, 4, 4, false),
+    MG_VARIANT(1, 4, 4, false), MG_VARIANT(2, 4, 3, false), MG_VARIANT(2, 4, 4, false), MG_VARIANT(4, 4, 3, false),
+    MG_VARIANT(4, 4, 4, false),
 };
 #undef MG_VARIANT
 constexpr int kNumWarpVariants = sizeof(kWarpVariants) / sizeof(kWarpVariants[0]);
@@ -684,7 +851,7 @@ constexpr int kNumWarpVariants = sizeof(kWarpVariants) / sizeof(kWarpVariants[0]
 bool variant_valid(int v, int L, int Q) {
     if (v < 0 || v >= kNumWarpVariants) return false;
     const WarpVariant &w = kWarpVariants[v];
-    if (w.G == 2 && L < 2) return false;
+    if (w.G > L) return false;
     return Q <= w.NB * (32 / w.G) && Q > (w.NB == 1 ? 0 : (w.NB / 2) * (32 / w.G));
 }
 
@@ -759,7 +926,7 @@ static int launch_mixed(mg_ctx *ctx, int variant) {
 // Default launch variant for a model: two lines per warp with two bins per lane when the
 // lines have <= 32 bins, otherwise one line per warp with as many bins per lane as needed.
 static int default_variant(int L, int Q) {
-    const int order[] = {4, 3, 2, 0, 1, 6, 5, 8, 7, 13, 12, 11, 9, 10, 15, 14, 17, 16};
+    const int order[] = {4, 3, 2, 0, 1, 6, 5, 8, 7, 12, 11, 10, 9, 17, 16, 15, 13, 14, 19, 18, 21, 20, 25, 24, 23, 22};
     for (int v : order)
         if (variant_valid(v, L, Q)) return v;
     return -1;
