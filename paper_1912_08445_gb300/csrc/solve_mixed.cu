@@ -400,23 +400,29 @@ __device__ __forceinline__ float planck_k(const SweepK &k, float nu_g) {
     return k.planck_a * nu_g * nu_g * nu_g / expm1f(k.planck_b * nu_g);
 }
 
-struct RingGeom {
-    // (ds / (2 sqrt 2) to the next point towards the origin, sqrt(log2 e) v/b,
-    //  sqrt(log2 e)(1 - v/c)/b, unused): the profile argument of bin a_q is then
-    //  x' = a_q g.z - g.y and the half-width interval factor yields delta = dtau/sqrt 2.
-    float4 g;
+// One staged point of the ring. The per-point scalars are stored twice so that a bin
+// pair reads them as the operand pairs of packed FP32x2 arithmetic:
+//   a = (g_z, g_z, -g_y, -g_y) with g_y = sqrt(log2 e) v/b and g_z = sqrt(log2 e)(1 - v/c)/b,
+//       so that the profile argument of bin a_q is x' = a_q g_z - g_y;
+//   b = (q, q, far, 0) with q = ds/(2 sqrt 2) to the next point towards the origin (the
+//       half-width interval factor that yields delta = dtau/sqrt 2).
+// The line data of a point are (X, X, S, S) per line: chi_l = X 2^(-x'^2) and the floored
+// source is S_eff = S min(chi_l/chi_min, 1), which is eta/chi with chi = max(chi_l, chi_min)
+// (exactly S where the line is not floored; finite for any finite S).
+struct RingPt {
+    float4 a, b;
 };
 
 // Expanded point x of the element in window slot i (sub-point (x - x0 + 1)/(ns + 1) of the
 // interval from the element's predecessor towards the origin to its own cell).
 // A point is "far" for the warp when every bin of the warp lies so far in the wings of
 // every line of its group that the opacity is floored there: X 2^(-x'^2) < chi_min with
-// x' = a_q g.z - g.y over the warp's range of a_q (monotonic in a_q, so the smallest
-// |x'| is at an end of the range or zero). Flagged in g.w. The divisions here use the
-// approximate reciprocal (the path computes in FP32).
+// x' = a_q g_z - g_y over the warp's range of a_q (monotonic in a_q, so the smallest
+// |x'| is at an end of the range or zero). The divisions here use the approximate
+// reciprocal (the path computes in FP32).
 template <int G>
 __device__ __forceinline__ void stage_ring_point(const MixArgs &a, const ElemWin<G> &w, int bf, int i, int l0, int x,
-                                                 float4 &g, float2 (&ln)[G], float aq_lo, float aq_hi) {
+                                                 RingPt &pt, float4 *ln, float aq_lo, float aq_hi) {
     const int x0 = w.x1[bf][i + 1];
     const int ns = w.x1[bf][i] - x0 - 1;
     const float rn = rcpf((float)(ns + 1));
@@ -427,8 +433,8 @@ __device__ __forceinline__ void stage_ring_point(const MixArgs &a, const ElemWin
     const float bb = (1.0f - wt) * w.b[bf][i + 1] + wt * w.b[bf][i];
     const float ib = rcpf(bb);
     const float pz = kSqrtLog2e * ib;
-    g = make_float4(qds, v * pz, (1.0f - v * (float)(1.0 / kC)) * pz, 0.0f);
-    const float xlo = aq_lo * g.z - g.y, xhi = aq_hi * g.z - g.y;
+    const float gy = v * pz, gz = (1.0f - v * (float)(1.0 / kC)) * pz;
+    const float xlo = aq_lo * gz - gy, xhi = aq_hi * gz - gy;
     const float xm = xlo > 0.0f ? xlo : (xhi < 0.0f ? -xhi : 0.0f);
     const float wing = ex2f(-xm * xm);
     bool far = true;
@@ -439,61 +445,137 @@ __device__ __forceinline__ void stage_ring_point(const MixArgs &a, const ElemWin
         const float2 p1 = w.ln[bf][k][i];
         const float et = (1.0f - wt) * p0.x + wt * p1.x;
         const float ch = (1.0f - wt) * p0.y + wt * p1.y;
-        ln[k] = make_float2(fmaxf(ch, 0.0f) * a.kline[l] * ib, ch > 0.0f ? et * rcpf(ch) : 0.0f);
-        far = far && (ln[k].x * wing < a.chi_min);
+        const float X = fmaxf(ch, 0.0f) * a.kline[l] * ib;
+        // (a line whose opacity is below the smallest normal float has no source here)
+        const float S = ch >= 1.17549435e-38f ? et * rcpf(ch) : 0.0f;
+        ln[k * kRing] = make_float4(X, X, S, S);   // line k's slot of this point
+        far = far && (X * wing < a.chi_min);
     }
-    g.w = far ? 1.0f : 0.0f;
+    pt.a = make_float4(gz, gz, -gy, -gy);
+    pt.b = make_float4(qds, qds, far ? 1.0f : 0.0f, 0.0f);
 }
 
 // Per-bin sweep state in the variables delta = dtau/sqrt 2, Phi^ = sqrt 2 Phi and
 // psi^ = sqrt 2 psi, in which the recursion carries no factor 1/2:
 //   s = delta_prev + delta,  Phi^ = s + Phi^_prev iota_prev,  iota = 1/(1 + delta Phi^),
 //   psi^ = (s S_prev + psi^_prev) iota.
+// Bins 2p and 2p+1 of a lane form pair p and are updated together with packed FP32x2
+// arithmetic (fma/mul/add on float2); an odd last bin is updated alone.
 template <int NB>
 struct BinState {
-    float aq[NB];
-    float chi_p[NB], S_p[NB], d_p[NB], Phi[NB], iota[NB], psi[NB];
+    static constexpr int NP = NB / 2;
+    static constexpr bool ODD = (NB & 1) != 0;
+    float2 aq2[NP > 0 ? NP : 1], chi_p2[NP > 0 ? NP : 1], S_p2[NP > 0 ? NP : 1], d_p2[NP > 0 ? NP : 1];
+    float2 Phi2[NP > 0 ? NP : 1], iota2[NP > 0 ? NP : 1], psi2[NP > 0 ? NP : 1];
+    float aq1, chi_p1, S_p1, d_p1, Phi1, iota1, psi1;
+    __device__ __forceinline__ float aq(int i) const {
+        return i < 2 * NP ? ((i & 1) ? aq2[i >> 1].y : aq2[i >> 1].x) : aq1;
+    }
+    __device__ __forceinline__ void set_aq(int i, float v) {
+        if (i < 2 * NP) {
+            if (i & 1) aq2[i >> 1].y = v; else aq2[i >> 1].x = v;
+        } else {
+            aq1 = v;
+        }
+    }
 };
+
+__device__ __forceinline__ float2 ex2f2(const float2 t) { return make_float2(ex2f(-t.x), ex2f(-t.y)); }
 
 // The far end of a half: the boundary row is the interior update from the virtual state
 // Phi^ iota = sqrt 2, psi^ = sqrt 2 I, delta = 0.
 template <int NB>
-__device__ __forceinline__ void first_point(const SweepK &a, BinState<NB> &st, const float4 g, const float2 d,
+__device__ __forceinline__ void first_point(const SweepK &k, BinState<NB> &st, const float4 A, const float4 D,
                                             const float nu_g, const float v) {
-    const float SI = d.y * a.inv_chi_min;
+    const float2 gz = make_float2(A.x, A.y), ngy = make_float2(A.z, A.w);
+    const float2 X = make_float2(D.x, D.y), S = make_float2(D.z, D.w);
+    const float2 icm = make_float2(k.inv_chi_min, k.inv_chi_min);
+    const float dop = 1.0f - v * (float)(1.0 / kC);
 #pragma unroll
-    for (int i = 0; i < NB; i++) {
-        const float x = fmaf(st.aq[i], g.z, -g.y);
-        const float chil = d.x * ex2f(-x * x);
-        st.chi_p[i] = fmaxf(chil, a.chi_min);
-        st.S_p[i] = fminf(d.y, chil * SI);
-        st.Phi[i] = kSqrt2;
-        st.iota[i] = 1.0f;
-        st.d_p[i] = 0.0f;
-        const float A1 = 1.0f + st.aq[i] * (float)(1.0 / kC);
-        st.psi[i] = kSqrt2 * planck_k(a, nu_g * A1 * (1.0f - v * (float)(1.0 / kC)));
+    for (int p = 0; p < BinState<NB>::NP; p++) {
+        const float2 x = __ffma2_rn(st.aq2[p], gz, ngy);
+        const float2 chil = __fmul2_rn(X, ex2f2(__fmul2_rn(x, x)));
+        st.chi_p2[p] = make_float2(fmaxf(chil.x, k.chi_min), fmaxf(chil.y, k.chi_min));
+        const float2 t = __fmul2_rn(chil, icm);
+        st.S_p2[p] = __fmul2_rn(S, make_float2(fminf(t.x, 1.0f), fminf(t.y, 1.0f)));
+        st.Phi2[p] = make_float2(kSqrt2, kSqrt2);
+        st.iota2[p] = make_float2(1.0f, 1.0f);
+        st.d_p2[p] = make_float2(0.0f, 0.0f);
+        st.psi2[p] = make_float2(kSqrt2 * planck_k(k, nu_g * (1.0f + st.aq2[p].x * (float)(1.0 / kC)) * dop),
+                                 kSqrt2 * planck_k(k, nu_g * (1.0f + st.aq2[p].y * (float)(1.0 / kC)) * dop));
+    }
+    if constexpr (BinState<NB>::ODD) {
+        const float x = fmaf(st.aq1, gz.x, ngy.x);
+        const float chil = X.x * ex2f(-x * x);
+        st.chi_p1 = fmaxf(chil, k.chi_min);
+        st.S_p1 = S.x * fminf(chil * k.inv_chi_min, 1.0f);
+        st.Phi1 = kSqrt2;
+        st.iota1 = 1.0f;
+        st.d_p1 = 0.0f;
+        st.psi1 = kSqrt2 * planck_k(k, nu_g * (1.0f + st.aq1 * (float)(1.0 / kC)) * dop);
     }
 }
 
-// Update with the interval (previous point, this point), qds_p = ds/(2 sqrt 2).
+// Update with the interval (previous point, this point); qp = (q, q) of that interval,
+// A and D the point's ring entries.
 template <int NB>
-__device__ __forceinline__ void step_point(const SweepK &a, BinState<NB> &st, const float4 g, const float2 d,
-                                           const float qds_p) {
-    const float SI = d.y * a.inv_chi_min;
+__device__ __forceinline__ void step_point(const SweepK &k, BinState<NB> &st, const float4 A, const float4 D,
+                                           const float2 qp) {
+    const float2 gz = make_float2(A.x, A.y), ngy = make_float2(A.z, A.w);
+    const float2 X = make_float2(D.x, D.y), S = make_float2(D.z, D.w);
+    const float2 icm = make_float2(k.inv_chi_min, k.inv_chi_min);
 #pragma unroll
-    for (int i = 0; i < NB; i++) {
-        const float x = fmaf(st.aq[i], g.z, -g.y);
-        const float chil = d.x * ex2f(-x * x);
-        const float chi = fmaxf(chil, a.chi_min);
-        const float Sx = fminf(d.y, chil * SI);
-        const float dl = fmaxf((st.chi_p[i] + chi) * qds_p, a.dtau_min);
-        const float sm = st.d_p[i] + dl;
-        st.Phi[i] = fmaf(st.Phi[i], st.iota[i], sm);
-        st.iota[i] = rcpf(fmaf(dl, st.Phi[i], 1.0f));
-        st.psi[i] = fmaf(sm, st.S_p[i], st.psi[i]) * st.iota[i];
-        st.d_p[i] = dl;
-        st.chi_p[i] = chi;
-        st.S_p[i] = Sx;
+    for (int p = 0; p < BinState<NB>::NP; p++) {
+        const float2 x = __ffma2_rn(st.aq2[p], gz, ngy);
+        const float2 chil = __fmul2_rn(X, ex2f2(__fmul2_rn(x, x)));
+        const float2 chi = make_float2(fmaxf(chil.x, k.chi_min), fmaxf(chil.y, k.chi_min));
+        const float2 t = __fmul2_rn(chil, icm);
+        const float2 Sx = __fmul2_rn(S, make_float2(fminf(t.x, 1.0f), fminf(t.y, 1.0f)));
+        const float2 d0 = __fmul2_rn(__fadd2_rn(st.chi_p2[p], chi), qp);
+        const float2 dl = make_float2(fmaxf(d0.x, k.dtau_min), fmaxf(d0.y, k.dtau_min));
+        const float2 sm = __fadd2_rn(st.d_p2[p], dl);
+        st.Phi2[p] = __ffma2_rn(st.Phi2[p], st.iota2[p], sm);
+        const float2 den = __ffma2_rn(dl, st.Phi2[p], make_float2(1.0f, 1.0f));
+        st.iota2[p] = make_float2(rcpf(den.x), rcpf(den.y));
+        st.psi2[p] = __fmul2_rn(__ffma2_rn(sm, st.S_p2[p], st.psi2[p]), st.iota2[p]);
+        st.d_p2[p] = dl;
+        st.chi_p2[p] = chi;
+        st.S_p2[p] = Sx;
+    }
+    if constexpr (BinState<NB>::ODD) {
+        const float x = fmaf(st.aq1, gz.x, ngy.x);
+        const float chil = X.x * ex2f(-x * x);
+        const float chi = fmaxf(chil, k.chi_min);
+        const float Sx = S.x * fminf(chil * k.inv_chi_min, 1.0f);
+        const float dl = fmaxf((st.chi_p1 + chi) * qp.x, k.dtau_min);
+        const float sm = st.d_p1 + dl;
+        st.Phi1 = fmaf(st.Phi1, st.iota1, sm);
+        st.iota1 = rcpf(fmaf(dl, st.Phi1, 1.0f));
+        st.psi1 = fmaf(sm, st.S_p1, st.psi1) * st.iota1;
+        st.d_p1 = dl;
+        st.chi_p1 = chi;
+        st.S_p1 = Sx;
+    }
+}
+
+// (Phi^ iota, psi^, delta) of every bin.
+template <int NB>
+__device__ __forceinline__ void bin_results(const BinState<NB> &st, float (&pi)[NB], float (&ps)[NB],
+                                            float (&dt)[NB]) {
+#pragma unroll
+    for (int p = 0; p < BinState<NB>::NP; p++) {
+        const float2 pp = __fmul2_rn(st.Phi2[p], st.iota2[p]);
+        pi[2 * p] = pp.x;
+        pi[2 * p + 1] = pp.y;
+        ps[2 * p] = st.psi2[p].x;
+        ps[2 * p + 1] = st.psi2[p].y;
+        dt[2 * p] = st.d_p2[p].x;
+        dt[2 * p + 1] = st.d_p2[p].y;
+    }
+    if constexpr (BinState<NB>::ODD) {
+        pi[NB - 1] = st.Phi1 * st.iota1;
+        ps[NB - 1] = st.psi1;
+        dt[NB - 1] = st.d_p1;
     }
 }
 
@@ -503,8 +585,8 @@ __device__ __forceinline__ void step_point(const SweepK &a, BinState<NB> &st, co
 // return it says the same of rnext (the half-ray swept next, -1 for none).
 template <int G, int NB, bool SKIP>
 __device__ __forceinline__ void sweep_half(const MixArgs &a, const SweepK &k, int64_t o, int l0, int grp, int r,
-                                           int rnext, float nu_g, const float4 go, const float2 dlo, RingGeom *rg,
-                                           float2 *rl, ElemWin<G> &w, int &bf, bool &pre, BinState<NB> &st,
+                                           int rnext, float nu_g, const float4 Ao, const float4 Do, RingPt *rg,
+                                           float4 *rl, ElemWin<G> &w, int &bf, bool &pre, BinState<NB> &st,
                                            float (&pi)[NB], float (&ps)[NB], float (&dt)[NB], float aq_lo,
                                            float aq_hi) {
     const int lane = threadIdx.x & 31;
@@ -520,7 +602,7 @@ __device__ __forceinline__ void sweep_half(const MixArgs &a, const SweepK &k, in
 #pragma unroll
         for (int i = 0; i < NB; i++) {
             pi[i] = kSqrt2;
-            ps[i] = kSqrt2 * planck_k(k, nu_g * (1.0f + st.aq[i] * (float)(1.0 / kC)));
+            ps[i] = kSqrt2 * planck_k(k, nu_g * (1.0f + st.aq(i) * (float)(1.0 / kC)));
             dt[i] = 0.0f;
         }
         return;
@@ -531,10 +613,10 @@ __device__ __forceinline__ void sweep_half(const MixArgs &a, const SweepK &k, in
         win_gathers<G>(a, l0, w, bf);
     }
     pre = false;
-    const float2 *my = rl + grp * kRing;
+    const float4 *my = rl + grp * kRing;
     int top = len - 1;         // element in window slot 0; it holds point xnext
     int xnext = -1;            // next point to stage (descending towards the origin)
-    float qds_p = 0.0f;
+    float2 qp = make_float2(0.0f, 0.0f);   // (q, q) of the interval ending at the next point
     bool first = true, far1 = false, far2 = false;
     do {
         cp_async_wait_all();
@@ -551,14 +633,11 @@ __device__ __forceinline__ void sweep_half(const MixArgs &a, const SweepK &k, in
         bool my_far = false;
         int top_next = 0;
         if (lane < cnt) {
-            float4 g;
-            float2 ln[G];
+            RingPt pt;
             const int x = xnext - lane;
-            stage_ring_point<G>(a, w, bf, own, l0, x, g, ln, aq_lo, aq_hi);
-            rg[lane].g = g;
-            my_far = g.w != 0.0f;
-#pragma unroll
-            for (int kk = 0; kk < G; kk++) rl[kk * kRing + lane] = ln[kk];
+            stage_ring_point<G>(a, w, bf, own, l0, x, pt, rl + lane, aq_lo, aq_hi);
+            rg[lane] = pt;
+            my_far = pt.b.z != 0.0f;
             // element of point x - 1: this point's own, or the next one if x opens it
             top_next = top - own - (w.x1[bf][own + 1] == x ? 1 : 0);
         }
@@ -579,10 +658,11 @@ __device__ __forceinline__ void sweep_half(const MixArgs &a, const SweepK &k, in
         };
         int j = 0;
         if (first) {
-            const float4 g = rg[0].g;
-            const float vfar = g.y / (g.z + g.y * (float)(1.0 / kC));   // v = (v pz)/pz
-            first_point<NB>(k, st, g, my[0], nu_g, vfar);
-            qds_p = g.x;
+            const float4 A = rg[0].a;
+            const float vfar = -A.z / (A.x - A.z * (float)(1.0 / kC));   // v = (v pz)/pz
+            first_point<NB>(k, st, A, my[0], nu_g, vfar);
+            const float4 B = rg[0].b;
+            qp = make_float2(B.x, B.y);
             far1 = false;
             far2 = false;
             j = 1;
@@ -608,22 +688,29 @@ __device__ __forceinline__ void sweep_half(const MixArgs &a, const SweepK &k, in
                     const int jend = seg ? cnt : mid;
 #pragma unroll 4
                     for (; j < jend; j++) {
-                        const float4 g = rg[j].g;
-                        step_point<NB>(k, st, g, my[j], qds_p);
-                        qds_p = g.x;
+                        step_point<NB>(k, st, rg[j].a, my[j], qp);
+                        const float4 B = rg[j].b;
+                        qp = make_float2(B.x, B.y);
                     }
                 } else {
                     unsigned bits = proc & (seg ? 0xffff0000u : 0x0000ffffu);
                     while (bits) {
                         const int jj = __ffs(bits) - 1;
                         bits &= bits - 1u;
-                        const float qprev = jj ? rg[jj - 1].g.x : qds_p;
-                        step_point<NB>(k, st, rg[jj].g, my[jj], qprev);
+                        float2 qprev = qp;
+                        if (jj) {
+                            const float4 B = rg[jj - 1].b;
+                            qprev = make_float2(B.x, B.y);
+                        }
+                        step_point<NB>(k, st, rg[jj].a, my[jj], qprev);
                     }
                 }
                 if (seg == 0) gathers();
             }
-            qds_p = rg[cnt - 1].g.x;
+            {
+                const float4 B = rg[cnt - 1].b;
+                qp = make_float2(B.x, B.y);
+            }
             if (cnt >= 2) {
                 far1 = (farmask >> (cnt - 1)) & 1u;
                 far2 = (farmask >> (cnt - 2)) & 1u;
@@ -637,9 +724,9 @@ __device__ __forceinline__ void sweep_half(const MixArgs &a, const SweepK &k, in
                 const int jend = seg ? cnt : mid;
 #pragma unroll 4
                 for (; j < jend; j++) {
-                    const float4 g = rg[j].g;
-                    step_point<NB>(k, st, g, my[j], qds_p);
-                    qds_p = g.x;
+                    step_point<NB>(k, st, rg[j].a, my[j], qp);
+                    const float4 B = rg[j].b;
+                    qp = make_float2(B.x, B.y);
                 }
                 if (seg == 0) gathers();
             }
@@ -649,13 +736,8 @@ __device__ __forceinline__ void sweep_half(const MixArgs &a, const SweepK &k, in
         xnext -= cnt;
         if (!more) pre = issue;
     } while (xnext >= 0);
-    step_point<NB>(k, st, go, dlo, qds_p);   // the origin
-#pragma unroll
-    for (int i = 0; i < NB; i++) {
-        pi[i] = st.Phi[i] * st.iota[i];
-        ps[i] = st.psi[i];
-        dt[i] = st.d_p[i];
-    }
+    step_point<NB>(k, st, Ao, Do, qp);   // the origin
+    bin_results<NB>(st, pi, ps, dt);
 }
 
 // Per-lane, per-bin values that live across the ray pairs (slot [.][i][lane]): the pair
@@ -669,7 +751,7 @@ struct PairSmem {
 
 // One work item: origin o, lines l0 .. l0+G-1, all ray pairs, all bins (one warp).
 template <int G, int NB, bool SKIP>
-__device__ __forceinline__ void solve_item(const MixArgs &a, int64_t o, int l0, RingGeom *rg, float2 *rl,
+__device__ __forceinline__ void solve_item(const MixArgs &a, int64_t o, int l0, RingPt *rg, float4 *rl,
                                            ElemWin<G> &w, PairSmem<NB> &ps) {
     constexpr int LPG = 32 / G;   // lanes per line
     const int lane = threadIdx.x & 31;
@@ -681,15 +763,19 @@ __device__ __forceinline__ void solve_item(const MixArgs &a, int64_t o, int l0, 
     const float bo = a.b[o];
     const float ibo = 1.0f / bo;
     const float2 dl = reinterpret_cast<const float2 *>(a.line)[o * a.L + lc];
-    const float4 go = make_float4(0.0f, 0.0f, kSqrtLog2e * ibo, 0.0f);   // v = 0 at the origin
-    const float2 dlo = make_float2(fmaxf(dl.y, 0.0f) * a.kline[lc] * ibo, dl.y > 0.0f ? dl.x / dl.y : 0.0f);
+    // ring entries of the origin (v = 0 there): a = (g_z, g_z, -0, -0), line = (X, X, S, S)
+    const float gzo = kSqrtLog2e * ibo;
+    const float Xo = fmaxf(dl.y, 0.0f) * a.kline[lc] * ibo;
+    const float So = dl.y > 0.0f ? dl.x / dl.y : 0.0f;
+    const float4 Ao = make_float4(gzo, gzo, -0.0f, -0.0f);
+    const float4 Do = make_float4(Xo, Xo, So, So);
     const float nu_g = a.nu_ghz[lc];
     const SweepK k{a.chi_min, a.inv_chi_min, a.dtau_min, a.planck_a, a.planck_b};
     BinState<NB> st;
 #pragma unroll
     for (int i = 0; i < NB; i++) {
         const int q = li + LPG * i;
-        st.aq[i] = q < Q ? (float)(a.roots[q] * (double)bo) : 0.0f;
+        st.set_aq(i, q < Q ? (float)(a.roots[q] * (double)bo) : 0.0f);
         ps.acc[0][i][lane] = ps.acc[1][i][lane] = ps.acc[2][i][lane] = ps.acc[3][i][lane] = 0.0f;
     }
     // range of a_q over the whole warp (all lanes, all bins)
@@ -697,7 +783,7 @@ __device__ __forceinline__ void solve_item(const MixArgs &a, int64_t o, int l0, 
 #pragma unroll
     for (int i = 0; i < NB; i++) {
         const int q = li + LPG * i;
-        if (q < Q) { aq_lo = fminf(aq_lo, st.aq[i]); aq_hi = fmaxf(aq_hi, st.aq[i]); }
+        if (q < Q) { aq_lo = fminf(aq_lo, st.aq(i)); aq_hi = fmaxf(aq_hi, st.aq(i)); }
     }
     for (int d = 16; d; d >>= 1) {
         aq_lo = fminf(aq_lo, __shfl_xor_sync(0xffffffffu, aq_lo, d));
@@ -711,7 +797,7 @@ __device__ __forceinline__ void solve_item(const MixArgs &a, int64_t o, int l0, 
         float pif[NB], psf[NB], dtf[NB];
 #pragma unroll 1
         for (int h = 0; h < 2; h++) {   // backward half, then forward half (one code copy)
-            sweep_half<G, NB, SKIP>(a, k, o, l0, grp, h ? rf : rb, h ? rn : rf, nu_g, go, dlo, rg, rl, w, bf, pre,
+            sweep_half<G, NB, SKIP>(a, k, o, l0, grp, h ? rf : rb, h ? rn : rf, nu_g, Ao, Do, rg, rl, w, bf, pre,
                                     st, pif, psf, dtf, aq_lo, aq_hi);
             if (h == 0) {
 #pragma unroll
@@ -726,10 +812,10 @@ __device__ __forceinline__ void solve_item(const MixArgs &a, int64_t o, int l0, 
         for (int i = 0; i < NB; i++) {
             const float pib = ps.pi[i][lane], psb = ps.ps[i][lane], dtb = ps.dt[i][lane];
             // the origin's line opacity, floored opacity and floored source in this bin
-            const float xo = st.aq[i] * go.z;
-            const float chilo = dlo.x * ex2f(-xo * xo);
+            const float xo = st.aq(i) * gzo;
+            const float chilo = Xo * ex2f(-xo * xo);
             const float chio = fmaxf(chilo, k.chi_min);
-            const float Sov = fminf(dlo.y, chilo * dlo.y * k.inv_chi_min);
+            const float Sov = So * fminf(chilo * k.inv_chi_min, 1.0f);
             float u, lam, uml, oml;
             if (dtb == 0.0f && dtf[i] == 0.0f) {   // isolated origin: both halves empty
                 u = psb * (float)(1.0 / 1.4142135623730951); lam = 0.0f; uml = u; oml = 1.0f;
@@ -747,7 +833,7 @@ __device__ __forceinline__ void solve_item(const MixArgs &a, int64_t o, int l0, 
             const float ichi = 1.0f / chio;
             ps.acc[0][i][lane] += u;
             ps.acc[1][i][lane] += lam * chilo * ichi;
-            ps.acc[2][i][lane] += uml + lam * (Sov * chio - chilo * dlo.y) * ichi;
+            ps.acc[2][i][lane] += uml + lam * (Sov * chio - chilo * So) * ichi;
             ps.acc[3][i][lane] += oml + lam * (chio - chilo) * ichi;
         }
     }
@@ -777,8 +863,8 @@ __device__ __forceinline__ void solve_item(const MixArgs &a, int64_t o, int l0, 
 
 template <int G, int NB, int MINB, bool SKIP>
 __global__ void __launch_bounds__(32 * kWarps2, MINB) k_feautrier_warp(MixArgs a) {
-    __shared__ RingGeom rgs[kWarps2][kRing];
-    __shared__ float2 rls[kWarps2][G * kRing];
+    __shared__ RingPt rgs[kWarps2][kRing];
+    __shared__ float4 rls[kWarps2][G * kRing];
     __shared__ ElemWin<G> ews[kWarps2];
     __shared__ PairSmem<NB> pss[kWarps2];
     const int warp = threadIdx.x >> 5;
@@ -802,8 +888,8 @@ template <int G, int NB, int MINB, bool SKIP>
 __global__ void __launch_bounds__(32 * kWarps2, MINB)
 k_feautrier_batch(const MixArgs *__restrict__ models, const BatchItem *__restrict__ items, int64_t n_items,
                   unsigned long long *counter, const int32_t *__restrict__ active) {
-    __shared__ RingGeom rgs[kWarps2][kRing];
-    __shared__ float2 rls[kWarps2][G * kRing];
+    __shared__ RingPt rgs[kWarps2][kRing];
+    __shared__ float4 rls[kWarps2][G * kRing];
     __shared__ ElemWin<G> ews[kWarps2];
     __shared__ PairSmem<NB> pss[kWarps2];
     __shared__ MixArgs sa[kWarps2];
