@@ -425,12 +425,13 @@ def run_batch(args):
 
 def run_disc(args):
     """Keplerian disc (200k points, 192 rays, 20-level rotor, 19 lines x 63 bins), mixed
-    precision: one ALI iteration per step."""
+    precision: one ALI iteration per step. With --tau-fp64 T the cells whose diagonal ALO
+    weight reaches 1 - 1/T are solved again in FP64 every step."""
     import torch
     import paper_1912_08445_gb300 as mg
     import synthetic as syn
     m = syn.model_disc(n=args.disc_points, seed=0)
-    ctx = mg.Context(precision=mg.MG_MIXED, profile=1)
+    ctx = mg.Context(precision=mg.MG_MIXED, profile=1, tau_fp64=args.tau_fp64)
     ctx.load_model(m)
     t0 = time.perf_counter()
     st, _ = ctx.trace_rays()
@@ -450,6 +451,7 @@ def run_disc(args):
     print(json.dumps({"metric": METRIC, "unit": UNIT, "workload": "Keplerian disc, "
                       f"{m.n} points, 192 rays, 20 levels, 19 lines x 63 bins", "value": solves / dt,
                       "ms_per_step": dt * 1e3, "cell_freq_updates": updates, "variant": v,
+                      "tau_fp64": args.tau_fp64, "promoted_cells": ctx.promoted_cells() if args.tau_fp64 > 0 else 0,
                       "trace_s": trace_s, "ray_stats": st, "kernel_ms": {k: v2[0] / max(v2[1], 1) for k, v2 in kt.items()}}))
 
 
@@ -519,6 +521,8 @@ def main():
     ap.add_argument("--epochs", type=int, default=30)
     ap.add_argument("--batch-models", type=int, default=64)
     ap.add_argument("--disc-points", type=int, default=200_000)
+    ap.add_argument("--tau-fp64", type=float, default=0.0,
+                    help="disc workload: re-solve cells with L >= 1 - 1/T in FP64 (0: off)")
     ap.add_argument("--ali-precisions", default="mixed")
     ap.add_argument("--ali-max-iter", type=int, default=300)
     args = ap.parse_args()

@@ -264,6 +264,11 @@ int mg_batch_iterate(mg_batch *batch, mg_ali_report *reps);
  * in cost order and in natural order (CUDA events, best of reps after a warm-up) and keeps
  * the fastest. Leaves a valid radiation field in every model. */
 int mg_batch_autotune(mg_batch *batch, int32_t reps, int32_t *variant, int32_t *sorted, double *ms);
+/* Sets the launch variant of the persistent kernel (an index as for mg_set_variant) and the
+ * order of its work queue (sorted != 0: longest origins first; 0: natural order). A
+ * variant that is not valid for the batch's (n_lines, n_q) gives MG_ERR_ARG and leaves
+ * the previous choice; -1 restores the default. Invalidates the captured graph. */
+int mg_batch_set_variant(mg_batch *batch, int32_t variant, int32_t sorted);
 /* Sum of mg_work_counts over the batch's models. */
 int mg_batch_work_counts(const mg_batch *batch, int64_t *solves, int64_t *cell_freq_updates);
 

@@ -109,6 +109,7 @@ _SIGS = {
     "mg_batch_last_error": (C.c_char_p, [_P]),
     "mg_batch_formal_solve": (C.c_int, [_P]),
     "mg_batch_iterate": (C.c_int, [_P, _P]),
+    "mg_batch_set_variant": (C.c_int, [_P, C.c_int32, C.c_int32]),
     "mg_batch_autotune": (C.c_int, [_P, C.c_int32, _P, _P, _P]),
     "mg_batch_work_counts": (C.c_int, [_P, _P, _P]),
     "mg_set_variant": (C.c_int, [_P, C.c_int32]),
@@ -409,6 +410,10 @@ class Batch:
         if rc < 0 and not (allow_not_converged and rc == MG_ERR_NOT_CONVERGED):
             self._chk(rc, "mg_batch_iterate")
         return [{k: getattr(r, k) for k, _ in r._fields_ if k != "pad"} for r in reps], rc
+
+    def set_variant(self, variant, sorted_queue=True):
+        self._chk(self.lib.mg_batch_set_variant(self.h, int(variant), 1 if sorted_queue else 0),
+                  "mg_batch_set_variant")
 
     def autotune(self, reps=2):
         v = C.c_int32(0); s = C.c_int32(0); ms = C.c_double(0)

@@ -49,15 +49,19 @@ struct mg_batch {
     cudaStream_t stream = nullptr;
     int L = 0, Q = 0;
     int variant = -1, grid = 0, sorted = 1;
-    int64_t n_items_g[3] = {0, 0, 0};
+    // work-item lists per lines-per-warp value G (index G, 1 <= G <= kMaxG), natural and
+    // cost order
+    static constexpr int kMaxG = 4;
+    int64_t n_items_g[kMaxG + 1] = {};
     void *d_args = nullptr;
-    Item *d_items_g[3][2] = {{nullptr, nullptr}, {nullptr, nullptr}, {nullptr, nullptr}};
+    Item *d_items_g[kMaxG + 1][2] = {};
     unsigned long long *d_counter = nullptr;
     int32_t *d_active = nullptr;
     int32_t *h_active = nullptr;         // pinned
     unsigned long long **d_scal_ptrs = nullptr;
     unsigned long long *d_scal_all = nullptr, *h_scal_all = nullptr;   // pinned host copy
     cudaGraphExec_t exec = nullptr;
+    cudaEvent_t ev_order = nullptr;      // orders the batch stream after each model's stream
     std::string err;
     int num_sms = 152;
 };
@@ -73,8 +77,9 @@ static int bfail(mg_batch *b, int code, const std::string &m) {
         if (e_ != cudaSuccess) return bfail(b, MG_ERR_CUDA, std::string(#call ": ") + cudaGetErrorString(e_)); \
     } while (0)
 
-// Work items (model, origin * L + first line of the group) for lines-per-warp G = 1 and 2,
-// each in cost order (longest first) and in natural order.
+// Work items (model, origin * L + first line of the group) for every lines-per-warp value
+// G of the launch variants (1, 2 and 4), each in cost order (longest first) and in natural
+// order.
 static int build_items(mg_batch *b) {
     std::vector<int64_t> cost_all;
     std::vector<std::pair<int32_t, int64_t>> who;   // (model, origin)
@@ -95,7 +100,7 @@ static int build_items(mg_batch *b) {
     std::vector<size_t> order(who.size());
     std::iota(order.begin(), order.end(), 0);
     std::stable_sort(order.begin(), order.end(), [&](size_t x, size_t y) { return cost_all[x] > cost_all[y]; });
-    for (int G = 1; G <= 2; G++) {
+    for (int G = 1; G <= mg_batch::kMaxG; G *= 2) {
         std::vector<Item> nat, srt;
         for (size_t i = 0; i < who.size(); i++)
             for (int l0 = 0; l0 < b->L; l0 += G) nat.push_back(Item{who[i].first, (int32_t)(who[i].second * b->L + l0)});
@@ -119,19 +124,25 @@ static int launch_solve(mg_batch *b) {
     const int v = b->variant >= 0 ? b->variant : mg_variant_default(b->L, b->Q);
     const int grid = b->grid > 0 ? b->grid : b->num_sms * mg_variant_minb(v);
     const int G = mg_variant_g(v);
+    if (G < 1 || G > mg_batch::kMaxG || !b->d_items_g[G][0] || !b->d_items_g[G][1])
+        return bfail(b, MG_ERR_ARG, "batch: no work-item list for this launch variant");
     int rc = mg_batch_launch(v, grid, b->d_args, b->d_items_g[G][b->sorted ? 1 : 0], b->n_items_g[G],
                              b->d_counter, b->d_active, b->stream);
     if (rc) return bfail(b, rc, "batch: persistent formal-solve launch failed");
     return MG_OK;
 }
 
-// Points every model's context at the batch stream (and back).
+// Points every model's context at the batch stream (and back). The batch stream first
+// waits for the work already queued on each model's own stream (population uploads,
+// initialisations), which it would otherwise overtake.
 struct StreamSwap {
     mg_batch *b;
     std::vector<cudaStream_t> saved;
     std::vector<int32_t> prof;
     explicit StreamSwap(mg_batch *bb) : b(bb) {
         for (auto *c : b->models) {
+            if (c->stream != b->stream && cudaEventRecord(b->ev_order, c->stream) == cudaSuccess)
+                cudaStreamWaitEvent(b->stream, b->ev_order, 0);
             saved.push_back(c->stream);
             prof.push_back(c->opt.profile);
             c->stream = b->stream;
@@ -169,6 +180,11 @@ extern "C" int mg_batch_create(mg_batch **out, int32_t n_models, mg_ctx *const *
     cudaSetDevice(b->device);
     cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, b->device);
     if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) { delete b; return MG_ERR_CUDA; }
+    if (cudaEventCreateWithFlags(&b->ev_order, cudaEventDisableTiming) != cudaSuccess) {
+        cudaStreamDestroy(b->stream);
+        delete b;
+        return MG_ERR_CUDA;
+    }
     const size_t asz = mg_mixargs_size();
     std::vector<unsigned char> args(asz * n_models);
     for (int m = 0; m < n_models; m++) {
@@ -191,6 +207,8 @@ extern "C" int mg_batch_create(mg_batch **out, int32_t n_models, mg_ctx *const *
     cudaMemcpyAsync(b->d_args, args.data(), asz * n_models, cudaMemcpyHostToDevice, b->stream);
     cudaMemcpyAsync(b->d_scal_ptrs, sp.data(), sizeof(void *) * n_models, cudaMemcpyHostToDevice, b->stream);
     cudaMemcpyAsync(b->d_active, b->h_active, sizeof(int32_t) * n_models, cudaMemcpyHostToDevice, b->stream);
+    for (auto *c : b->models)   // the ray stores may still be in flight on the models' streams
+        if (cudaEventRecord(b->ev_order, c->stream) == cudaSuccess) cudaStreamWaitEvent(b->stream, b->ev_order, 0);
     int rc = build_items(b);
     if (rc) { mg_batch_destroy(b); return rc; }
     *out = b;
@@ -202,12 +220,13 @@ extern "C" int mg_batch_destroy(mg_batch *b) {
     cudaSetDevice(b->device);
     if (b->stream) cudaStreamSynchronize(b->stream);
     if (b->exec) cudaGraphExecDestroy(b->exec);
-    for (int G = 1; G <= 2; G++)
+    for (int G = 1; G <= mg_batch::kMaxG; G++)
         for (int k = 0; k < 2; k++) cudaFree(b->d_items_g[G][k]);
     cudaFree(b->d_args); cudaFree(b->d_counter);
     cudaFree(b->d_active); cudaFree(b->d_scal_ptrs); cudaFree(b->d_scal_all);
     if (b->h_active) cudaFreeHost(b->h_active);
     if (b->h_scal_all) cudaFreeHost(b->h_scal_all);
+    if (b->ev_order) cudaEventDestroy(b->ev_order);
     if (b->stream) cudaStreamDestroy(b->stream);
     delete b;
     return MG_OK;
@@ -317,6 +336,17 @@ extern "C" int mg_batch_iterate(mg_batch *b, mg_ali_report *reps) {
 
 // Times every valid launch variant of the persistent kernel, with the queue sorted by
 // cost and unsorted, and keeps the fastest (one warm-up, best of reps).
+extern "C" int mg_batch_set_variant(mg_batch *b, int32_t variant, int32_t sorted) {
+    if (!b) return MG_ERR_ARG;
+    if (variant != -1 && !mg_variant_valid(variant, b->L, b->Q))
+        return bfail(b, MG_ERR_ARG, "mg_batch_set_variant: variant not valid for this batch's lines and bins");
+    b->variant = variant;
+    b->sorted = sorted ? 1 : 0;
+    b->grid = 0;
+    if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
+    return MG_OK;
+}
+
 extern "C" int mg_batch_autotune(mg_batch *b, int32_t reps, int32_t *variant, int32_t *sorted, double *ms) {
     if (!b) return MG_ERR_ARG;
     cudaSetDevice(b->device);

@@ -72,3 +72,43 @@ def test_batch_ali_matches_single_model_ali():
         assert r2["converged"] and r2["iterations"] == rep["iterations"]
         assert np.max(rel_err(c.get_populations(), pops)) < 1e-12
     b.close()
+
+
+def test_every_batch_variant_does_the_work():
+    """Every launch variant valid for 4 lines x 31 bins, in both queue orders, gives the
+    persistent batch kernel the same radiation field as the per-model launch of that
+    variant (the batch holds a work-item list for every lines-per-warp value)."""
+    import paper_1912_08445_gb300 as mg
+    ms = _models(k=3, seed=5)
+    ctxs = []
+    for m in ms:
+        c = gpu_context(m, precision=1)
+        c.trace_rays()
+        c.init_populations()
+        ctxs.append(c)
+    b = mg.Batch(ctxs)
+    for v in [0, 1, 2, 3, 4, 11, 12, 13, 14, 15, 16, 17, 24, 25]:
+        refs = []
+        for c in ctxs:
+            c.set_variant(v)
+            c.formal_solve()
+            refs.append(c.get_radiation())
+        for srt in (True, False):
+            # leave another field (every molecule in the ground level) in the buffers, so
+            # that a launch doing nothing is caught, then restore the populations
+            for c in ctxs:
+                p1 = c.get_populations()
+                p2 = np.zeros_like(p1)
+                p2[:, 0] = p1.sum(axis=1)
+                c.set_populations(p2)
+                c.formal_solve()
+                c.set_populations(p1)
+            b.set_variant(v, srt)
+            b.formal_solve()
+            for c, (J, L, E) in zip(ctxs, refs):
+                J2, L2, E2 = c.get_radiation()
+                assert np.max(rel_err(J2, J)) < 1e-12, (v, srt)
+                assert np.max(rel_err(E2, E)) < 1e-12, (v, srt)
+    with pytest.raises(mg.MagritteError):
+        b.set_variant(5)      # two bins per lane for 32 lanes: not valid for 31 bins
+    b.close()
