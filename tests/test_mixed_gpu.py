@@ -46,20 +46,37 @@ def test_formal_solve_mixed_parity(name):
     assert np.max(np.abs(L[sel] - Lo)) < TOL_MIX * max(1e-6, float(np.max(np.abs(Lo))))
 
 
-def test_formal_solve_mixed_clumpy_50k_sampled():
-    """The bench workload (50k points, 48 rays, 4 lines x 31 bins) in the bench's launch
-    configuration: sampled origins against the oracle."""
-    m = syn.model_clumpy_3d(n=50_000, seed=0)
+def _full_size_variants(m, variants, n_origins, seed):
+    """Every launch variant the autotuner may pick for a full-size workload, each against
+    the oracle on sampled origins; then the autotuned choice itself."""
     o = Oracle(m, nthreads=16)
     ctx = gpu_context(m, precision=1)
     ctx.trace_rays()
     ctx.init_populations()
-    ctx.formal_solve()
-    J, L, E = ctx.get_radiation()
-    origins = np.sort(np.random.default_rng(5).choice(m.n, 24, replace=False))
+    origins = np.sort(np.random.default_rng(seed).choice(m.n, n_origins, replace=False))
     Jo, Lo, Eo = o.formal_solve(o.lte(), origins)
-    assert np.max(rel_err(J[origins], Jo)) < TOL_MIX
-    assert np.max(rel_err(E[origins], Eo)) < TOL_MIX
+    for v in variants:
+        ctx.set_variant(v)
+        ctx.formal_solve()
+        J, L, E = ctx.get_radiation()
+        assert np.max(rel_err(J[origins], Jo)) < TOL_MIX, v
+        assert np.max(rel_err(E[origins], Eo)) < TOL_MIX, v
+        assert np.max(np.abs(L[origins] - Lo)) < TOL_MIX * float(np.max(np.abs(Lo))), v
+    best, _, tried = ctx.autotune(reps=1)
+    assert best in variants and tried == len(variants)
+
+
+def test_formal_solve_mixed_clumpy_50k_sampled():
+    """The bench workload (50k points, 48 rays, 4 lines x 31 bins) in every launch
+    configuration the bench may time: sampled origins against the oracle."""
+    _full_size_variants(syn.model_clumpy_3d(n=50_000, seed=0),
+                        [0, 1, 2, 3, 4, 11, 12, 13, 14, 15, 16, 17, 24, 25], 24, 5)
+
+
+def test_formal_solve_mixed_disc_200k_sampled():
+    """The disc workload at full size (200k points, 192 rays, 20-level rotor, 19 lines x
+    63 bins), every valid launch variant: sampled origins against the oracle."""
+    _full_size_variants(syn.model_disc(n=200_000, seed=0), [5, 6, 9, 10, 18, 19, 22, 23], 8, 7)
 
 
 @pytest.mark.parametrize("name", ["sphere1d", "sphere1d_thick"])
