@@ -59,6 +59,7 @@ extern "C" {
 /* initial populations */
 #define MG_INIT_LTE    0
 #define MG_INIT_GIVEN  1   /* keep what mg_set_populations stored */
+#define MG_INIT_MLP    2   /* the network attached with mg_attach_mlp (see below) */
 
 typedef struct mg_ctx mg_ctx;
 
@@ -318,6 +319,20 @@ int mg_features(mg_ctx *ctx, float *out);
 /* Initial populations from the network (n_out must equal n_lev); cells whose output is
  * not finite keep LTE populations (their count: mg_status_counts' fallback_cells). */
 int mg_init_populations_mlp(mg_ctx *ctx, mg_mlp *mlp);
+/* Attaches a network to the context (NULL detaches) for mg_init_populations(ctx,
+ * MG_INIT_MLP), which then does what mg_init_populations_mlp does. The context keeps the
+ * pointer and does not own the network: the caller keeps it alive while attached.
+ * MG_ERR_ARG if its outputs differ from the species' level count (when the species is set);
+ * mg_init_populations(MG_INIT_MLP) without an attached network gives MG_ERR_STATE. */
+int mg_attach_mlp(mg_ctx *ctx, mg_mlp *mlp);
+/* Writes the network (output count, parameters and input normalisation; not the Adam
+ * moments) to a file: the 8 bytes "MGMLP001", int32 n_out, int32 0, int64 n_params,
+ * float mean[4], float std[4], float theta[n_params], little-endian. MG_ERR_ARG for a
+ * file that cannot be written. */
+int mg_mlp_save(const mg_mlp *mlp, const char *path);
+/* Creates a network on `device` from a file written by mg_mlp_save. MG_ERR_ARG for a
+ * missing, short or foreign file; *out is then NULL. */
+int mg_mlp_load(mg_mlp **out, const char *path, int32_t device);
 
 /* Kernel timing (opt.profile = 1): total milliseconds and launch counts per kernel
  * since the last reset, for up to cap kernels; names[i] points to static strings. */

@@ -19,7 +19,7 @@ MG_ERR_NOT_CONVERGED, MG_ERR_NUMERIC, MG_ERR_CAPACITY = -5, -6, -7
 MG_WARN_DEAD_END_RAYS, MG_WARN_NEG_POP_FALLBACK, MG_WARN_NEG_OPACITY = 1, 2, 3
 MG_FP64, MG_MIXED = 0, 1
 MG_GEOM_3D, MG_GEOM_SPHERICAL_1D = 0, 1
-MG_INIT_LTE, MG_INIT_GIVEN = 0, 1
+MG_INIT_LTE, MG_INIT_GIVEN, MG_INIT_MLP = 0, 1, 2
 
 
 class mg_options(C.Structure):
@@ -103,6 +103,9 @@ _SIGS = {
     "mg_mlp_loss_grad": (C.c_int, [_P, C.c_int64, _P, _P, _P, _P]),
     "mg_mlp_train": (C.c_int, [_P, C.c_int64, _P, _P, _P, _P]),
     "mg_features": (C.c_int, [_P, _P]),
+    "mg_attach_mlp": (C.c_int, [_P, _P]),
+    "mg_mlp_save": (C.c_int, [_P, C.c_char_p]),
+    "mg_mlp_load": (C.c_int, [_P, C.c_char_p, C.c_int32]),
     "mg_init_populations_mlp": (C.c_int, [_P, _P]),
     "mg_batch_create": (C.c_int, [_P, C.c_int32, _P]),
     "mg_batch_destroy": (C.c_int, [_P]),
@@ -341,6 +344,12 @@ class Context:
     def init_populations_mlp(self, mlp):
         self._chk(self.lib.mg_init_populations_mlp(self.h, mlp.h), "mg_init_populations_mlp")
 
+    def attach_mlp(self, mlp):
+        """Attaches a network for init_populations(MG_INIT_MLP) (None detaches); the
+        context keeps a reference so that the network outlives the attachment."""
+        self._chk(self.lib.mg_attach_mlp(self.h, mlp.h if mlp is not None else None), "mg_attach_mlp")
+        self._mlp = mlp
+
     def autotune(self, reps=2):
         v = C.c_int32(0); ms = C.c_double(0); nt = C.c_int32(0)
         self._chk(self.lib.mg_autotune(self.h, int(reps), C.byref(v), C.byref(ms), C.byref(nt)), "mg_autotune")
@@ -467,6 +476,25 @@ class MLP:
         t = _c(theta, np.float32)
         self._chk(self.lib.mg_mlp_set_params(self.h, _ptr(t), t.size), "mg_mlp_set_params")
 
+    def save(self, path):
+        self._chk(self.lib.mg_mlp_save(self.h, str(path).encode()), "mg_mlp_save")
+
+    @classmethod
+    def load(cls, path, device=0):
+        """A network read from a file written by save()."""
+        self = cls.__new__(cls)
+        self.lib = load()
+        h = C.c_void_p()
+        rc = self.lib.mg_mlp_load(C.byref(h), str(path).encode(), int(device))
+        if rc != MG_OK:
+            raise MagritteError(rc, f"mg_mlp_load: cannot read a network from {path}")
+        self.h = h
+        c = C.c_int64(0)
+        self.lib.mg_mlp_param_count(self.h, C.byref(c))
+        self.n_params = c.value
+        self.n_out = (self.n_params - (4 * 128 + 128 + 2 * (128 * 128 + 128))) // 129
+        return self
+
     def set_normalisation(self, mean, std):
         m, s = _c(mean, np.float32), _c(std, np.float32)
         self.mean, self.std = m, s
@@ -493,13 +521,3 @@ class MLP:
         self._chk(self.lib.mg_mlp_train(self.h, X.shape[0], _ptr(X), _ptr(Y), C.byref(o), C.byref(r)), "mg_mlp_train")
         return {k: getattr(r, k) for k, _ in r._fields_}
 
-    def save(self, path):
-        np.savez(path, theta=self.get_params(), mean=self.mean, std=self.std, n_out=self.n_out)
-
-    @classmethod
-    def load(cls, path, device=0):
-        d = np.load(path)
-        m = cls(int(d["n_out"]), device=device)
-        m.set_params(d["theta"])
-        m.set_normalisation(d["mean"], d["std"])
-        return m

@@ -136,6 +136,7 @@ struct mg_ctx {
     int32_t *d_err = nullptr;               // kernel error word
 
     // ---- FP64 promotion of optically thick cells (mixed precision)
+    mg_mlp *mlp = nullptr;        // attached network for MG_INIT_MLP (not owned)
     int32_t *d_promo = nullptr;   // [n] origin list, then [n] count in d_promo[n]
 
     // ---- launch variant of the mixed formal solve (-1: default for the model)

@@ -594,6 +594,10 @@ extern "C" int mg_init_populations(mg_ctx *ctx, int32_t mode) {
         if (!ctx->have_pops) return mg_fail(ctx, MG_ERR_STATE, "mg_init_populations: no populations given");
         return MG_OK;
     }
+    if (mode == MG_INIT_MLP) {
+        if (!ctx->mlp) return mg_fail(ctx, MG_ERR_STATE, "mg_init_populations: no network attached");
+        return mg_init_populations_mlp(ctx, ctx->mlp);
+    }
     if (mode != MG_INIT_LTE) return mg_fail(ctx, MG_ERR_ARG, "mg_init_populations: unknown mode");
     if ((rc = ensure_state(ctx))) return rc;
     if ((rc = mg_launch_lte(ctx))) return rc;

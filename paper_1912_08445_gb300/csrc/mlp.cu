@@ -16,6 +16,8 @@
 #include <cstring>
 #include <algorithm>
 #include <random>
+#include <cstdio>
+#include <cstring>
 #include "common.cuh"
 
 using namespace mg;
@@ -763,4 +765,62 @@ extern "C" int mg_init_populations_mlp(mg_ctx *ctx, mg_mlp *p) {
     ctx->have_pops = true;
     ctx->have_rad = false;
     return rc;
+}
+
+extern "C" int mg_attach_mlp(mg_ctx *ctx, mg_mlp *p) {
+    if (!ctx) return MG_ERR_ARG;
+    if (p && ctx->have_species && p->L.n_out != ctx->n_lev)
+        return mg_fail(ctx, MG_ERR_ARG, "mg_attach_mlp: network outputs != levels");
+    ctx->mlp = p;
+    return MG_OK;
+}
+
+// ------------------------------------------------------------------ file format
+static const char kMagic[8] = {'M', 'G', 'M', 'L', 'P', '0', '0', '1'};
+
+extern "C" int mg_mlp_save(const mg_mlp *cp, const char *path) {
+    mg_mlp *p = const_cast<mg_mlp *>(cp);
+    if (!p || !path) return MG_ERR_ARG;
+    std::vector<float> th(p->L.total);
+    int rc = mg_mlp_get_params(p, th.data(), p->L.total);
+    if (rc) return rc;
+    FILE *f = std::fopen(path, "wb");
+    if (!f) return mfail(p, MG_ERR_ARG, std::string("mg_mlp_save: cannot open ") + path);
+    const int32_t hdr[2] = {p->L.n_out, 0};
+    const int64_t np = p->L.total;
+    float mean[kIn], sd[kIn];
+    for (int i = 0; i < kIn; i++) { mean[i] = p->mean[i]; sd[i] = 1.f / p->istd[i]; }
+    bool ok = std::fwrite(kMagic, 1, 8, f) == 8 && std::fwrite(hdr, 4, 2, f) == 2 && std::fwrite(&np, 8, 1, f) == 1 &&
+              std::fwrite(mean, 4, kIn, f) == (size_t)kIn && std::fwrite(sd, 4, kIn, f) == (size_t)kIn &&
+              std::fwrite(th.data(), 4, th.size(), f) == th.size();
+    ok = (std::fclose(f) == 0) && ok;
+    return ok ? MG_OK : mfail(p, MG_ERR_ARG, std::string("mg_mlp_save: short write to ") + path);
+}
+
+extern "C" int mg_mlp_load(mg_mlp **out, const char *path, int32_t device) {
+    if (!out || !path) return MG_ERR_ARG;
+    *out = nullptr;
+    FILE *f = std::fopen(path, "rb");
+    if (!f) return MG_ERR_ARG;
+    char magic[8];
+    int32_t hdr[2];
+    int64_t np = 0;
+    float mean[kIn], sd[kIn];
+    bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, kMagic, 8) == 0 &&
+              std::fread(hdr, 4, 2, f) == 2 && std::fread(&np, 8, 1, f) == 1 &&
+              std::fread(mean, 4, kIn, f) == (size_t)kIn && std::fread(sd, 4, kIn, f) == (size_t)kIn &&
+              hdr[0] >= 2 && hdr[0] <= kMaxOut && np == make_layout(hdr[0]).total;
+    std::vector<float> th(ok ? (size_t)np : 0);
+    ok = ok && std::fread(th.data(), 4, th.size(), f) == th.size();
+    std::fclose(f);
+    if (!ok) return MG_ERR_ARG;
+    mg_mlp *p = nullptr;
+    int rc = mg_mlp_create(&p, hdr[0], 0, device);
+    if (rc) return rc;
+    if ((rc = mg_mlp_set_params(p, th.data(), np)) || (rc = mg_mlp_set_normalisation(p, mean, sd))) {
+        mg_mlp_destroy(p);
+        return rc;
+    }
+    *out = p;
+    return MG_OK;
 }

@@ -101,3 +101,37 @@ def test_training_reduces_loss():
     th = net.get_params()
     lp = bf16_forward(th, X[:2000], n_out, np.zeros(4), np.ones(4))
     assert omlp.loss(lp, Y[:2000].astype(np.float64)) < rep["first_loss"] / 10
+
+
+def test_save_load_attach(tmp_path):
+    """A network written to a file and read back has the same parameters,
+    normalisation and outputs; attached to a context it gives mg_init_populations
+    (MG_INIT_MLP) the populations of mg_init_populations_mlp."""
+    import paper_1912_08445_gb300 as mg
+    m = syn.model_clumpy_3d(n=1500, seed=22)
+    ctx = gpu_context(m)
+    net = mg.MLP(ctx.n_lev, seed=5)
+    net.set_normalisation([1.0, 2.0, -3.0, 0.5], [2.0, 0.5, 1.5, 3.0])
+    path = tmp_path / "net.bin"
+    net.save(path)
+    back = mg.MLP.load(path)
+    assert back.n_out == net.n_out and back.n_params == net.n_params
+    assert np.array_equal(back.get_params(), net.get_params())
+    X = np.random.default_rng(1).normal(size=(300, 4)).astype(np.float32)
+    assert np.array_equal(back.forward(X), net.forward(X))
+    # attached network: the init mode and the direct call agree bit for bit
+    ctx.init_populations_mlp(back)
+    direct = ctx.get_populations()
+    ctx.init_populations()
+    with pytest.raises(mg.MagritteError):
+        ctx.init_populations(mg.MG_INIT_MLP)          # nothing attached yet
+    ctx.attach_mlp(back)
+    ctx.init_populations(mg.MG_INIT_MLP)
+    assert np.array_equal(ctx.get_populations(), direct)
+    # a file that is not a network is refused
+    bad = tmp_path / "bad.bin"
+    bad.write_bytes(b"not a network file")
+    with pytest.raises(mg.MagritteError):
+        mg.MLP.load(bad)
+    with pytest.raises(mg.MagritteError):
+        ctx.attach_mlp(mg.MLP(ctx.n_lev + 1))      # outputs != levels
