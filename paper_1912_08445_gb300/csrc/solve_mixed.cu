@@ -18,6 +18,7 @@
 // the rescaled Rybicki-Hummer recursion described with the FP64 kernel.
 #include <cmath>
 #include <cstring>
+#include <type_traits>
 #include "common.cuh"
 
 using namespace mg;
@@ -71,6 +72,7 @@ struct MixArgs {
     const int32_t *ovl_off;
     const Overlap *ovl;
     float chi_min, dtau_min, inv_chi_min;
+    float q_nofloor;             // q = ds/(2 sqrt 2) from which 2 chi_min q >= dtau_min in FP32
     float planck_a, planck_b;    // B'(nu) = a nu_G^3 / expm1(b nu_G): a = 2h 1e27/c^2/I0, b = h 1e9/(k T_cmb)
     double *J, *Lout, *Jeff, *Lc, *Jnu;
     int32_t kmax;
@@ -517,8 +519,9 @@ __device__ __forceinline__ void first_point(const SweepK &k, BinState<NB> &st, c
 }
 
 // Update with the interval (previous point, this point); qp = (q, q) of that interval,
-// A and D the point's ring entries.
-template <int NB>
+// A and D the point's ring entries. FLOOR = false drops the dtau floor where the caller
+// knows that it cannot bind (q >= q_nofloor): the result is the same bit for bit.
+template <int NB, bool FLOOR = true>
 __device__ __forceinline__ void step_point(const SweepK &k, BinState<NB> &st, const float4 A, const float4 D,
                                            const float2 qp) {
     const float2 gz = make_float2(A.x, A.y), ngy = make_float2(A.z, A.w);
@@ -532,7 +535,7 @@ __device__ __forceinline__ void step_point(const SweepK &k, BinState<NB> &st, co
         const float2 t = __fmul2_rn(chil, icm);
         const float2 Sx = __fmul2_rn(S, make_float2(fminf(t.x, 1.0f), fminf(t.y, 1.0f)));
         const float2 d0 = __fmul2_rn(__fadd2_rn(st.chi_p2[p], chi), qp);
-        const float2 dl = make_float2(fmaxf(d0.x, k.dtau_min), fmaxf(d0.y, k.dtau_min));
+        const float2 dl = FLOOR ? make_float2(fmaxf(d0.x, k.dtau_min), fmaxf(d0.y, k.dtau_min)) : d0;
         const float2 sm = __fadd2_rn(st.d_p2[p], dl);
         st.Phi2[p] = __ffma2_rn(st.Phi2[p], st.iota2[p], sm);
         const float2 den = __ffma2_rn(dl, st.Phi2[p], make_float2(1.0f, 1.0f));
@@ -547,7 +550,8 @@ __device__ __forceinline__ void step_point(const SweepK &k, BinState<NB> &st, co
         const float chil = X.x * ex2f(-x * x);
         const float chi = fmaxf(chil, k.chi_min);
         const float Sx = S.x * fminf(chil * k.inv_chi_min, 1.0f);
-        const float dl = fmaxf((st.chi_p1 + chi) * qp.x, k.dtau_min);
+        const float d0 = (st.chi_p1 + chi) * qp.x;
+        const float dl = FLOOR ? fmaxf(d0, k.dtau_min) : d0;
         const float sm = st.d_p1 + dl;
         st.Phi1 = fmaf(st.Phi1, st.iota1, sm);
         st.iota1 = rcpf(fmaf(dl, st.Phi1, 1.0f));
@@ -630,7 +634,7 @@ __device__ __forceinline__ void sweep_half(const MixArgs &a, const SweepK &k, in
         const unsigned starts = __reduce_or_sync(0xffffffffu, bit);
         const int own = __popc(starts & (0xffffffffu >> (31 - lane))) - 1;
         const int cnt = min(kRing, xnext + 1);
-        bool my_far = false;
+        bool my_far = false, my_tiny = false;
         int top_next = 0;
         if (lane < cnt) {
             RingPt pt;
@@ -638,6 +642,7 @@ __device__ __forceinline__ void sweep_half(const MixArgs &a, const SweepK &k, in
             stage_ring_point<G>(a, w, bf, own, l0, x, pt, rl + lane, aq_lo, aq_hi);
             rg[lane] = pt;
             my_far = pt.b.z != 0.0f;
+            my_tiny = pt.b.x < a.q_nofloor;
             // element of point x - 1: this point's own, or the next one if x opens it
             top_next = top - own - (w.x1[bf][own + 1] == x ? 1 : 0);
         }
@@ -670,7 +675,17 @@ __device__ __forceinline__ void sweep_half(const MixArgs &a, const SweepK &k, in
         }
         // The chunk is swept in two segments, points [0, 16) and [16, cnt), with the
         // gathers of the next window issued between them (one copy of each loop body).
+        // A chunk whose intervals all have q >= q_nofloor sweeps without the dtau floor.
         const int mid = cnt < 16 ? cnt : 16;
+        const bool floor_needed = __any_sync(0xffffffffu, my_tiny) || qp.x < a.q_nofloor;
+        auto dense = [&](auto floor_tag, int jend) {
+#pragma unroll 4
+            for (; j < jend; j++) {
+                step_point<NB, decltype(floor_tag)::value>(k, st, rg[j].a, my[j], qp);
+                const float4 B = rg[j].b;
+                qp = make_float2(B.x, B.y);
+            }
+        };
         if (SKIP) {
             // A point whose own and two previous points are all far changes the state by
             // O(chi_min ds) only (no-ops in FP32): rows that involve a non-floored interval
@@ -681,17 +696,12 @@ __device__ __forceinline__ void sweep_half(const MixArgs &a, const SweepK &k, in
             const unsigned all = cnt == 32 ? 0xffffffffu : ((1u << cnt) - 1u);
             unsigned proc = ~(farmask & f1 & f2) & all;
             if (j) proc &= ~1u;   // point 0 of the first chunk is the far end, done above
-            const bool dense = (proc | (j ? 1u : 0u)) == all;
+            const bool dense_chunk = (proc | (j ? 1u : 0u)) == all;
 #pragma unroll 1
             for (int seg = 0; seg < 2; seg++) {
-                if (dense) {   // nothing to skip in this chunk: the unrolled sweep
-                    const int jend = seg ? cnt : mid;
-#pragma unroll 4
-                    for (; j < jend; j++) {
-                        step_point<NB>(k, st, rg[j].a, my[j], qp);
-                        const float4 B = rg[j].b;
-                        qp = make_float2(B.x, B.y);
-                    }
+                if (dense_chunk) {   // nothing to skip in this chunk: the unrolled sweep
+                    if (floor_needed) dense(std::true_type{}, seg ? cnt : mid);
+                    else dense(std::false_type{}, seg ? cnt : mid);
                 } else {
                     unsigned bits = proc & (seg ? 0xffff0000u : 0x0000ffffu);
                     while (bits) {
@@ -721,13 +731,8 @@ __device__ __forceinline__ void sweep_half(const MixArgs &a, const SweepK &k, in
         } else {
 #pragma unroll 1
             for (int seg = 0; seg < 2; seg++) {
-                const int jend = seg ? cnt : mid;
-#pragma unroll 4
-                for (; j < jend; j++) {
-                    step_point<NB>(k, st, rg[j].a, my[j], qp);
-                    const float4 B = rg[j].b;
-                    qp = make_float2(B.x, B.y);
-                }
+                if (floor_needed) dense(std::true_type{}, seg ? cnt : mid);
+                else dense(std::false_type{}, seg ? cnt : mid);
                 if (seg == 0) gathers();
             }
         }
@@ -963,6 +968,9 @@ static void fill_args(mg_ctx *ctx, MixArgs &a) {
     a.roots = ctx->d_roots; a.weights = ctx->d_weights; a.ovl_off = ctx->d_ovl_off; a.ovl = ctx->d_ovl;
     a.chi_min = (float)ctx->opt.chi_min; a.dtau_min = (float)ctx->opt.dtau_min;
     a.inv_chi_min = (float)(1.0 / ctx->opt.chi_min);
+    // Every floored opacity is >= chi_min, so an interval with q >= q_nofloor has
+    // dtau/sqrt 2 = (chi_prev + chi) q >= dtau_min: the floor cannot bind there.
+    a.q_nofloor = std::nextafter((float)(ctx->opt.dtau_min / (2.0 * ctx->opt.chi_min)) * 1.000001f, INFINITY);
     a.planck_a = (float)(2.0 * kH * 1e27 / (kC * kC) / (double)kI0);
     a.planck_b = (float)(kH * 1e9 / (kKB * ctx->opt.T_cmb));
     a.J = ctx->d_J; a.Lout = ctx->d_L; a.Jeff = ctx->d_Jeff; a.Lc = ctx->d_Lc;
