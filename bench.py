@@ -346,7 +346,11 @@ def run_ali(args):
             ctx = mg.Context(precision=prec, tol=1e-6, max_iter=args.ali_max_iter, ng_period=ng)
             ctx.set_stream(stream.cuda_stream)
             ctx.load_model(model)
+            torch.cuda.synchronize()
+            t_tr = time.perf_counter()
             ctx.trace_rays()
+            torch.cuda.synchronize()
+            trace_s = time.perf_counter() - t_tr
             ctx.init_populations()
             if prec == mg.MG_MIXED:
                 ctx.autotune(reps=1)
@@ -359,7 +363,7 @@ def run_ali(args):
             out["runs"].append({"precision": prec_name, "ng_period": ng, "seconds": dt,
                                 "iterations": rep["iterations"], "ng_steps": rep["ng_steps"],
                                 "converged": bool(rep["converged"]), "last_change": rep["last_change"],
-                                "fallback_cells": rep["n_fallback"]})
+                                "fallback_cells": rep["n_fallback"], "trace_seconds_untimed": trace_s})
             ctx.close()
     print(json.dumps(out))
 
@@ -427,6 +431,7 @@ def run_disc(args):
     """Keplerian disc (200k points, 192 rays, 20-level rotor, 19 lines x 63 bins), mixed
     precision: one ALI iteration per step. With --tau-fp64 T the cells whose diagonal ALO
     weight reaches 1 - 1/T are solved again in FP64 every step."""
+    import numpy as np
     import torch
     import paper_1912_08445_gb300 as mg
     import synthetic as syn
@@ -452,6 +457,7 @@ def run_disc(args):
                       f"{m.n} points, 192 rays, 20 levels, 19 lines x 63 bins", "value": solves / dt,
                       "ms_per_step": dt * 1e3, "cell_freq_updates": updates, "variant": v,
                       "tau_fp64": args.tau_fp64, "promoted_cells": ctx.promoted_cells() if args.tau_fp64 > 0 else 0,
+                      "max_L": float(np.max(ctx.get_radiation()[1])),
                       "trace_s": trace_s, "ray_stats": st, "kernel_ms": {k: v2[0] / max(v2[1], 1) for k, v2 in kt.items()}}))
 
 

@@ -1,21 +1,24 @@
 // K3 in mixed precision: the Feautrier formal solve of Sec. 3.3-3.4 in FP32 (the
-// statistical equilibrium that follows stays in FP64).
+// statistical equilibrium that follows stays in FP64). Intensities are carried in units
+// of I0 = 1e-20 W m^-2 Hz^-1 sr^-1 and the float line data are scaled (chi x 1e5,
+// eta x 1e25) so that no FP32 quantity underflows. The line opacity of bin a_q at a point
+// is chi_l = X 2^(-x'^2), with X = chi_int c / (nu_l b sqrt(pi)) and the profile
+// argument x' in units of sqrt(log2 e) Doppler widths; for a line that overlaps no other
+// line the source function S = eta_int/chi_int is frequency independent.
 //
-// Layout: one CTA per origin point, one warp per line (lanes = Gauss-Hermite bins; a
-// warp loops when there are more lines than warps or more bins than lanes). For each ray
-// pair the CTA stages the expanded pair in shared memory:
-//   pt[k]   = (ds_k / 2, v_k, sqrt(log2 e)/b_k, 0)          (float4)
-//   ln[k][l] = (X_l = chi_int c / (nu_l b sqrt(pi)), S_l = eta_int/chi_int / I0)  (float2)
-// so that chi = X exp(-x^2) and, for a line that overlaps no other line, the source
-// function S is frequency independent. Intensities are carried in units of
-// I0 = 1e-20 W m^-2 Hz^-1 sr^-1 and the float line data are scaled (chi x 1e5,
-// eta x 1e25) so that no FP32 quantity underflows.
+// Two kernels:
+// - k_feautrier_warp (the common case: lines that do not overlap) gives each warp one
+//   origin and a group of G lines, with the bins of those lines across its lanes (NB
+//   per lane), and sweeps every ray pair through a per-warp ring of staged points; the
+//   persistent k_feautrier_batch runs the same work item over a queue of models.
+// - k_feautrier_mixed (lines that overlap, so that a bin sums several lines) gives each
+//   origin a CTA and stages every ray pair whole in shared memory.
 //
-// Per point and bin the sweep costs one ex2 and one rcp (MUFU) and ~12 FMA-pipe ops:
-//   x' = (a_q - v (1 + a_q/c)) ib,  e = 2^(-x'^2),  chi = max(X e, chi_min),
+// Per point and bin the sweep costs one ex2 and one rcp (MUFU) and a handful of FMA-
+// and ALU-pipe ops, in the rescaled Rybicki-Hummer recursion described with the FP64
+// kernel:
 //   dtau = max((chi_prev + chi) ds/2, dtau_min),  t = (dtau_prev + dtau)/2,
-//   Phi = t + Phi iota,  iota = 1/(1 + dtau Phi),  psi = (t S + psi) iota,
-// the rescaled Rybicki-Hummer recursion described with the FP64 kernel.
+//   Phi = t + Phi iota,  iota = 1/(1 + dtau Phi),  psi = (t S + psi) iota.
 #include <cmath>
 #include <cstring>
 #include <type_traits>
@@ -84,7 +87,10 @@ __device__ __forceinline__ float planck_f(const MixArgs &a, float nu_g) {
     return a.planck_a * nu_g * nu_g * nu_g / expm1f(a.planck_b * nu_g);
 }
 
-// Stages half-ray (o, r) in FP32: point x of the half sits at pair index base + dir x.
+// CTA kernel (overlapping lines). Stages half-ray (o, r) in FP32, point x of the half at
+// pair index base + dir x:
+//   pt[k]    = (ds_k / 2, v_k, sqrt(log2 e)/b_k, 0)
+//   ln[k][l] = (X_l, S_l) of every line l.
 __device__ void stage_half32(const MixArgs &a, int64_t o, int r, int base, int dir, float4 *pt, float2 *ln) {
     const int L = a.L;
     const int64_t off = a.ray_off[o * a.R + r];
