@@ -453,11 +453,13 @@ def run_disc(args):
     torch.cuda.synchronize()
     dt = (time.perf_counter() - t0) / args.steps
     kt = ctx.kernel_times()
+    ctx.formal_solve()   # (untimed) the radiation field of the final populations, for max L
+    max_L = float(np.max(ctx.get_radiation()[1]))
     print(json.dumps({"metric": METRIC, "unit": UNIT, "workload": "Keplerian disc, "
                       f"{m.n} points, 192 rays, 20 levels, 19 lines x 63 bins", "value": solves / dt,
                       "ms_per_step": dt * 1e3, "cell_freq_updates": updates, "variant": v,
                       "tau_fp64": args.tau_fp64, "promoted_cells": ctx.promoted_cells() if args.tau_fp64 > 0 else 0,
-                      "max_L": float(np.max(ctx.get_radiation()[1])),
+                      "max_L": max_L,
                       "trace_s": trace_s, "ray_stats": st, "kernel_ms": {k: v2[0] / max(v2[1], 1) for k, v2 in kt.items()}}))
 
 

@@ -13,6 +13,7 @@ struct TraceArgs {
     int32_t R;
     int32_t geometry;
     const double *pos, *vel, *b, *dirs;
+    const float4 *posf;                // (x, y, z, |x| + |y| + |z|) in FP32, for the filter
     const int64_t *nbr_off;
     const int32_t *nbr_idx;
     const uint8_t *bdy;
@@ -65,12 +66,65 @@ __device__ __forceinline__ bool emit(const TraceArgs &a, int64_t base, int32_t &
 // 3D point cloud: from the current cell, the neighbour with a strictly larger projection
 // on the ray that lies closest to the ray (ties: smaller squared distance, smaller
 // projection, smaller index); stop after a boundary cell or at a dead end.
+//
+// The decisions are those of the FP64 expressions below, bit for bit, but most of them
+// are taken in FP32 (64x the FP64 rate on this GPU) with a rigorous error bound, and FP64
+// is evaluated only where the bound cannot decide:
+// - a candidate is valid when s > s_cur: the FP32 projection decides unless it lies
+//   within its error bound of s_cur, where the FP64 projection decides;
+// - the FP32 squared distance of every valid candidate comes with an interval
+//   [lo, hi] that contains the FP64 value; the FP64 winner's lo is at most the smallest
+//   hi, so every valid candidate with lo <= min hi is evaluated in FP64 and the winner
+//   is chosen among those with the exact tie-breaks. (A non-finite bound leaves the
+//   candidate to FP64.)
+// The bounds follow from |fl32(a) - a| <= u|a| (u = 2^-24) for the conversions of the
+// positions and the direction and for each FP32 operation; they are doubled for margin.
+struct Cand32 {
+    bool valid;
+    float lo, hi;   // interval of the FP64 squared distance
+};
+
+__device__ __forceinline__ double proj64(const TraceArgs &a, int64_t c, double xo0, double xo1, double xo2,
+                                         double n0, double n1, double n2) {
+    const double dx = a.pos[3 * c] - xo0;
+    const double dy = a.pos[3 * c + 1] - xo1;
+    const double dz = a.pos[3 * c + 2] - xo2;
+    return dx * n0 + dy * n1 + dz * n2;
+}
+
+__device__ __forceinline__ Cand32 classify32(const TraceArgs &a, int64_t c, const float4 po, float n0f, float n1f,
+                                             float n2f, float scf, double s_cur, double xo0, double xo1,
+                                             double xo2, double n0, double n1, double n2) {
+    constexpr float k2u = 1.2e-7f;   // 2u with margin
+    const float4 pc = a.posf[c];
+    const float dx = pc.x - po.x, dy = pc.y - po.y, dz = pc.z - po.z;
+    const float D = fabsf(dx) + fabsf(dy) + fabsf(dz);
+    const float P = pc.w + po.w;
+    const float sf = dx * n0f + dy * n1f + dz * n2f;
+    const float Es = k2u * (P + 6.0f * D);   // |sf - s64|
+    const float diff = sf - scf;
+    const float margin = Es + k2u * (fabsf(scf) + fabsf(diff));
+    Cand32 r;
+    if (diff > margin) r.valid = true;
+    else if (diff < -margin) r.valid = false;
+    else r.valid = proj64(a, c, xo0, xo1, xo2, n0, n1, n2) > s_cur;   // inconclusive in FP32
+    const float px = dx - sf * n0f, py = dy - sf * n1f, pz = dz - sf * n2f;
+    const float d2 = px * px + py * py + pz * pz;
+    const float Ep = 2.0f * (Es + 0.6e-7f * (P + 4.0f * D + 3.0f * fabsf(sf)));   // |px - px64| and so on
+    const float Ed = 1.1f * (2.0f * Ep * (fabsf(px) + fabsf(py) + fabsf(pz)) + 9.0f * Ep * Ep + k2u * 2.0f * d2);
+    r.lo = d2 - Ed;
+    r.hi = d2 + Ed;
+    return r;
+}
+
 template <bool FILL>
 __device__ void walk_3d(const TraceArgs &a, int64_t o, int r, int64_t base, int32_t &len, int32_t &x,
                         bool &dead, bool &overflow) {
     const double n0 = a.dirs[3 * r], n1 = a.dirs[3 * r + 1], n2 = a.dirs[3 * r + 2];
     const double xo0 = a.pos[3 * o], xo1 = a.pos[3 * o + 1], xo2 = a.pos[3 * o + 2];
     const double vo0 = a.vel[3 * o], vo1 = a.vel[3 * o + 1], vo2 = a.vel[3 * o + 2];
+    const float n0f = (float)n0, n1f = (float)n1, n2f = (float)n2;
+    const float4 po = a.posf[o];
     int64_t cur = o;
     double s_cur = 0.0;
     double va = 0.0, ba = a.b[o];
@@ -79,16 +133,25 @@ __device__ void walk_3d(const TraceArgs &a, int64_t o, int r, int64_t base, int3
     dead = false;
     overflow = false;
     for (;;) {
+        const float scf = (float)s_cur;
+        const int64_t e0 = a.nbr_off[cur], e1 = a.nbr_off[cur + 1];
+        // pass 1: validity and the smallest upper bound of a valid candidate's distance
+        float minhi = INFINITY;
+        for (int64_t e = e0; e < e1; e++) {
+            const Cand32 k = classify32(a, a.nbr_idx[e], po, n0f, n1f, n2f, scf, s_cur, xo0, xo1, xo2, n0, n1, n2);
+            if (k.valid) minhi = fminf(minhi, k.hi);
+        }
+        // pass 2: FP64 for every valid candidate that may be the closest
         int64_t best = -1;
         double bs = 0.0, bd2 = 0.0;
-        const int64_t e1 = a.nbr_off[cur + 1];
-        for (int64_t e = a.nbr_off[cur]; e < e1; e++) {
+        for (int64_t e = e0; e < e1; e++) {
             const int64_t c = a.nbr_idx[e];
+            const Cand32 k = classify32(a, c, po, n0f, n1f, n2f, scf, s_cur, xo0, xo1, xo2, n0, n1, n2);
+            if (!k.valid || k.lo > minhi) continue;
             const double dx = a.pos[3 * c] - xo0;
             const double dy = a.pos[3 * c + 1] - xo1;
             const double dz = a.pos[3 * c + 2] - xo2;
             const double s = dx * n0 + dy * n1 + dz * n2;
-            if (!(s > s_cur)) continue;
             const double px = dx - s * n0, py = dy - s * n1, pz = dz - s * n2;
             const double d2 = px * px + py * py + pz * pz;
             const bool better = (best < 0) || (d2 < bd2) || (d2 == bd2 && s < bs) || (d2 == bd2 && s == bs && c < best);
@@ -328,6 +391,13 @@ int mg_scan_counts(mg_ctx *ctx, const int32_t *d_cnt, int64_t m, int64_t *d_out)
     return MG_OK;
 }
 
+__global__ void k_posf(int64_t n, const double *__restrict__ pos, float4 *__restrict__ posf) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float x = (float)pos[3 * i], y = (float)pos[3 * i + 1], z = (float)pos[3 * i + 2];
+    posf[i] = make_float4(x, y, z, fabsf(x) + fabsf(y) + fabsf(z));
+}
+
 int mg_launch_trace(mg_ctx *ctx) {
     const int64_t nr = ctx->n * ctx->R;
     int rc;
@@ -341,6 +411,12 @@ int mg_launch_trace(mg_ctx *ctx) {
     a.nbr_off = ctx->d_nbr_off; a.nbr_idx = ctx->d_nbr_idx; a.bdy = ctx->d_bdy;
     a.dshift_frac = ctx->opt.dshift_frac; a.max_steps = ctx->opt.max_steps;
     a.len = d_len; a.xlen = d_xlen; a.err = ctx->d_err;
+    float4 *d_posf = nullptr;
+    if (ctx->geometry == MG_GEOM_3D) {
+        if ((rc = mg_alloc(ctx, &d_posf, ctx->n))) return rc;
+        k_posf<<<(unsigned)((ctx->n + 255) / 256), 256, 0, ctx->stream>>>(ctx->n, ctx->d_pos, d_posf);
+    }
+    a.posf = d_posf;
     // record up to cap_tmp cells per half-ray in the count pass (at most 32 GiB of scratch)
     int32_t *d_tmp = nullptr;
     int32_t cap_tmp = 128;
@@ -364,7 +440,7 @@ int mg_launch_trace(mg_ctx *ctx) {
     MG_CUDA(cudaMemcpy(&total, ctx->d_ray_off + nr, 8, cudaMemcpyDeviceToHost));
     MG_CUDA(cudaMemcpy(&kerr, ctx->d_err, 4, cudaMemcpyDeviceToHost));
     if (kerr) {
-        cudaFree(d_len); cudaFree(d_xlen); cudaFree(d_tmp);
+        cudaFree(d_len); cudaFree(d_xlen); cudaFree(d_tmp); cudaFree(d_posf);
         return mg_fail(ctx, MG_ERR_CAPACITY, "ray tracing: a half-ray exceeded max_steps");
     }
     if ((rc = mg_alloc(ctx, &ctx->d_cells, total)) || (rc = mg_alloc(ctx, &ctx->d_xcum, total)) ||
@@ -392,6 +468,7 @@ int mg_launch_trace(mg_ctx *ctx) {
     cudaFree(d_len);
     cudaFree(d_xlen);
     cudaFree(d_tmp);
+    cudaFree(d_posf);
     ctx->n_elements = (int64_t)st[0];
     ctx->n_expanded = (int64_t)st[1];
     ctx->max_pair_len = (int64_t)st[2];
