@@ -41,13 +41,26 @@ def test_quadrature_matches_oracle(Q):
 
 
 # ------------------------------------------------------------------ ray tracing
-@pytest.mark.parametrize("name", ["tiny", "lattice", "sphere1d", "clumpy3000", "hubble_fast"])
+def _moved(m, scale=1.0, shift=0.0):
+    """The same cloud with its positions scaled and shifted (the walk's FP32 filter meets
+    overflowing squares, or bounds too wide to decide, and must defer to FP64)."""
+    import dataclasses
+    return dataclasses.replace(m, pos=m.pos * scale + shift)
+
+
+@pytest.mark.parametrize("name", ["tiny", "lattice", "sphere1d", "clumpy3000", "hubble_fast",
+                                  "clumpy_huge_scale", "clumpy_far_offset"])
 def test_trace_bit_exact(name):
     m = {"tiny": lambda: syn.model_tiny_3d(seed=4, n=20),
          "lattice": lambda: syn.model_lattice_3d(m=6),
          "sphere1d": lambda: syn.model_sphere_1d(n=200, seed=1),
          "clumpy3000": lambda: small_clumpy(),
-         "hubble_fast": lambda: syn.hubble_line_1d(n_cells=60, c_dbeta=0.5)}[name]()
+         "hubble_fast": lambda: syn.hubble_line_1d(n_cells=60, c_dbeta=0.5),
+         # squares of 1e35 m overflow FP32: every comparison goes to FP64
+         "clumpy_huge_scale": lambda: _moved(small_clumpy(n=1500, seed=8), scale=1e22),
+         # a cloud 1e6 radii from the origin of coordinates: FP32 positions resolve only
+         # ~1/6 of a cell spacing, so many decisions are left to FP64
+         "clumpy_far_offset": lambda: _moved(small_clumpy(n=1500, seed=9), shift=1e21)}[name]()
     o = Oracle(m, nthreads=8)
     ctx = gpu_context(m, oracle_dirs=o.dirs)
     st, rc = ctx.trace_rays()
