@@ -59,7 +59,7 @@ __device__ __forceinline__ double planck_d(double nu, double T) {
 // memory during the sweep). Point x of the half (0 = nearest the origin) sits at pair
 // index base + dir x; its path length goes to ds slot (dir < 0 ? idx : idx - 1).
 struct PairSmem64 {
-    double *ds, *v, *b, *w;
+    double *ds, *v, *ib, *w;   // ib: 1/b, the reciprocal width (one division per point, not per bin)
     int32_t *ca, *cb;
 };
 
@@ -79,7 +79,7 @@ __device__ void stage_half64(const SolveArgs &a, int64_t o, int r, int base, int
             const int idx = base + dir * (x0 + j - 1);
             S.ds[dir < 0 ? idx : idx - 1] = dse / (double)(ns + 1);
             S.v[idx] = (1.0 - w) * pv + w * ve;
-            S.b[idx] = (1.0 - w) * bp + w * bc;
+            S.ib[idx] = 1.0 / ((1.0 - w) * bp + w * bc);
             S.w[idx] = w;
             S.ca[idx] = prev;
             S.cb[idx] = c;
@@ -92,17 +92,18 @@ struct Pt64 {
     double chi, eta, chil, etal;
 };
 
-__device__ __forceinline__ Pt64 point64(const SolveArgs &a, int l, double aq, int k, const PairSmem64 &S) {
-    const double v = S.v[k], bk = S.b[k], w = S.w[k];
+// k1 = 1 + a_q/c: the comoving shift a_q (1 - v/c) - v is a_q - v k1 (no division).
+__device__ __forceinline__ Pt64 point64(const SolveArgs &a, int l, double aq, double k1, int k, const PairSmem64 &S) {
+    constexpr double kCsp = kC / kSqrtPi;
+    const double v = S.v[k], ibk = S.ib[k], w = S.w[k];
     const double *pa = a.line + (int64_t)S.ca[k] * 2 * a.L, *pb = a.line + (int64_t)S.cb[k] * 2 * a.L;
-    const double ibk = 1.0 / bk;
     Pt64 p{0.0, 0.0, 0.0, 0.0};
     const int o0 = a.ovl_off[l], o1 = a.ovl_off[l + 1];
-    const double base = aq * (1.0 - v / kC) - v;
+    const double base = aq - v * k1;
     for (int i = o0; i < o1; i++) {
         const Overlap ov = a.ovl[i];
         const double x = (ov.dnl + ov.rat * base) * ibk;
-        const double phi = exp(-x * x) * kC * ov.inv_nu2 * ibk / kSqrtPi;
+        const double phi = exp(-x * x) * (ov.inv_nu2 * ibk) * kCsp;
         const double et = ((1.0 - w) * pa[2 * ov.l2] + w * pb[2 * ov.l2]) * phi;
         const double ch = ((1.0 - w) * pa[2 * ov.l2 + 1] + w * pb[2 * ov.l2 + 1]) * phi;
         p.eta += et;
@@ -129,17 +130,17 @@ struct Side64 {
     double phi_iota, psi, dtau;
 };
 
-__device__ __forceinline__ Side64 sweep64(const SolveArgs &a, int l, double aq, double nu_o, int kstart, int kend,
-                                          int step, const PairSmem64 &S, Pt64 &po) {
+__device__ __forceinline__ Side64 sweep64(const SolveArgs &a, int l, double aq, double k1, double nu_o, int kstart,
+                                          int kend, int step, const PairSmem64 &S, Pt64 &po) {
     // kstart: far end, kend: origin; step = +1 (backward half) or -1 (forward half)
-    Pt64 p = point64(a, l, aq, kstart, S);
+    Pt64 p = point64(a, l, aq, k1, kstart, S);
     double chi_prev = fmax(p.chi, a.chi_min);
     double S_prev = p.eta / chi_prev;
     const double I = planck_d(nu_o * (1.0 - S.v[kstart] / kC), a.T_cmb);
     double Phi = 0.0, iota = 0.0, psi = 0.0, dt_prev = 0.0;
     int row = 0;
     for (int k = kstart + step;; k += step) {
-        Pt64 q = point64(a, l, aq, k, S);
+        Pt64 q = point64(a, l, aq, k1, k, S);
         const double chi = fmax(q.chi, a.chi_min);
         const double Sk = q.eta / chi;
         const double dsk = S.ds[step > 0 ? k - 1 : k];
@@ -174,8 +175,8 @@ __global__ void k_feautrier64(SolveArgs a) {
     PairSmem64 S;
     S.ds = smem;
     S.v = S.ds + kmax;
-    S.b = S.v + kmax;
-    S.w = S.b + kmax;
+    S.ib = S.v + kmax;
+    S.w = S.ib + kmax;
     double *acc = S.w + kmax;   // [F][4]
     S.ca = reinterpret_cast<int32_t *>(acc + 4 * F);
     S.cb = S.ca + kmax;
@@ -203,7 +204,7 @@ __global__ void k_feautrier64(SolveArgs a) {
         stage_half64(a, o, rf, Kb + 1, +1, S);
         if (threadIdx.x == 0) {
             S.v[Kb] = 0.0;
-            S.b[Kb] = bo;
+            S.ib[Kb] = 1.0 / bo;
             S.w[Kb] = 0.0;
             S.ca[Kb] = (int32_t)o;
             S.cb[Kb] = (int32_t)o;
@@ -212,18 +213,19 @@ __global__ void k_feautrier64(SolveArgs a) {
         for (int f = threadIdx.x; f < F; f += blockDim.x) {
             const int l = f / Q, q = f - l * Q;
             const double aq = a.roots[q] * bo;
-            const double nu_o = a.lc[l].nu * (1.0 + aq / kC);
+            const double k1 = 1.0 + aq / kC;
+            const double nu_o = a.lc[l].nu * k1;
             Side64 sb, sf;
             Pt64 po{0, 0, 0, 0};
             double u, lam, uml, oml;
             if (K == 1) {
                 const double I = planck_d(nu_o, a.T_cmb);
                 u = I; lam = 0.0; uml = I; oml = 1.0;
-                po = point64(a, l, aq, Kb, S);
+                po = point64(a, l, aq, k1, Kb, S);
                 po.chi = fmax(po.chi, a.chi_min);
             } else {
-                if (Kb > 0) sb = sweep64(a, l, aq, nu_o, 0, Kb, +1, S, po);
-                if (Kf > 0) sf = sweep64(a, l, aq, nu_o, K - 1, Kb, -1, S, po);
+                if (Kb > 0) sb = sweep64(a, l, aq, k1, nu_o, 0, Kb, +1, S, po);
+                if (Kf > 0) sf = sweep64(a, l, aq, k1, nu_o, K - 1, Kb, -1, S, po);
                 if (Kb == 0 || Kf == 0) {
                     const double Io = planck_d(nu_o, a.T_cmb);
                     if (Kb == 0) sb = Side64{1.0, Io, 0.0};
