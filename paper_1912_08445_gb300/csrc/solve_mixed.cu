@@ -31,6 +31,7 @@ namespace {
 constexpr float kSqrtLog2e = 1.2011224087864498f;
 constexpr float kSqrt2 = 1.4142135623730951f;
 constexpr float kInvSqrt8 = 0.35355339059327373f;   // 1/(2 sqrt 2)
+constexpr float kLog2e = 1.4426950408889634f;
 
 __device__ __forceinline__ float ex2f(float x) {
     float y;
@@ -57,8 +58,11 @@ __global__ void k_line_data_f32(int64_t n, int L, int nlev, const double *__rest
     line[2 * t] = eta;
     line[2 * t + 1] = chi;
     if (chi < 0.0) atomicAdd(neg, 1ull);
-    linef[2 * t] = (float)(eta * kEtaScale);
-    linef[2 * t + 1] = (float)(chi * kChiScale);
+    // (eta, chi) times the profile normalisation c / (nu_l sqrt(pi)): the line opacity of a
+    // bin is then chi' 2^(-x'^2) / b, and S = eta'/chi' keeps the scale kEtaScale/kChiScale
+    const double kl = kC / (k.nu * kSqrtPi);
+    linef[2 * t] = (float)(eta * (kEtaScale / kChiScale) * kl);
+    linef[2 * t + 1] = (float)(chi * kl);
 }
 
 struct MixArgs {
@@ -68,8 +72,7 @@ struct MixArgs {
     const int64_t *ray_off;
     const int32_t *cells, *xcum;
     const float *ds, *vpar, *b;
-    const float *line;           // [n][L][2] scaled (eta, chi)
-    const float *kline;          // [L] c / (nu_l sqrt(pi)) / kChiScale
+    const float *line;           // [n][L][2] (eta, chi) times c/(nu_l sqrt(pi)), eta also times kEtaScale/kChiScale
     const float *nu_ghz;         // [L]
     const double *roots, *weights;
     const int32_t *ovl_off;
@@ -117,7 +120,7 @@ __device__ void stage_half32(const MixArgs &a, int64_t o, int r, int base, int d
                 const float2 p0 = lp[l], p1 = lq[l];
                 const float et = (1.0f - w) * p0.x + w * p1.x;
                 const float ch = (1.0f - w) * p0.y + w * p1.y;
-                const float X = ch * a.kline[l] * ib;
+                const float X = ch * ib;
                 const float S = ch > 0.0f ? et / ch : 0.0f;
                 ln[(size_t)idx * L + l] = make_float2(X, S);
             }
@@ -243,7 +246,7 @@ __global__ void __launch_bounds__(256) k_feautrier_mixed(MixArgs a) {
         if (threadIdx.x == 0) pt[Kb] = make_float4(0.f, 0.f, kSqrtLog2e / bo, 0.f);
         for (int l = threadIdx.x; l < L; l += blockDim.x) {
             const float2 d = lo[l];
-            const float X = d.y * a.kline[l] / bo;
+            const float X = d.y / bo;
             ln[(size_t)Kb * L + l] = make_float2(X, d.y > 0.f ? d.x / d.y : 0.f);
         }
         __syncthreads();
@@ -327,10 +330,12 @@ __global__ void __launch_bounds__(256) k_feautrier_mixed(MixArgs a) {
 // half-ray prefetches the first window of the next half-ray.
 constexpr int kRing = 32;
 constexpr int kWarps2 = 4;
-constexpr int kWin = 33;   // elements top, top-1, ..., top-32 of a half-ray
+constexpr int kWin = 32;   // elements top, top-1, ..., top-31 of a half-ray
 
-// Element window of one warp, double-buffered. Element e of the half-ray sits at slot
-// top - e; element -1 (reached when top < 32) is the origin itself: xcum 0, cell o, v 0.
+// Element window of one warp, double-buffered: one slot per lane. Element e of the
+// half-ray sits at slot top - e; element -1 (reached when top < 31) is the origin itself:
+// xcum 0, cell o, v 0. Slots 0 .. 30 own the points of a refill; slot 31 only serves as
+// the predecessor (towards the origin) of slot 30.
 template <int G>
 struct ElemWin {
     int32_t x1[2][kWin];      // xcum[e]: the element's expanded points are xcum[e-1] .. xcum[e]-1
@@ -352,28 +357,24 @@ __device__ __forceinline__ void cp_async8(void *dst, const void *src) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
-// Issues the copies of the records of elements top .. top-32 of the half-ray at `off`
-// into buffer bf (lane i: slot i; lane 0 also slot 32).
+// Issues the copies of the records of elements top .. top-31 of the half-ray at `off`
+// into buffer bf (lane i: slot i).
 template <int G>
 __device__ __forceinline__ void win_records(const MixArgs &a, int64_t off, int top, int32_t o, ElemWin<G> &w,
                                             int bf) {
-    const int lane = threadIdx.x & 31;
-#pragma unroll
-    for (int t = 0; t < 2; t++) {
-        if (t == 1 && lane != 0) break;
-        const int i = lane + 32 * t;
-        const int e = top - i;
-        if (e >= 0) {
-            cp_async4(&w.x1[bf][i], a.xcum + off + e);
-            cp_async4(&w.cell[bf][i], a.cells + off + e);
-            cp_async4(&w.v[bf][i], a.vpar + off + e);
-            cp_async4(&w.ds[bf][i], a.ds + off + e);
-        } else {
-            w.x1[bf][i] = 0;
-            w.cell[bf][i] = o;
-            w.v[bf][i] = 0.0f;
-            w.ds[bf][i] = 0.0f;
-        }
+    const int i = threadIdx.x & 31;
+    const int e = top - i;
+    if (e >= 0) {
+        const int64_t k = off + e;
+        cp_async4(&w.x1[bf][i], a.xcum + k);
+        cp_async4(&w.cell[bf][i], a.cells + k);
+        cp_async4(&w.v[bf][i], a.vpar + k);
+        cp_async4(&w.ds[bf][i], a.ds + k);
+    } else {
+        w.x1[bf][i] = 0;
+        w.cell[bf][i] = o;
+        w.v[bf][i] = 0.0f;
+        w.ds[bf][i] = 0.0f;
     }
     cp_async_commit();
 }
@@ -382,20 +383,12 @@ __device__ __forceinline__ void win_records(const MixArgs &a, int64_t off, int t
 // (each lane reads only the slots it copied itself).
 template <int G>
 __device__ __forceinline__ void win_gathers(const MixArgs &a, int l0, ElemWin<G> &w, int bf) {
-    const int lane = threadIdx.x & 31;
-    const float2 *line2 = reinterpret_cast<const float2 *>(a.line);
+    const int i = threadIdx.x & 31;
+    const int64_t c = w.cell[bf][i];
+    cp_async4(&w.b[bf][i], a.b + c);
+    const float2 *lc = reinterpret_cast<const float2 *>(a.line) + c * a.L;
 #pragma unroll
-    for (int t = 0; t < 2; t++) {
-        if (t == 1 && lane != 0) break;
-        const int i = lane + 32 * t;
-        const int64_t c = w.cell[bf][i];
-        cp_async4(&w.b[bf][i], a.b + c);
-#pragma unroll
-        for (int k = 0; k < G; k++) {
-            const int l = l0 + k < a.L ? l0 + k : a.L - 1;
-            cp_async8(&w.ln[bf][k][i], line2 + c * a.L + l);
-        }
-    }
+    for (int k = 0; k < G; k++) cp_async8(&w.ln[bf][k][i], lc + (l0 + k < a.L ? l0 + k : a.L - 1));
     cp_async_commit();
 }
 
@@ -404,8 +397,10 @@ struct SweepK {
     float chi_min, inv_chi_min, dtau_min, planck_a, planck_b;
 };
 
+// B_nu / I0 at nu_g GHz; e^x - 1 from one ex2 (x = h nu / k T_cmb is O(1) at line
+// frequencies, so the subtraction costs no precision there).
 __device__ __forceinline__ float planck_k(const SweepK &k, float nu_g) {
-    return k.planck_a * nu_g * nu_g * nu_g / expm1f(k.planck_b * nu_g);
+    return k.planck_a * nu_g * nu_g * nu_g * rcpf(ex2f(k.planck_b * kLog2e * nu_g) - 1.0f);
 }
 
 // One staged point of the ring. The per-point scalars are stored twice so that a bin
@@ -448,12 +443,11 @@ __device__ __forceinline__ void stage_ring_point(const MixArgs &a, const ElemWin
     bool far = true;
 #pragma unroll
     for (int k = 0; k < G; k++) {
-        const int l = l0 + k < a.L ? l0 + k : a.L - 1;
         const float2 p0 = w.ln[bf][k][i + 1];
         const float2 p1 = w.ln[bf][k][i];
         const float et = (1.0f - wt) * p0.x + wt * p1.x;
         const float ch = (1.0f - wt) * p0.y + wt * p1.y;
-        const float X = fmaxf(ch, 0.0f) * a.kline[l] * ib;
+        const float X = fmaxf(ch, 0.0f) * ib;
         // (a line whose opacity is below the smallest normal float has no source here)
         const float S = ch >= 1.17549435e-38f ? et * rcpf(ch) : 0.0f;
         ln[k * kRing] = make_float4(X, X, S, S);   // line k's slot of this point
@@ -636,10 +630,11 @@ __device__ __forceinline__ void sweep_half(const MixArgs &a, const SweepK &k, in
         // xnext - xcum + 1 (<= 0 for slot 0); the owner of position j is the last slot
         // starting at or before j.
         const int pos = xnext - w.x1[bf][lane] + 1;
-        const unsigned bit = (top - lane >= 0 && pos < 32) ? (1u << (pos > 0 ? pos : 0)) : 0u;
+        const unsigned bit = (lane < kWin - 1 && top - lane >= 0 && pos < 32) ? (1u << (pos > 0 ? pos : 0)) : 0u;
         const unsigned starts = __reduce_or_sync(0xffffffffu, bit);
         const int own = __popc(starts & (0xffffffffu >> (31 - lane))) - 1;
-        const int cnt = min(kRing, xnext + 1);
+        // points owned by slots 0 .. 30: those from xcum of slot 31 up to xnext
+        const int cnt = min(kRing, xnext - w.x1[bf][kWin - 1] + 1);
         bool my_far = false, my_tiny = false;
         int top_next = 0;
         if (lane < cnt) {
@@ -776,7 +771,7 @@ __device__ __forceinline__ void solve_item(const MixArgs &a, int64_t o, int l0, 
     const float2 dl = reinterpret_cast<const float2 *>(a.line)[o * a.L + lc];
     // ring entries of the origin (v = 0 there): a = (g_z, g_z, -0, -0), line = (X, X, S, S)
     const float gzo = kSqrtLog2e * ibo;
-    const float Xo = fmaxf(dl.y, 0.0f) * a.kline[lc] * ibo;
+    const float Xo = fmaxf(dl.y, 0.0f) * ibo;
     const float So = dl.y > 0.0f ? dl.x / dl.y : 0.0f;
     const float4 Ao = make_float4(gzo, gzo, -0.0f, -0.0f);
     const float4 Do = make_float4(Xo, Xo, So, So);
@@ -832,16 +827,16 @@ __device__ __forceinline__ void solve_item(const MixArgs &a, int64_t o, int l0, 
                 u = psb * (float)(1.0 / 1.4142135623730951); lam = 0.0f; uml = u; oml = 1.0f;
             } else {
                 // sigma (Phi iota) = Phi^ iota / (delta_- + delta_+), sigma psi = psi^ / (delta_- + delta_+)
-                const float sig = 1.0f / (dtb + dtf[i]);
+                const float sig = rcpf(dtb + dtf[i]);
                 const float pi2 = pib + pif[i];
-                const float iD = 1.0f / fmaf(sig, pi2, 1.0f);
+                const float iD = rcpf(fmaf(sig, pi2, 1.0f));
                 const float s2 = sig * (psb + psf[i]);
                 u = (Sov + s2) * iD;
                 lam = iD;
                 uml = s2 * iD;
                 oml = sig * pi2 * iD;
             }
-            const float ichi = 1.0f / chio;
+            const float ichi = rcpf(chio);
             ps.acc[0][i][lane] += u;
             ps.acc[1][i][lane] += lam * chilo * ichi;
             ps.acc[2][i][lane] += uml + lam * (Sov * chio - chilo * So) * ichi;
@@ -970,7 +965,7 @@ static void fill_args(mg_ctx *ctx, MixArgs &a) {
     a.n = ctx->n; a.R = ctx->R; a.P = ctx->P; a.L = L; a.Q = Q;
     a.pf = ctx->d_pf; a.pb = ctx->d_pb; a.ray_off = ctx->d_ray_off; a.cells = ctx->d_cells; a.xcum = ctx->d_xcum;
     a.ds = ctx->d_dsf; a.vpar = ctx->d_vparf; a.b = ctx->d_bf; a.line = ctx->d_linef;
-    a.kline = ctx->d_lconst; a.nu_ghz = ctx->d_lconst + L;
+    a.nu_ghz = ctx->d_lconst + L;
     a.roots = ctx->d_roots; a.weights = ctx->d_weights; a.ovl_off = ctx->d_ovl_off; a.ovl = ctx->d_ovl;
     a.chi_min = (float)ctx->opt.chi_min; a.dtau_min = (float)ctx->opt.dtau_min;
     a.inv_chi_min = (float)(1.0 / ctx->opt.chi_min);
