@@ -618,25 +618,29 @@ __device__ __forceinline__ void sweep_half(const MixArgs &a, const SweepK &k, in
     }
     pre = false;
     const float4 *my = rl + grp * kRing;
-    int top = len - 1;         // element in window slot 0; it holds point xnext
+    int top = len - 1;         // element in window slot 0
     int xnext = -1;            // next point to stage (descending towards the origin)
     float2 qp = make_float2(0.0f, 0.0f);   // (q, q) of the interval ending at the next point
     bool first = true, far1 = false, far2 = false;
+    bool fresh = true;         // first refill from this window: prefetch the next one
     do {
-        cp_async_wait_all();
+        if (fresh) cp_async_wait_all();
         __syncwarp();
         if (first) xnext = w.x1[bf][0] - 1;
-        // Owner slot of the point of each lane: slot i's element starts at chunk position
-        // xnext - xcum + 1 (<= 0 for slot 0); the owner of position j is the last slot
-        // starting at or before j.
+        // Owner slot of the point of each lane. Slot i's element ends (its highest point)
+        // at chunk position p_i = xnext - xcum + 1, increasing with i. The n0 slots with
+        // p_i <= 0 hold or lie above xnext (the last of them holds it); the owner of
+        // position j is slot n0 - 1 plus the number of slots with 1 <= p_i <= j. Slot 31
+        // only precedes slot 30 and owns no point.
         const int pos = xnext - w.x1[bf][lane] + 1;
-        const unsigned bit = (lane < kWin - 1 && top - lane >= 0 && pos < 32) ? (1u << (pos > 0 ? pos : 0)) : 0u;
-        const unsigned starts = __reduce_or_sync(0xffffffffu, bit);
-        const int own = __popc(starts & (0xffffffffu >> (31 - lane))) - 1;
+        const bool slot_ok = lane < kWin - 1 && top - lane >= 0;
+        const int n0 = __popc(__ballot_sync(0xffffffffu, slot_ok && pos <= 0));
+        const unsigned starts = __reduce_or_sync(0xffffffffu, (slot_ok && pos > 0 && pos < 32) ? (1u << pos) : 0u);
+        const int own = n0 - 1 + __popc(starts & (0xffffffffu >> (31 - lane)));
         // points owned by slots 0 .. 30: those from xcum of slot 31 up to xnext
-        const int cnt = min(kRing, xnext - w.x1[bf][kWin - 1] + 1);
+        const int xw = w.x1[bf][kWin - 1];
+        const int cnt = min(kRing, xnext - xw + 1);
         bool my_far = false, my_tiny = false;
-        int top_next = 0;
         if (lane < cnt) {
             RingPt pt;
             const int x = xnext - lane;
@@ -644,17 +648,17 @@ __device__ __forceinline__ void sweep_half(const MixArgs &a, const SweepK &k, in
             rg[lane] = pt;
             my_far = pt.b.z != 0.0f;
             my_tiny = pt.b.x < a.q_nofloor;
-            // element of point x - 1: this point's own, or the next one if x opens it
-            top_next = top - own - (w.x1[bf][own + 1] == x ? 1 : 0);
         }
         const unsigned farmask = SKIP ? __ballot_sync(0xffffffffu, my_far) : 0u;
-        top_next = __shfl_sync(0xffffffffu, top_next, cnt - 1);
         __syncwarp();
-        // the next window: the rest of this half-ray, else the start of the next one
-        const bool more = xnext - cnt >= 0;
-        const bool issue = more || lenn > 0;
-        if (more) win_records<G>(a, off, top_next, (int32_t)o, w, bf ^ 1);
-        else if (lenn > 0) win_records<G>(a, offn, lenn - 1, (int32_t)o, w, bf ^ 1);
+        // On the first refill from a window, the next window: the following 31 elements of
+        // this half-ray, else (this window reaches element 0) the start of the next one.
+        const bool last_window = top - (kWin - 1) < 0;
+        const bool issue = fresh && (!last_window || lenn > 0);
+        if (fresh && !last_window) win_records<G>(a, off, top - (kWin - 1), (int32_t)o, w, bf ^ 1);
+        else if (issue) win_records<G>(a, offn, lenn - 1, (int32_t)o, w, bf ^ 1);
+        if (fresh && last_window) pre = issue;
+        fresh = false;
         const int nb = bf ^ 1;
         auto gathers = [&]() {
             if (issue) {
@@ -737,11 +741,14 @@ __device__ __forceinline__ void sweep_half(const MixArgs &a, const SweepK &k, in
                 if (seg == 0) gathers();
             }
         }
-        bf = nb;
-        top = top_next;
         xnext -= cnt;
-        if (!more) pre = issue;
+        if (xnext >= 0 && xnext < xw) {   // window exhausted: move to the prefetched one
+            bf = nb;
+            top -= kWin - 1;
+            fresh = true;
+        }
     } while (xnext >= 0);
+    if (pre) bf ^= 1;   // the next half-ray's first window sits in the other buffer
     step_point<NB>(k, st, Ao, Do, qp);   // the origin
     bin_results<NB>(st, pi, ps, dt);
 }
