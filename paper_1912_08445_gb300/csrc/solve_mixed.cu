@@ -340,7 +340,8 @@ template <int G>
 struct ElemWin {
     int32_t x1[2][kWin];      // xcum[e]: the element's expanded points are xcum[e-1] .. xcum[e]-1
     int32_t cell[2][kWin];
-    float v[2][kWin], ds[2][kWin], b[2][kWin];
+    float ds[2][kWin];
+    float2 vb[2][kWin];        // (line-of-sight velocity, width b) of the element's cell
     float2 ln[2][G][kWin];    // scaled (eta, chi) of the warp's lines at the element's cell
 };
 
@@ -368,12 +369,12 @@ __device__ __forceinline__ void win_records(const MixArgs &a, int64_t off, int t
         const int64_t k = off + e;
         cp_async4(&w.x1[bf][i], a.xcum + k);
         cp_async4(&w.cell[bf][i], a.cells + k);
-        cp_async4(&w.v[bf][i], a.vpar + k);
+        cp_async4(&w.vb[bf][i].x, a.vpar + k);
         cp_async4(&w.ds[bf][i], a.ds + k);
     } else {
         w.x1[bf][i] = 0;
         w.cell[bf][i] = o;
-        w.v[bf][i] = 0.0f;
+        w.vb[bf][i].x = 0.0f;
         w.ds[bf][i] = 0.0f;
     }
     cp_async_commit();
@@ -385,7 +386,7 @@ template <int G>
 __device__ __forceinline__ void win_gathers(const MixArgs &a, int l0, ElemWin<G> &w, int bf) {
     const int i = threadIdx.x & 31;
     const int64_t c = w.cell[bf][i];
-    cp_async4(&w.b[bf][i], a.b + c);
+    cp_async4(&w.vb[bf][i].y, a.b + c);
     const float2 *lc = reinterpret_cast<const float2 *>(a.line) + c * a.L;
 #pragma unroll
     for (int k = 0; k < G; k++) cp_async8(&w.ln[bf][k][i], lc + (l0 + k < a.L ? l0 + k : a.L - 1));
@@ -431,30 +432,29 @@ __device__ __forceinline__ void stage_ring_point(const MixArgs &a, const ElemWin
     const float rn = rcpf((float)(ns + 1));
     // exactly 1 at the element's own cell, so that a thick neighbour cannot leak into it
     const float wt = x - x0 == ns ? 1.0f : (float)(x - x0 + 1) * rn;
-    const float v = (1.0f - wt) * w.v[bf][i + 1] + wt * w.v[bf][i];
+    // interpolations (1 - w) p0 + w p1 in packed pairs; w = 1 gives p1 exactly
+    const float2 w1 = make_float2(wt, wt), w0 = make_float2(1.0f - wt, 1.0f - wt);
+    const float2 vbi = __ffma2_rn(w1, w.vb[bf][i], __fmul2_rn(w0, w.vb[bf][i + 1]));
+    const float v = vbi.x;
     const float qds = kInvSqrt8 * w.ds[bf][i] * rn;
-    const float bb = (1.0f - wt) * w.b[bf][i + 1] + wt * w.b[bf][i];
-    const float ib = rcpf(bb);
+    const float ib = rcpf(vbi.y);
     const float pz = kSqrtLog2e * ib;
     const float gy = v * pz, gz = (1.0f - v * (float)(1.0 / kC)) * pz;
     const float xlo = aq_lo * gz - gy, xhi = aq_hi * gz - gy;
     const float xm = xlo > 0.0f ? xlo : (xhi < 0.0f ? -xhi : 0.0f);
     const float wing = ex2f(-xm * xm);
-    bool far = true;
+    float Xmax = 0.0f;
 #pragma unroll
     for (int k = 0; k < G; k++) {
-        const float2 p0 = w.ln[bf][k][i + 1];
-        const float2 p1 = w.ln[bf][k][i];
-        const float et = (1.0f - wt) * p0.x + wt * p1.x;
-        const float ch = (1.0f - wt) * p0.y + wt * p1.y;
-        const float X = fmaxf(ch, 0.0f) * ib;
+        const float2 e = __ffma2_rn(w1, w.ln[bf][k][i], __fmul2_rn(w0, w.ln[bf][k][i + 1]));   // (eta, chi)
+        const float X = fmaxf(e.y, 0.0f) * ib;
         // (a line whose opacity is below the smallest normal float has no source here)
-        const float S = ch >= 1.17549435e-38f ? et * rcpf(ch) : 0.0f;
+        const float S = e.y >= 1.17549435e-38f ? e.x * rcpf(e.y) : 0.0f;
         ln[k * kRing] = make_float4(X, X, S, S);   // line k's slot of this point
-        far = far && (X * wing < a.chi_min);
+        Xmax = fmaxf(Xmax, X);
     }
     pt.a = make_float4(gz, gz, -gy, -gy);
-    pt.b = make_float4(qds, qds, far ? 1.0f : 0.0f, 0.0f);
+    pt.b = make_float4(qds, qds, Xmax * wing < a.chi_min ? 1.0f : 0.0f, 0.0f);
 }
 
 // Per-bin sweep state in the variables delta = dtau/sqrt 2, Phi^ = sqrt 2 Phi and
