@@ -317,17 +317,18 @@ __global__ void __launch_bounds__(256) k_feautrier_mixed(MixArgs a) {
 // bins of its line, so each shared-memory read and loop step is shared by NB updates.
 // The warp loops over all ray pairs of its origin and stages the expanded points through
 // a private ring of kRing points (one point per lane per refill): no CTA barrier is ever
-// needed and the pair sums stay in registers in a fixed order. The boundary row is the
+// needed, and the pair sums are kept per lane in a fixed order. The boundary row is the
 // interior update started from the virtual state (Phi iota = 1, psi = I, dtau = 0).
-// The opacity floor costs three instructions: chi = max(chi_l, chi_min) and
-// S = min(S_l, chi_l S_l / chi_min), which is eta/chi with chi floored.
+// The opacity floor: chi = max(chi_l, chi_min) and S_eff = S min(chi_l/chi_min, 1),
+// which is eta/chi with chi floored.
 //
-// The ray elements behind each ring refill come from an element window in shared memory
-// that is filled asynchronously (cp.async) one refill ahead: while the warp sweeps the
-// points of one refill, the records (xcum, cell, v, ds) of the next window stream in, and
-// half-way through the sweep the gathers through the cell index (b and the line data)
-// are issued, so a refill normally finds its window complete. The last refill of a
-// half-ray prefetches the first window of the next half-ray.
+// The ray elements behind the ring come from an element window in shared memory (one
+// element per lane). A window serves refills until its points are used up; meanwhile
+// the next window is filled asynchronously (cp.async): its records (xcum, cell, v, ds)
+// are issued on the first refill from the current window, and the gathers through the
+// cell index (b and the line data) half-way through that refill's sweep, so a window is
+// normally complete when it is needed. The last window of a half-ray prefetches the
+// first window of the next half-ray.
 constexpr int kRing = 32;
 constexpr int kWarps2 = 4;
 constexpr int kWin = 32;   // elements top, top-1, ..., top-31 of a half-ray
