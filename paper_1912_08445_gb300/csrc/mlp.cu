@@ -745,7 +745,11 @@ extern "C" int mg_init_populations_mlp(mg_ctx *ctx, mg_mlp *p) {
     int rc;
     if ((rc = mg_init_populations(ctx, MG_INIT_LTE))) return rc;   // fallback for rows the network cannot give
     float *dF = nullptr, *dL = nullptr;
-    if ((rc = mg_alloc(ctx, &dF, 4 * ctx->n)) || (rc = mg_alloc(ctx, &dL, ctx->n * ctx->n_lev))) return rc;
+    if ((rc = mg_alloc(ctx, &dF, 4 * ctx->n))) return rc;
+    if ((rc = mg_alloc(ctx, &dL, ctx->n * ctx->n_lev))) {
+        cudaFree(dF);
+        return rc;
+    }
     k_features<<<(unsigned)((ctx->n + 127) / 128), 128, 0, ctx->stream>>>(
         ctx->n, ctx->d_pos, ctx->d_vel, ctx->d_nbr_off, ctx->d_nbr_idx, ctx->d_T, ctx->d_ncoll, ctx->d_nspec, ctx->d_b,
         ctx->n_lev, ctx->d_E, ctx->d_g, ctx->h_lines[0], dF);

@@ -398,11 +398,25 @@ __global__ void k_posf(int64_t n, const double *__restrict__ pos, float4 *__rest
     posf[i] = make_float4(x, y, z, fabsf(x) + fabsf(y) + fabsf(z));
 }
 
+// Temporaries of one trace, freed on every return (cudaFree waits for the kernels that
+// may still use them).
+struct TraceScratch {
+    int32_t *len = nullptr, *xlen = nullptr, *tmp = nullptr;
+    float4 *posf = nullptr;
+    ~TraceScratch() {
+        cudaFree(len);
+        cudaFree(xlen);
+        cudaFree(tmp);
+        cudaFree(posf);
+    }
+};
+
 int mg_launch_trace(mg_ctx *ctx) {
     const int64_t nr = ctx->n * ctx->R;
     int rc;
-    int32_t *d_len = nullptr, *d_xlen = nullptr;
-    if ((rc = mg_alloc(ctx, &d_len, nr)) || (rc = mg_alloc(ctx, &d_xlen, nr))) return rc;
+    TraceScratch sc;
+    if ((rc = mg_alloc(ctx, &sc.len, nr)) || (rc = mg_alloc(ctx, &sc.xlen, nr))) return rc;
+    int32_t *const d_len = sc.len, *const d_xlen = sc.xlen;
     if ((rc = mg_alloc(ctx, &ctx->d_ray_off, nr + 1))) return rc;
     MG_CUDA(cudaMemsetAsync(ctx->d_err, 0, sizeof(int32_t), ctx->stream));
     TraceArgs a{};
@@ -411,14 +425,13 @@ int mg_launch_trace(mg_ctx *ctx) {
     a.nbr_off = ctx->d_nbr_off; a.nbr_idx = ctx->d_nbr_idx; a.bdy = ctx->d_bdy;
     a.dshift_frac = ctx->opt.dshift_frac; a.max_steps = ctx->opt.max_steps;
     a.len = d_len; a.xlen = d_xlen; a.err = ctx->d_err;
-    float4 *d_posf = nullptr;
     if (ctx->geometry == MG_GEOM_3D) {
-        if ((rc = mg_alloc(ctx, &d_posf, ctx->n))) return rc;
-        k_posf<<<(unsigned)((ctx->n + 255) / 256), 256, 0, ctx->stream>>>(ctx->n, ctx->d_pos, d_posf);
+        if ((rc = mg_alloc(ctx, &sc.posf, ctx->n))) return rc;
+        k_posf<<<(unsigned)((ctx->n + 255) / 256), 256, 0, ctx->stream>>>(ctx->n, ctx->d_pos, sc.posf);
     }
-    a.posf = d_posf;
+    a.posf = sc.posf;
     // record up to cap_tmp cells per half-ray in the count pass (at most 32 GiB of scratch)
-    int32_t *d_tmp = nullptr;
+    int32_t *&d_tmp = sc.tmp;
     int32_t cap_tmp = 128;
     while (cap_tmp > 0 && (double)nr * cap_tmp * 4.0 > 32.0 * (1 << 30)) cap_tmp /= 2;
     if (ctx->geometry == MG_GEOM_3D && cap_tmp > 0 && cudaMalloc(&d_tmp, (size_t)nr * cap_tmp * 4) != cudaSuccess) {
@@ -440,7 +453,6 @@ int mg_launch_trace(mg_ctx *ctx) {
     MG_CUDA(cudaMemcpy(&total, ctx->d_ray_off + nr, 8, cudaMemcpyDeviceToHost));
     MG_CUDA(cudaMemcpy(&kerr, ctx->d_err, 4, cudaMemcpyDeviceToHost));
     if (kerr) {
-        cudaFree(d_len); cudaFree(d_xlen); cudaFree(d_tmp); cudaFree(d_posf);
         return mg_fail(ctx, MG_ERR_CAPACITY, "ray tracing: a half-ray exceeded max_steps");
     }
     if ((rc = mg_alloc(ctx, &ctx->d_cells, total)) || (rc = mg_alloc(ctx, &ctx->d_xcum, total)) ||
@@ -465,10 +477,6 @@ int mg_launch_trace(mg_ctx *ctx) {
     unsigned long long st[4];
     MG_CUDA(cudaMemcpyAsync(st, ctx->d_scal, sizeof(st), cudaMemcpyDeviceToHost, ctx->stream));
     MG_CUDA(cudaStreamSynchronize(ctx->stream));
-    cudaFree(d_len);
-    cudaFree(d_xlen);
-    cudaFree(d_tmp);
-    cudaFree(d_posf);
     ctx->n_elements = (int64_t)st[0];
     ctx->n_expanded = (int64_t)st[1];
     ctx->max_pair_len = (int64_t)st[2];
