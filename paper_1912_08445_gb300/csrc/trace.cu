@@ -41,25 +41,27 @@ __device__ __forceinline__ int32_t velocity_inserts(double va, double ba, double
     return 0;
 }
 
-// Records one element of the half-ray (count pass: counts only).
+// Records one element of the half-ray. The count pass records only the cell (its count,
+// and the first cells for the replay); the fill pass also the path length, the
+// line-of-sight velocity and the expanded-point count of the velocity-step rule.
 template <bool FILL>
 __device__ __forceinline__ bool emit(const TraceArgs &a, int64_t base, int32_t &len, int32_t &x, int32_t cell,
                                      double ds, double vp, double &va, double &ba) {
     if (len >= a.max_steps) return false;
-    double bb = a.b[cell];
-    int32_t ns = velocity_inserts(va, ba, vp, bb, a.dshift_frac);
-    x += ns + 1;
     if (FILL) {
+        double bb = a.b[cell];
+        int32_t ns = velocity_inserts(va, ba, vp, bb, a.dshift_frac);
+        x += ns + 1;
         a.cells[base + len] = cell;
         a.xcum[base + len] = x;
         a.ds[base + len] = ds;
         a.vpar[base + len] = vp;
+        va = vp;
+        ba = bb;
     } else if (a.tmp && len < a.cap_tmp) {
         a.tmp[(int64_t)len * a.n * a.R + base] = cell;   // base = thread index in the count pass
     }
     len++;
-    va = vp;
-    ba = bb;
     return true;
 }
 
@@ -135,16 +137,36 @@ __device__ void walk_3d(const TraceArgs &a, int64_t o, int r, int64_t base, int3
     for (;;) {
         const float scf = (float)s_cur;
         const int64_t e0 = a.nbr_off[cur], e1 = a.nbr_off[cur + 1];
-        // pass 1: validity and the smallest upper bound of a valid candidate's distance
-        float minhi = INFINITY;
+        // pass 1: validity, the smallest upper bound of a valid candidate's distance, and
+        // the two smallest lower bounds
+        float minhi = INFINITY, lo1 = INFINITY, lo2 = INFINITY;
+        int64_t c1 = -1;
+        bool full = false;   // a bound that is not finite leaves the choice to pass 2
         for (int64_t e = e0; e < e1; e++) {
-            const Cand32 k = classify32(a, a.nbr_idx[e], po, n0f, n1f, n2f, scf, s_cur, xo0, xo1, xo2, n0, n1, n2);
-            if (k.valid) minhi = fminf(minhi, k.hi);
+            const int64_t c = a.nbr_idx[e];
+            const Cand32 k = classify32(a, c, po, n0f, n1f, n2f, scf, s_cur, xo0, xo1, xo2, n0, n1, n2);
+            if (!k.valid) continue;
+            if (!(k.lo <= k.hi) || !(fabsf(k.hi) < INFINITY)) full = true;
+            minhi = fminf(minhi, k.hi);
+            if (k.lo < lo1) {
+                lo2 = lo1;
+                lo1 = k.lo;
+                c1 = c;
+            } else if (k.lo < lo2) {
+                lo2 = k.lo;
+            }
         }
-        // pass 2: FP64 for every valid candidate that may be the closest
         int64_t best = -1;
         double bs = 0.0, bd2 = 0.0;
-        for (int64_t e = e0; e < e1; e++) {
+        // Only the candidate with the smallest lower bound reaches min hi: it is the
+        // closest, and only its FP64 projection is needed.
+        const bool unique = c1 >= 0 && !full && lo2 > minhi;
+        if (unique) {
+            best = c1;
+            bs = proj64(a, c1, xo0, xo1, xo2, n0, n1, n2);
+        }
+        // pass 2: FP64 for every valid candidate that may be the closest
+        for (int64_t e = unique ? e1 : e0; e < e1; e++) {
             const int64_t c = a.nbr_idx[e];
             const Cand32 k = classify32(a, c, po, n0f, n1f, n2f, scf, s_cur, xo0, xo1, xo2, n0, n1, n2);
             if (!k.valid || k.lo > minhi) continue;
@@ -158,8 +180,9 @@ __device__ void walk_3d(const TraceArgs &a, int64_t o, int r, int64_t base, int3
             if (better) { best = c; bs = s; bd2 = d2; }
         }
         if (best < 0) { dead = true; return; }
-        const double vp = n0 * (a.vel[3 * best] - vo0) + n1 * (a.vel[3 * best + 1] - vo1) +
-                          n2 * (a.vel[3 * best + 2] - vo2);
+        const double vp = FILL ? n0 * (a.vel[3 * best] - vo0) + n1 * (a.vel[3 * best + 1] - vo1) +
+                                     n2 * (a.vel[3 * best + 2] - vo2)
+                               : 0.0;
         if (!emit<FILL>(a, base, len, x, (int32_t)best, bs - s_cur, vp, va, ba)) { overflow = true; return; }
         s_cur = bs;
         cur = best;
@@ -268,7 +291,7 @@ __global__ void k_trace(TraceArgs a) {
     if (overflow) atomicOr(a.err, 1);
     if (!FILL) {
         a.len[ray] = len;
-        a.xlen[ray] = dead ? -x - 1 : x;   // sign marks a dead end
+        a.xlen[ray] = dead ? -1 : 0;   // dead-end flag; the expanded lengths come from the fill pass
     }
 }
 
@@ -332,6 +355,16 @@ __global__ void k_scan_apply(const int32_t *cnt, int64_t m, const int64_t *bsum,
     int64_t ex = block_excl_scan(v, nullptr);
     if (i < m) out[i] = bsum[blockIdx.x] + ex;
     if (i == m - 1) out[m] = bsum[blockIdx.x] + ex + v;
+}
+
+// Expanded length of every half-ray from the filled store (xcum of its last cell), with
+// the count pass's dead-end flag kept as the sign (-x - 1).
+__global__ void k_xlen(int64_t nr, const int64_t *__restrict__ ray_off, const int32_t *__restrict__ len,
+                       const int32_t *__restrict__ xcum, int32_t *__restrict__ xlen) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nr) return;
+    const int32_t x = len[t] ? xcum[ray_off[t] + len[t] - 1] : 0;
+    xlen[t] = xlen[t] < 0 ? -x - 1 : x;
 }
 
 // ---------------------------------------------------------------- statistics
@@ -469,6 +502,7 @@ int mg_launch_trace(mg_ctx *ctx) {
         k_to_float<<<(unsigned)((total + 255) / 256), 256, 0, ctx->stream>>>(ctx->d_ds, ctx->d_dsf, total);
         k_to_float<<<(unsigned)((total + 255) / 256), 256, 0, ctx->stream>>>(ctx->d_vpar, ctx->d_vparf, total);
     }
+    k_xlen<<<(unsigned)((nr + 255) / 256), 256, 0, ctx->stream>>>(nr, ctx->d_ray_off, d_len, ctx->d_xcum, d_xlen);
     MG_CUDA(cudaMemsetAsync(ctx->d_scal, 0, 4 * sizeof(unsigned long long), ctx->stream));
     const int64_t np = std::max<int64_t>(nr, ctx->n * ctx->P);
     k_ray_stats<<<(unsigned)((np + 255) / 256), 256, 0, ctx->stream>>>(ctx->n, ctx->R, ctx->P, ctx->d_pf, ctx->d_pb,
