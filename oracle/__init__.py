@@ -5,5 +5,5 @@ reference legs may import this package. The CUDA library never calls it.
 """
 from .oracle import (  # noqa: F401
     Oracle, healpix_dirs, antipodes, gauss_hermite, build_oracle, lib_path,
-    CONST, planck, line_width_nu,
+    CONST, planck, line_width_nu, first_order,
 )

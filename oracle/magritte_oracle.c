@@ -755,3 +755,163 @@ int or_trace_all(const or_model *m, int64_t n_orig, const int64_t *origins, cons
     }
     return err ? -1 : 0;
 }
+
+/* ------------------------------------------------------------------ imaging */
+
+/* Formal solution of the first-order transfer equation dI/dtau = S - I across one
+ * interval of optical depth d, with S linear in tau between its end values Sa (entry)
+ * and Sb (exit) (Olson & Kunasz 1987):
+ *   I_out = e I_in + (alpha - e) Sa + (1 - alpha) Sb,  e = exp(-d), alpha = (1 - e)/d.
+ * Reading: for d < 1e-3 the two weights are taken from their Taylor series,
+ *   1 - alpha = d/2 - d^2/6 + d^3/24 - d^4/120,  alpha - e = d/2 - d^2/3 + d^3/8 - d^4/30,
+ * because 1 - alpha cancels there and a floored opacity makes S as large as eta/chi_min. */
+double or_linear_source_step(double I_in, double d, double Sa, double Sb) {
+    double e = exp(-d), wa, wb;
+    if (d < 1e-3) {
+        wb = d * (0.5 - d * (1.0 / 6.0 - d * (1.0 / 24.0 - d / 120.0)));
+        wa = d * (0.5 - d * (1.0 / 3.0 - d * (1.0 / 8.0 - d / 30.0)));
+    } else {
+        double alpha = -expm1(-d) / d;
+        wb = 1.0 - alpha;
+        wa = alpha - e;
+    }
+    return e * I_in + wa * Sa + wb * Sb;
+}
+
+/* Outward intensity after K points with increments dtau[0..K-2] and source S[0..K-1],
+ * entering with I0 at point 0. */
+double or_first_order(int64_t K, const double *dtau, const double *S, double I0) {
+    double I = I0;
+    for (int64_t k = 0; k + 1 < K; k++) I = or_linear_source_step(I, dtau[k], S[k], S[k + 1]);
+    return I;
+}
+
+/* Image of the model along ray direction r (Sec. 3.5, 'Imaging the model'): every
+ * origin point o gives one image point, the projection of its position on the plane
+ * orthogonal to n = dirs[r], with the intensity leaving the model along n on the ray
+ * pair through o. xy[o] = (x.e1, x.e2) with e1 = (z x n)/|z x n| (x in place of z when
+ * |n_z| >= 0.9) and e2 = n x e1.
+ * Readings (the paper says only that images come from the outward radiation at the
+ * ray-pair end points):
+ *  - channel c has frequency nu_l (1 + u_c/c) in the rest frame of the model (u_c in
+ *    velocity units, as the bins' r_q b_o); at a point of velocity v its comoving
+ *    frequency is nu (1 - n.v/c), to first order in v/c, for radiation travelling
+ *    along n; all lines contribute to opacity and emissivity as in the formal solve;
+ *  - the points, path lengths, interpolation, floors and dtau are those of the formal
+ *    solve's ray pair (the far end of the half-ray along -n first);
+ *  - the intensity is carried along n with the first-order linear-source step above,
+ *    entering with the CMB at the comoving frequency of the far end of the -n half;
+ *    a model point with both halves empty shows the CMB at its own comoving frequency.
+ * Output I[io][n_ch]. */
+int or_image(const or_model *m, const double *pops, int r, int line, int n_ch, const double *u_ch,
+             int64_t n_orig, const int64_t *origins, double *I, double *xy, int nthreads) {
+    if (r < 0 || r >= m->R || line < 0 || line >= m->n_lines || n_ch < 1) return -1;
+    int nl = m->n_lines;
+    int64_t N = m->n;
+    const double *n = &m->dirs[3 * r];
+    int rb = m->antipode[r];
+    double e1[3], e2[3];
+    {
+        double a[3] = {0.0, 0.0, 1.0};
+        if (fabs(n[2]) >= 0.9) { a[0] = 1.0; a[2] = 0.0; }
+        e1[0] = a[1] * n[2] - a[2] * n[1];
+        e1[1] = a[2] * n[0] - a[0] * n[2];
+        e1[2] = a[0] * n[1] - a[1] * n[0];
+        double l1 = sqrt(e1[0] * e1[0] + e1[1] * e1[1] + e1[2] * e1[2]);
+        for (int i = 0; i < 3; i++) e1[i] /= l1;
+        e2[0] = n[1] * e1[2] - n[2] * e1[1];
+        e2[1] = n[2] * e1[0] - n[0] * e1[2];
+        e2[2] = n[0] * e1[1] - n[1] * e1[0];
+    }
+    double *eta_c = malloc(sizeof(double) * N * nl), *chi_c = malloc(sizeof(double) * N * nl);
+    if (!eta_c || !chi_c) { free(eta_c); free(chi_c); return -2; }
+    all_line_integrals(m, pops, eta_c, chi_c);
+    double nu_l = line_nu(m, line);
+    int err = 0;
+    int64_t cap = m->max_steps;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+    #pragma omp parallel for schedule(dynamic, 4) reduction(|:err)
+#endif
+    for (int64_t io = 0; io < n_orig; io++) {
+        int64_t o = origins[io];
+        const double *x = &m->pos[3 * o];
+        if (xy) {
+            xy[2 * io] = x[0] * e1[0] + x[1] * e1[1] + x[2] * e1[2];
+            xy[2 * io + 1] = x[0] * e2[0] + x[1] * e2[1] + x[2] * e2[2];
+        }
+        int32_t *cf = malloc(sizeof(int32_t) * cap), *cb = malloc(sizeof(int32_t) * cap);
+        int32_t *nf = malloc(sizeof(int32_t) * cap), *nb = malloc(sizeof(int32_t) * cap);
+        double *dsf = malloc(sizeof(double) * cap), *dsb = malloc(sizeof(double) * cap);
+        double *vf = malloc(sizeof(double) * cap), *vb = malloc(sizeof(double) * cap);
+        double *buf = NULL;
+        do {
+            if (!cf || !cb || !nf || !nb || !dsf || !dsb || !vf || !vb) { err |= 1; break; }
+            int64_t lf, lb; int de;
+            if (or_trace(m, o, r, cap, cf, nf, dsf, vf, &lf, &de)) { err |= 2; break; }
+            if (or_trace(m, o, rb, cap, cb, nb, dsb, vb, &lb, &de)) { err |= 2; break; }
+            int64_t Kb = 0, Kf = 0;
+            for (int64_t e = 0; e < lb; e++) Kb += nb[e] + 1;
+            for (int64_t e = 0; e < lf; e++) Kf += nf[e] + 1;
+            int64_t K = Kb + 1 + Kf;
+            /* per point: path length to the next point, rest-frame line-of-sight velocity
+             * n.v, width, line data; then per channel chi, S and dtau */
+            buf = malloc(sizeof(double) * ((size_t)K * (6 + 2 * (size_t)nl) + 2 * (size_t)K));
+            if (!buf) { err |= 1; break; }
+            double *ds = buf, *w = ds + K, *b = w + K, *eta = b + K, *chi = eta + K * nl;
+            double *ch = chi + K * nl, *S = ch + K, *dtau = S + K, *tmp = dtau + K;
+            double *hds = tmp, *hv = tmp + K;   /* scratch for one expanded half (reused) */
+            double *hb = malloc(sizeof(double) * K * (1 + 2 * (size_t)nl));
+            if (!hb) { err |= 1; break; }
+            double *heta = hb + K, *hchi = heta + K * nl;
+            double nvo = n[0] * m->vel[3 * o] + n[1] * m->vel[3 * o + 1] + n[2] * m->vel[3 * o + 2];
+            /* the -n half, far end first: its line-of-sight velocity is (-n).(v - v_o) */
+            int64_t eb = expand_half(m, o, lb, cb, nb, dsb, vb, eta_c, chi_c, hds, hv, hb, heta, hchi, K, K);
+            int64_t k = 0;
+            for (int64_t j = eb - 1; j >= 0; j--, k++) {
+                ds[k] = hds[j];
+                w[k] = nvo - hv[j];
+                b[k] = hb[j];
+                for (int l = 0; l < nl; l++) { eta[l * K + k] = heta[l * K + j]; chi[l * K + k] = hchi[l * K + j]; }
+            }
+            ds[k] = 0.0; w[k] = nvo; b[k] = or_width(m, o);
+            for (int l = 0; l < nl; l++) { eta[l * K + k] = eta_c[l * N + o]; chi[l * K + k] = chi_c[l * N + o]; }
+            k++;
+            int64_t ef = expand_half(m, o, lf, cf, nf, dsf, vf, eta_c, chi_c, hds, hv, hb, heta, hchi, K, K);
+            for (int64_t j = 0; j < ef; j++, k++) {
+                ds[k - 1] = hds[j];
+                w[k] = nvo + hv[j];
+                b[k] = hb[j];
+                for (int l = 0; l < nl; l++) { eta[l * K + k] = heta[l * K + j]; chi[l * K + k] = hchi[l * K + j]; }
+            }
+            for (int c = 0; c < n_ch; c++) {
+                double u = u_ch[c];
+                for (int64_t q = 0; q < K; q++) {
+                    double x_ch = 0.0, x_et = 0.0;
+                    for (int l2 = 0; l2 < nl; l2++) {
+                        double nu2 = line_nu(m, l2);
+                        double xx = (C_LIGHT * (nu_l - nu2) / nu2 + (nu_l / nu2) * (u * (1.0 - w[q] / C_LIGHT) - w[q])) / b[q];
+                        double dnu = nu2 * b[q] / C_LIGHT;
+                        double phi = exp(-xx * xx) / (dnu * SQRT_PI);
+                        x_ch += chi[l2 * K + q] * phi;
+                        x_et += eta[l2 * K + q] * phi;
+                    }
+                    if (x_ch < m->chi_min) x_ch = m->chi_min;
+                    ch[q] = x_ch;
+                    S[q] = x_et / x_ch;
+                }
+                for (int64_t q = 0; q + 1 < K; q++) {
+                    double dt = 0.5 * (ch[q] + ch[q + 1]) * ds[q];
+                    dtau[q] = dt < m->dtau_min ? m->dtau_min : dt;
+                }
+                double nu_c = nu_l * (1.0 + u / C_LIGHT);
+                double I0 = planck(nu_c * (1.0 - w[0] / C_LIGHT), m->T_cmb);
+                I[io * n_ch + c] = or_first_order(K, dtau, S, I0);
+            }
+            free(hb);
+        } while (0);
+        free(cf); free(cb); free(nf); free(nb); free(dsf); free(dsb); free(vf); free(vb); free(buf);
+    }
+    free(eta_c); free(chi_c);
+    return err ? -3 : 0;
+}

@@ -165,6 +165,9 @@ def _lib():
         L.or_trace_all.argtypes = [P, C.c_int64, P, P, P, P, P, P, P, P, C.c_int]
         L.or_width.argtypes = [P, C.c_int64]
         L.or_width.restype = C.c_double
+        L.or_image.argtypes = [P, P, C.c_int, C.c_int, C.c_int, P, C.c_int64, P, P, P, C.c_int]
+        L.or_first_order.argtypes = [C.c_int64, P, P, C.c_double]
+        L.or_first_order.restype = C.c_double
         _LIB = L
     return _LIB
 
@@ -272,6 +275,24 @@ class Oracle:
             raise RuntimeError(f"or_formal_solve failed ({rc})")
         return (J, L, E, Jnu) if spectrum else (J, L, E)
 
+    def image(self, pops, ray, line, u_ch, origins=None):
+        """Image along direction dirs[ray] (Sec. 3.5): intensity I [n_orig][n_ch] leaving
+        the model along that direction on the ray pair through each origin, at channel
+        frequencies nu_line (1 + u_ch/c) in the model's rest frame, and the origins'
+        projections xy [n_orig][2] on the plane orthogonal to the direction."""
+        pops = np.ascontiguousarray(pops, np.float64)
+        if origins is None:
+            origins = np.arange(self.model.n, dtype=np.int64)
+        origins = np.ascontiguousarray(origins, np.int64)
+        u = np.ascontiguousarray(u_ch, np.float64)
+        I = np.empty((origins.shape[0], u.shape[0]))
+        xy = np.empty((origins.shape[0], 2))
+        rc = _lib().or_image(self.mp, _ptr(pops), int(ray), int(line), u.shape[0], _ptr(u),
+                             origins.shape[0], _ptr(origins), _ptr(I), _ptr(xy), self.nthreads)
+        if rc:
+            raise RuntimeError(f"or_image failed ({rc})")
+        return I, xy
+
     def stateq(self, J, L, Jeff):
         out = np.empty((self.model.n, self.model.species.n_lev))
         nf = C.c_int64(0)
@@ -314,3 +335,10 @@ def feautrier(dtau, S, I0, IK, ko):
     _lib().or_feautrier(K, int(ko), _ptr(dtau), _ptr(S), float(I0), float(IK), C.byref(u),
                         C.byref(lam), _ptr(work))
     return u.value, lam.value
+
+
+def first_order(dtau, S, I0):
+    """Outward intensity of dI/dtau = S - I over points with increments dtau, S linear in
+    tau between points (Olson & Kunasz 1987), entering with I0."""
+    dtau = np.ascontiguousarray(dtau, np.float64); S = np.ascontiguousarray(S, np.float64)
+    return _lib().or_first_order(S.shape[0], _ptr(dtau), _ptr(S), float(I0))

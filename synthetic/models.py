@@ -421,3 +421,75 @@ def model_lattice_3d(m=7, spacing=1e12, n_q=7):
                  species=sp, geometry=GEOM_3D, n_q=n_q,
                  dirs=np.array([[1.0, 0, 0], [-1.0, 0, 0], [0, 1.0, 0], [0, -1.0, 0],
                                 [0, 0, 1.0], [0, 0, -1.0]]))
+
+
+def shell_counts(radii, n_cells, floor=12):
+    """Points per shell for a shell mesh of n_cells points: proportional to r^2 (a
+    uniform point density), at least `floor` per shell, the rounding remainder taken
+    up by the outermost shell."""
+    r2 = np.asarray(radii, np.float64) ** 2
+    lo, hi = 0.0, float(n_cells) / r2.max() * 2.0
+    for _ in range(200):   # bisect the scale so that the counts sum to about n_cells
+        mid = 0.5 * (lo + hi)
+        s = np.maximum(floor, np.round(mid * r2)).sum()
+        lo, hi = (mid, hi) if s < n_cells else (lo, mid)
+    cnt = np.maximum(floor, np.round(lo * r2)).astype(np.int64)
+    cnt[-1] += n_cells - cnt.sum()
+    return cnt
+
+
+def shells_3d(radii, n_cells, seed=0, k=16):
+    """A 3D point mesh made of spherical shells (the paper's mapping of a 1D radial
+    grid to 3D, Sec. 4.1): shell i is a Fibonacci lattice of shell_counts() points at
+    radius radii[i], each turned by a seeded random rotation; the outermost shell is the
+    boundary. Returns positions, boundary flags and the shell index of every point."""
+    rng = np.random.default_rng(seed)
+    cnt = shell_counts(radii, n_cells)
+    pos, shell = [], []
+    for i, (r, m) in enumerate(zip(radii, cnt)):
+        q, _ = np.linalg.qr(rng.normal(size=(3, 3)))
+        pos.append(_fibonacci_sphere(int(m), r) @ q.T)
+        shell.append(np.full(int(m), i))
+    pos = np.concatenate(pos)
+    shell = np.concatenate(shell)
+    is_bdy = (shell == len(radii) - 1).astype(np.uint8)
+    return pos, is_bdy, shell
+
+
+def hubble_shells_3d(n_shells=50, n_cells=12_528, R=495e3, c_dbeta=0.01, n_q=100, nside=4,
+                     k=16, seed=0):
+    """3D Hubble-Lemaitre model of the paper's test table (Sec. 4.1.1): the radii of the
+    uniform 1D grid of 2 n_shells cells in [-R, R] as shells of 3D points (n_cells in
+    all), v = c dbeta x, n_H2 = 1e12 m^-3, X = 1e-4, T = 45 K, no turbulence, the 2-level
+    species of the paper's Table 'test_species'."""
+    x = np.linspace(-R, R, 2 * n_shells)
+    radii = x[n_shells:]
+    pos, is_bdy, shell = shells_3d(radii, n_cells, seed=seed)
+    n = pos.shape[0]
+    fields = dict(n_coll=np.full(n, 1e12), T=np.full(n, 45.0), v_turb=np.zeros(n),
+                  n_spec=np.full(n, 1e8))
+    m = _finish("hubble_shells", pos, c_dbeta * pos, is_bdy, fields, species_two_level(), k,
+                nside, n_q, dict(seed=seed, R=R, c_dbeta=c_dbeta))
+    return m
+
+
+def vz_problem1(abundance=1e-6, v_inf=0.0, gamma=0.5, n_shells=50, R_in=1e13, R=7.8e16,
+                n_in=2e13, n_q=31, nside=2):
+    """Van Zadelhoff et al. (2002) problem 1 as used in the paper (Sec. 4.2.1, 4.2.2): the
+    power-law cloud n_H2 = n_in (R_in/r)^2 on n_shells log-spaced radii in [R_in, R]
+    with an empty core, T = 20 K, 150 m/s turbulence, the 2-level species of Table
+    'test_species', X = 1e-8 (problem 1a) or 1e-6 (1b), and the radial outflow
+    v = v_inf ((r - R_in)/(R - R_in))^gamma of problems 1c/1d (v_inf = 0: 1a/1b).
+    Spherically symmetric geometry (one point per radius on the +z axis)."""
+    r = np.geomspace(R_in, R, n_shells)
+    m = model_sphere_1d(n=n_shells, r_min=R_in, r_max=R, n_q=n_q, nside=nside, A21=1.0e-4,
+                        abundance=abundance)
+    m.n_coll = n_in * (R_in / r) ** 2
+    m.n_spec = abundance * m.n_coll
+    m.T = np.full(n_shells, 20.0)
+    m.v_turb = np.full(n_shells, 150.0)
+    m.vel = np.zeros((n_shells, 3))
+    m.vel[:, 2] = v_inf * ((r - R_in) / (R - R_in)) ** gamma
+    m.name = "vz_p1"
+    m.meta = dict(abundance=abundance, v_inf=v_inf, gamma=gamma)
+    return m
