@@ -463,6 +463,65 @@ def run_disc(args):
                       "trace_s": trace_s, "ray_stats": st, "kernel_ms": {k: v2[0] / max(v2[1], 1) for k, v2 in kt.items()}}))
 
 
+def run_image(args):
+    """Images of the Keplerian disc (Sec. 3.5): one FP64 image per step of the lowest
+    line along one ray direction, 63 channels over +-15 km/s, every point a pixel.
+    value: pixel-channel intensities per second from the image kernel's CUDA-event time;
+    e2e: the same through mg_image with the image copied back to host memory every step.
+    The algorithmic work (points of the pairs along that direction x channels) is
+    estimated from 4000 sampled pairs."""
+    import numpy as np
+    import torch
+    import paper_1912_08445_gb300 as mg
+    import synthetic as syn
+    m = syn.model_disc(n=args.disc_points, seed=0)
+    ctx = mg.Context(precision=mg.MG_MIXED, profile=1)
+    ctx.load_model(m)
+    ctx.trace_rays()
+    ctx.init_populations()
+    ray, n_ch = 40, 63
+    u = np.linspace(-15e3, 15e3, n_ch)
+    anti = ctx.get_directions()[1][ray]
+    rng = np.random.default_rng(0)
+    samp = rng.choice(m.n, min(4000, m.n), replace=False)
+    def half_points(o, r):
+        g = ctx.get_ray(int(o), r, cap=8192)
+        return len(g["cells"]) + int(g["nsub"].sum())
+    plen = [1 + half_points(o, ray) + half_points(o, anti) for o in samp]
+    mean_K = float(np.mean(plen))
+    dI = torch.empty((m.n, n_ch), dtype=torch.float64, device="cuda")
+    for _ in range(args.warmup):
+        ctx.image_dev(ray, 0, u, dI.data_ptr())
+    ctx.reset_kernel_times()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        ctx.image_dev(ray, 0, u, dI.data_ptr())
+    torch.cuda.synchronize()
+    wall_dev = (time.perf_counter() - t0) / args.steps
+    kt = ctx.kernel_times()
+    k_ms, k_n = kt["image_fp64"]
+    kernel_s = k_ms / k_n / 1e3
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        I, xy = ctx.image(ray, 0, u)
+    e2e_s = (time.perf_counter() - t0) / args.steps
+    pix = m.n * n_ch
+    updates = mean_K * pix
+    # FP64 bound per point-channel update at the measured pipe rates of this GPU: three
+    # exponentials (profile, exp(-dtau), expm1), two divisions, ~30 DFMA-pipe operations
+    bound_s = updates * (3 / 31e9 + 2 / 66e9 + 30 / 0.50e12)
+    print(json.dumps({"metric": "image pixel-channel intensities/s", "unit": "intensities/s",
+                      "workload": f"Keplerian disc, {m.n} points, image along ray {ray} of 192, line 0, "
+                                  f"{n_ch} channels over +-15 km/s, FP64",
+                      "value": pix / kernel_s, "ms_per_image": kernel_s * 1e3, "wall_ms_per_image": wall_dev * 1e3,
+                      "e2e": {"value": pix / e2e_s, "unit": "intensities/s", "ms_per_image": e2e_s * 1e3,
+                              "d2h_bytes_per_step": int(pix * 8 + m.n * 16)},
+                      "mean_pair_points": mean_K, "cell_channel_updates_per_s": updates / kernel_s,
+                      "fp64_bound_ms": bound_s * 1e3, "fraction_of_fp64_bound": bound_s / kernel_s,
+                      "max_I": float(I.max()), "min_I": float(I.min())}))
+
+
 def run_learned(args):
     """Learned initial populations (20-level rotor): trains the network on converged
     populations of seeded cloud/disc models, then compares on held-out seeds the ALI to
@@ -523,7 +582,7 @@ def main():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--ali", action="store_true", help="measure ALI time to converge instead")
-    ap.add_argument("--workload", default="clumpy", choices=["clumpy", "batch", "disc", "learned"])
+    ap.add_argument("--workload", default="clumpy", choices=["clumpy", "batch", "disc", "learned", "image"])
     ap.add_argument("--corpus", type=int, default=200)
     ap.add_argument("--corpus-points", type=int, default=3000)
     ap.add_argument("--epochs", type=int, default=30)
@@ -540,6 +599,8 @@ def main():
         run_disc(args)
     elif args.workload == "learned":
         run_learned(args)
+    elif args.workload == "image":
+        run_image(args)
     elif args.ali:
         run_ali(args)
     elif args.impl == "reference":

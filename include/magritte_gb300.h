@@ -8,8 +8,8 @@
  *   HEALPix directions (Sec. 3.1.3), Doppler-shifted Gaussian line profiles (Sec. 2.2.1),
  *   the second-order Feautrier solve of each ray pair with the diagonal approximate
  *   Lambda operator (Sec. 3.3, 3.4, eq. 'GFE', 'ALO', 'ourJeff'), per-cell statistical
- *   equilibrium (eq. 'ourALI'), the validity check (Sec. 6.1) and Ng acceleration
- *   (Sec. 3.4).
+ *   equilibrium (eq. 'ourALI'), the validity check (Sec. 6.1), Ng acceleration
+ *   (Sec. 3.4), and images from the outward radiation on each point's ray pair (Sec. 3.5).
  *
  * Conventions
  *   - Units are SI: m, m/s, K, m^-3, J, s^-1, m^3 s^-1. Intensities are W m^-2 Hz^-1 sr^-1.
@@ -181,6 +181,33 @@ int mg_get_radiation(const mg_ctx *ctx, double *J, double *L, double *Jeff);
 int mg_get_radiation_dev(const mg_ctx *ctx, double *d_J, double *d_L, double *d_Jeff);
 /* Per-bin mean intensity (1/P) sum_pairs u, [n][n_lines][n_q]; needs opt.spectrum = 1. */
 int mg_get_spectrum(const mg_ctx *ctx, double *Jnu);
+
+/* Image of the model along ray direction `ray` (Sec. 3.5, 'Imaging the model'): every
+ * point o contributes one image point, its projection on the plane orthogonal to
+ * n = dirs[ray], carrying the intensity that leaves the model along n on the ray pair
+ * through o.
+ *   ray      in [0, R): the direction n (the pair is ray and its antipode);
+ *   line     in [0, n_lines): reference line of the channels;
+ *   u_ch     [n_ch] host: channel c has rest-frame frequency nu_line (1 + u_ch[c]/c)
+ *            (velocity units, as the formal solve's bins r_q b_o); |u_ch| < c/10;
+ *   I        [n][n_ch] output intensity, W m^-2 Hz^-1 sr^-1;
+ *   xy       [n][2] output sky-plane coordinates (x.e1, x.e2), e1 = (z x n)/|z x n|
+ *            (x in place of z when |n_z| >= 0.9), e2 = n x e1; NULL allowed.
+ * Method: along the pair's points (those of the formal solve: traced cells, inserted
+ * points, interpolated line data, floors, trapezoidal dtau) the intensity is carried
+ * from the far end of the -n half, where the CMB enters at its comoving frequency, to
+ * the far end of the n half with the first-order equation dI/dtau = S - I, the source
+ * linear in tau between points (Olson & Kunasz 1987). At a point of velocity v the
+ * comoving frequency is nu (1 - n.v/c). All lines whose profiles reach the channels add
+ * to opacity and emissivity. FP64 in both precisions, from the current populations.
+ * Requires traced rays and populations (MG_ERR_STATE otherwise); 1 <= n_ch <=
+ * MG_IMAGE_MAX_CHANNELS (MG_ERR_ARG otherwise). Synchronises the context's stream. */
+#define MG_IMAGE_MAX_CHANNELS 4096
+int mg_image(mg_ctx *ctx, int32_t ray, int32_t line, int32_t n_ch, const double *u_ch, double *I, double *xy);
+/* mg_image into device buffers d_I [n][n_ch] and d_xy [n][2] (d_xy may be NULL); u_ch
+ * stays a host array. Synchronises the context's stream. */
+int mg_image_dev(mg_ctx *ctx, int32_t ray, int32_t line, int32_t n_ch, const double *u_ch, double *d_I,
+                 double *d_xy);
 
 /* Statistical equilibrium with the diagonal ALO (eq. 'ourALI') for every cell, the
  * validity check (negative or non-finite populations -> the cell is solved again

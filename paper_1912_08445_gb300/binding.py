@@ -83,6 +83,8 @@ _SIGS = {
     "mg_get_radiation": (C.c_int, [_P, _P, _P, _P]),
     "mg_get_radiation_dev": (C.c_int, [_P, _P, _P, _P]),
     "mg_get_spectrum": (C.c_int, [_P, _P]),
+    "mg_image": (C.c_int, [_P, C.c_int32, C.c_int32, C.c_int32, _P, _P, _P]),
+    "mg_image_dev": (C.c_int, [_P, C.c_int32, C.c_int32, C.c_int32, _P, _P, _P]),
     "mg_update_populations": (C.c_int, [_P, _P]),
     "mg_update_populations_noalloc": (C.c_int, [_P, _P, _P, _P, _P]),
     "mg_iterate": (C.c_int, [_P, _P]),
@@ -295,6 +297,20 @@ class Context:
         out = np.empty((self.n, self.n_lines, self.Q))
         self._chk(self.lib.mg_get_spectrum(self.h, _ptr(out)), "mg_get_spectrum")
         return out
+
+    def image(self, ray, line, u_ch):
+        """Image along dirs[ray]: intensity I [n][n_ch] at channel offsets u_ch (m/s) of
+        line `line`, and sky-plane coordinates xy [n][2]."""
+        u = _c(u_ch, np.float64)
+        I = np.empty((self.n, u.shape[0])); xy = np.empty((self.n, 2))
+        self._chk(self.lib.mg_image(self.h, int(ray), int(line), u.shape[0], _ptr(u), _ptr(I), _ptr(xy)), "mg_image")
+        return I, xy
+
+    def image_dev(self, ray, line, u_ch, d_I, d_xy=None):
+        """mg_image into device buffers (integer device addresses)."""
+        u = _c(u_ch, np.float64)
+        self._chk(self.lib.mg_image_dev(self.h, int(ray), int(line), u.shape[0], _ptr(u), _ptr(d_I),
+                                        _ptr(d_xy)), "mg_image_dev")
 
     def update_populations(self):
         ch = C.c_double(0)

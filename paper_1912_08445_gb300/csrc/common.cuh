@@ -69,6 +69,8 @@ struct mg_ctx {
     int32_t *d_nbr_idx = nullptr;
     uint8_t *d_bdy = nullptr;
     std::vector<double> h_T, h_vturb;      // kept to compute widths once the mass is known
+    double vmax = 0.0;                     // largest |v| over the points (image line lists)
+    double bmax = 0.0;                     // largest velocity width
 
     // ---- model
     bool have_model = false;
@@ -139,6 +141,12 @@ struct mg_ctx {
     mg_mlp *mlp = nullptr;        // attached network for MG_INIT_MLP (not owned)
     int32_t *d_promo = nullptr;   // [n] origin list, then [n] count in d_promo[n]
 
+    // ---- images: channel offsets, candidate lines, output buffers (grow-only)
+    double *d_uch = nullptr, *d_img = nullptr, *d_imgxy = nullptr;
+    mg::Overlap *d_imgov = nullptr;
+    int64_t img_cap = 0;
+    int32_t uch_cap = 0;
+
     // ---- launch variant of the mixed formal solve (-1: default for the model)
     int mixed_variant = -1;
 
@@ -185,6 +193,9 @@ struct MgTimed {
 int mg_launch_trace(mg_ctx *ctx);
 int mg_launch_line_data(mg_ctx *ctx);
 int mg_launch_line_data_mixed(mg_ctx *ctx);
+int mg_launch_line_data64(mg_ctx *ctx, unsigned long long *neg);
+int mg_launch_image(mg_ctx *ctx, int ray, int line, int n_ch, const double *d_u, const mg::Overlap *d_ov,
+                    int n_ov, double *d_I, double *d_xy);
 int mg_launch_feautrier(mg_ctx *ctx);
 int mg_launch_feautrier_fp64_list(mg_ctx *ctx, const int32_t *olist, const int32_t *ocount);
 int mg_autotune_mixed(mg_ctx *ctx, int reps, int *best, double *best_ms, int *n_tried);

@@ -119,6 +119,7 @@ extern "C" int mg_destroy(mg_ctx *ctx) {
     mg_free(ctx->d_line); mg_free(ctx->d_linef); mg_free(ctx->d_J); mg_free(ctx->d_L);
     mg_free(ctx->d_Jeff); mg_free(ctx->d_Lc); mg_free(ctx->d_Jnu); mg_free(ctx->d_scal);
     mg_free(ctx->d_err);
+    mg_free(ctx->d_uch); mg_free(ctx->d_img); mg_free(ctx->d_imgxy); mg_free(ctx->d_imgov);
     if (ctx->h_scal) cudaFreeHost(ctx->h_scal);
     if (ctx->ev0) cudaEventDestroy(ctx->ev0);
     if (ctx->ev1) cudaEventDestroy(ctx->ev1);
@@ -170,6 +171,10 @@ extern "C" int mg_set_mesh(mg_ctx *ctx, int64_t n, const double *pos, const doub
     ctx->n = n;
     ctx->geometry = geometry;
     ctx->n_edges = E;
+    ctx->vmax = 0.0;
+    for (int64_t i = 0; i < n; i++)
+        ctx->vmax = std::max(ctx->vmax, std::sqrt(vel[3 * i] * vel[3 * i] + vel[3 * i + 1] * vel[3 * i + 1] +
+                                                  vel[3 * i + 2] * vel[3 * i + 2]));
     int rc;
     if ((rc = mg_alloc(ctx, &ctx->d_pos, 3 * n)) || (rc = mg_alloc(ctx, &ctx->d_vel, 3 * n)) ||
         (rc = mg_alloc(ctx, &ctx->d_nbr_off, n + 1)) || (rc = mg_alloc(ctx, &ctx->d_nbr_idx, E)) ||
@@ -199,8 +204,10 @@ static int refresh_widths(mg_ctx *ctx) {
     if (!ctx->have_model || !ctx->have_species) return MG_OK;
     std::vector<double> b(ctx->n);
     std::vector<float> bf(ctx->n);
+    ctx->bmax = 0.0;
     for (int64_t i = 0; i < ctx->n; i++) {
         b[i] = width_of(ctx->h_T[i], ctx->h_vturb[i], ctx->mass);
+        ctx->bmax = std::max(ctx->bmax, b[i]);
         bf[i] = (float)b[i];
     }
     int rc;
@@ -706,6 +713,76 @@ extern "C" int mg_get_spectrum(const mg_ctx *cctx, double *Jnu) {
     MG_CUDA(cudaMemcpyAsync(Jnu, ctx->d_Jnu, 8 * ctx->n * ctx->n_lines * ctx->Q, cudaMemcpyDeviceToHost, ctx->stream));
     MG_CUDA(cudaStreamSynchronize(ctx->stream));
     return MG_OK;
+}
+
+// ------------------------------------------------------------------ images
+static int image_common(mg_ctx *ctx, int32_t ray, int32_t line, int32_t n_ch, const double *u_ch, bool dev,
+                        double *I, double *xy) {
+    if (!ctx) return MG_ERR_ARG;
+    if (!ctx->traced) return mg_fail(ctx, MG_ERR_STATE, "mg_image: trace the rays first");
+    if (!ctx->have_pops) return mg_fail(ctx, MG_ERR_STATE, "mg_image: set or initialise populations first");
+    if (ray < 0 || ray >= ctx->R || line < 0 || line >= ctx->n_lines || n_ch < 1 || n_ch > MG_IMAGE_MAX_CHANNELS ||
+        !u_ch || !I)
+        return mg_fail(ctx, MG_ERR_ARG, "mg_image: bad ray, line, channel count or null pointer");
+    double umax = 0.0;
+    for (int c = 0; c < n_ch; c++) {
+        if (!(std::fabs(u_ch[c]) < 0.1 * kC)) return mg_fail(ctx, MG_ERR_ARG, "mg_image: channel offsets must be finite and below c/10");
+        umax = std::max(umax, std::fabs(u_ch[c]));
+    }
+    cudaSetDevice(ctx->device);
+    int rc;
+    if ((rc = ensure_state(ctx))) return rc;
+    // Lines within reach of the channels: for line l2, |x| >= (|dnl| - rat (umax + V (1 + umax/c)))/b_max
+    // with V the largest speed, so beyond 28 widths exp(-x^2) underflows to zero and the line is left out.
+    const double nu_l = ctx->h_lines[line].nu;
+    std::vector<Overlap> ov;
+    for (int l2 = 0; l2 < ctx->n_lines; l2++) {
+        const double nu2 = ctx->h_lines[l2].nu;
+        Overlap d{};
+        d.dnl = kC * (nu_l - nu2) / nu2;
+        d.rat = nu_l / nu2;
+        d.inv_nu2 = 1.0 / nu2;
+        d.l2 = l2;
+        const double reach = d.rat * (umax + ctx->vmax * (1.0 + umax / kC));
+        if (l2 == line || std::fabs(d.dnl) - reach <= 28.0 * ctx->bmax) ov.push_back(d);
+    }
+    const int64_t need = ctx->n * (int64_t)n_ch;
+    if (!dev && need > ctx->img_cap) {
+        if ((rc = mg_alloc(ctx, &ctx->d_img, need))) return rc;
+        ctx->img_cap = need;
+    }
+    if (n_ch > ctx->uch_cap) {
+        if ((rc = mg_alloc(ctx, &ctx->d_uch, n_ch))) return rc;
+        ctx->uch_cap = n_ch;
+    }
+    if (!ctx->d_imgov && (rc = mg_alloc(ctx, &ctx->d_imgov, ctx->n_lines))) return rc;
+    if (!ctx->d_imgxy && (rc = mg_alloc(ctx, &ctx->d_imgxy, 2 * ctx->n))) return rc;
+    MG_CUDA(cudaMemcpyAsync(ctx->d_uch, u_ch, 8 * (size_t)n_ch, cudaMemcpyHostToDevice, ctx->stream));
+    MG_CUDA(cudaMemcpyAsync(ctx->d_imgov, ov.data(), sizeof(Overlap) * ov.size(), cudaMemcpyHostToDevice, ctx->stream));
+    if ((rc = mg_launch_line_data64(ctx, ctx->d_scal + 6))) return rc;
+    double *d_I = dev ? I : ctx->d_img;
+    double *d_xy = dev ? xy : ctx->d_imgxy;
+    if (!d_xy) d_xy = ctx->d_imgxy;
+    if ((rc = mg_launch_image(ctx, ray, line, n_ch, ctx->d_uch, ctx->d_imgov, (int)ov.size(), d_I, d_xy))) return rc;
+    if (!dev) {
+        MG_CUDA(cudaMemcpyAsync(I, d_I, 8 * (size_t)need, cudaMemcpyDeviceToHost, ctx->stream));
+        if (xy) MG_CUDA(cudaMemcpyAsync(xy, d_xy, 16 * (size_t)ctx->n, cudaMemcpyDeviceToHost, ctx->stream));
+    }
+    int32_t err = 0;
+    MG_CUDA(cudaMemcpyAsync(&err, ctx->d_err, 4, cudaMemcpyDeviceToHost, ctx->stream));
+    MG_CUDA(cudaStreamSynchronize(ctx->stream));
+    if (err) return mg_fail(ctx, MG_ERR_CAPACITY, "mg_image: a ray pair is longer than the traced maximum");
+    return MG_OK;
+}
+
+extern "C" int mg_image(mg_ctx *ctx, int32_t ray, int32_t line, int32_t n_ch, const double *u_ch, double *I,
+                        double *xy) {
+    return image_common(ctx, ray, line, n_ch, u_ch, false, I, xy);
+}
+
+extern "C" int mg_image_dev(mg_ctx *ctx, int32_t ray, int32_t line, int32_t n_ch, const double *u_ch, double *d_I,
+                            double *d_xy) {
+    return image_common(ctx, ray, line, n_ch, u_ch, true, d_I, d_xy);
 }
 
 // ------------------------------------------------------------------ statistical equilibrium

@@ -262,6 +262,121 @@ __global__ void k_feautrier64(SolveArgs a) {
         for (int f = threadIdx.x; f < F; f += blockDim.x) a.Jnu[o * F + f] = acc[4 * f] * invP;
 }
 
+// ---------------------------------------------------------------- images
+// Image along direction n (Sec. 3.5): each origin point o gives the intensity leaving the
+// model along n on its ray pair, carried from the far end of the -n half to the far end
+// of the n half with the first-order equation dI/dtau = S - I, the source linear in tau
+// between points (Olson & Kunasz 1987):
+//   I_{k+1} = e I_k + (alpha - e) S_k + (1 - alpha) S_{k+1},  e = exp(-dtau), alpha = (1 - e)/dtau,
+// with the weights' Taylor series below dtau = 1e-3 (1 - alpha cancels there, and a
+// floored opacity makes S as large as eta/chi_min).
+// Channel c has rest-frame frequency nu_l (1 + u_c/c); at a point with rest-frame
+// line-of-sight velocity w = n.v its comoving frequency is nu (1 - w/c). The staged pair
+// holds each half's velocity relative to o along that half's own direction, so
+// w = n.v_o - v on the -n half and n.v_o + v on the n half. All lines within reach of
+// the channels (the host's list, which leaves out only lines whose profile underflows
+// to zero everywhere) add to opacity and emissivity.
+struct ImageArgs {
+    SolveArgs s;              // ray store, widths, line data, floors, kmax, err
+    int32_t rf, rb, n_ch, n_ov;
+    const double *u;          // [n_ch]
+    const Overlap *ov;        // [n_ov] lines within reach of the channels
+    const double *vel;        // [n][3]
+    const double *pos;        // [n][3]
+    double n0, n1, n2;        // direction
+    double e1[3], e2[3];      // sky-plane basis
+    double nu_l;              // reference line frequency
+    double *I;                // [n][n_ch]
+    double *xy;               // [n][2]
+};
+
+__device__ __forceinline__ double ls_step(double I, double d, double Sa, double Sb) {
+    const double e = exp(-d);
+    double wa, wb;
+    if (d < 1e-3) {
+        wb = d * (0.5 - d * (1.0 / 6.0 - d * (1.0 / 24.0 - d / 120.0)));
+        wa = d * (0.5 - d * (1.0 / 3.0 - d * (1.0 / 8.0 - d / 30.0)));
+    } else {
+        const double alpha = -expm1(-d) / d;
+        wb = 1.0 - alpha;
+        wa = alpha - e;
+    }
+    return e * I + wa * Sa + wb * Sb;
+}
+
+__global__ void k_image64(ImageArgs a) {
+    extern __shared__ double smem[];
+    const SolveArgs &sa = a.s;
+    const int kmax = sa.kmax;
+    PairSmem64 S;
+    S.ds = smem;
+    S.v = S.ds + kmax;
+    S.ib = S.v + kmax;
+    S.w = S.ib + kmax;
+    S.ca = reinterpret_cast<int32_t *>(S.w + kmax);
+    S.cb = S.ca + kmax;
+    const int64_t o = blockIdx.x;
+    const double *xo = a.pos + 3 * o, *vo = a.vel + 3 * o;
+    if (threadIdx.x == 0) {
+        a.xy[2 * o] = xo[0] * a.e1[0] + xo[1] * a.e1[1] + xo[2] * a.e1[2];
+        a.xy[2 * o + 1] = xo[0] * a.e2[0] + xo[1] * a.e2[1] + xo[2] * a.e2[2];
+    }
+    const double nvo = a.n0 * vo[0] + a.n1 * vo[1] + a.n2 * vo[2];
+    const int64_t ofb = sa.ray_off[o * sa.R + a.rb], ofl = sa.ray_off[o * sa.R + a.rf];
+    const int lb = (int)(sa.ray_off[o * sa.R + a.rb + 1] - ofb);
+    const int lf = (int)(sa.ray_off[o * sa.R + a.rf + 1] - ofl);
+    const int Kb = lb ? sa.xcum[ofb + lb - 1] : 0;
+    const int Kf = lf ? sa.xcum[ofl + lf - 1] : 0;
+    const int K = Kb + 1 + Kf;
+    if (K > kmax) {
+        if (threadIdx.x == 0) atomicOr(sa.err, 2);
+        return;
+    }
+    stage_half64(sa, o, a.rb, Kb - 1, -1, S);
+    stage_half64(sa, o, a.rf, Kb + 1, +1, S);
+    if (threadIdx.x == 0) {
+        S.v[Kb] = 0.0;
+        S.ib[Kb] = 1.0 / sa.b[o];
+        S.w[Kb] = 0.0;
+        S.ca[Kb] = (int32_t)o;
+        S.cb[Kb] = (int32_t)o;
+    }
+    __syncthreads();
+    constexpr double kCsp = kC / kSqrtPi;
+    for (int c = threadIdx.x; c < a.n_ch; c += blockDim.x) {
+        const double u = a.u[c];
+        const double k1 = 1.0 + u / kC;
+        double I = 0.0, chi_prev = 0.0, S_prev = 0.0;
+        for (int k = 0; k < K; k++) {
+            const double w = nvo + (k < Kb ? -S.v[k] : S.v[k]);
+            const double ibk = S.ib[k], wt = S.w[k];
+            const double *pa = sa.line + (int64_t)S.ca[k] * 2 * sa.L, *pb = sa.line + (int64_t)S.cb[k] * 2 * sa.L;
+            const double base = u - w * k1;
+            double eta = 0.0, chi = 0.0;
+            for (int i = 0; i < a.n_ov; i++) {
+                const Overlap ov = a.ov[i];
+                const double x = (ov.dnl + ov.rat * base) * ibk;
+                const double x2 = x * x;
+                if (x2 > 746.0) continue;   // exp(-x^2) is zero in FP64
+                const double phi = exp(-x2) * (ov.inv_nu2 * ibk) * kCsp;
+                eta += ((1.0 - wt) * pa[2 * ov.l2] + wt * pb[2 * ov.l2]) * phi;
+                chi += ((1.0 - wt) * pa[2 * ov.l2 + 1] + wt * pb[2 * ov.l2 + 1]) * phi;
+            }
+            chi = fmax(chi, sa.chi_min);
+            const double Sk = eta / chi;
+            if (k == 0) {
+                I = planck_d(a.nu_l * k1 * (1.0 - w / kC), sa.T_cmb);
+            } else {
+                const double dt = fmax(0.5 * (chi_prev + chi) * S.ds[k - 1], sa.dtau_min);
+                I = ls_step(I, dt, S_prev, Sk);
+            }
+            chi_prev = chi;
+            S_prev = Sk;
+        }
+        a.I[o * a.n_ch + c] = I;
+    }
+}
+
 }  // namespace
 
 int mg_launch_line_data(mg_ctx *ctx) {
@@ -330,6 +445,63 @@ static int launch_fp64(mg_ctx *ctx, const int32_t *olist, const int32_t *ocount,
     {
         MgTimed t(ctx, olist ? "feautrier_fp64_promoted" : "feautrier_fp64");
         k_feautrier64<<<grid, threads, smem, ctx->stream>>>(a);
+    }
+    MG_CUDA(cudaGetLastError());
+    return MG_OK;
+}
+
+// FP64 line data from the current populations (the images need it in either precision).
+int mg_launch_line_data64(mg_ctx *ctx, unsigned long long *neg) {
+    const int64_t m = ctx->n * ctx->n_lines;
+    k_line_data<<<(unsigned)((m + 255) / 256), 256, 0, ctx->stream>>>(
+        ctx->n, ctx->n_lines, ctx->n_lev, ctx->d_pops, ctx->d_lines, ctx->d_line, nullptr, neg);
+    MG_CUDA(cudaGetLastError());
+    return MG_OK;
+}
+
+int mg_launch_image(mg_ctx *ctx, int ray, int line, int n_ch, const double *d_u, const Overlap *d_ov, int n_ov,
+                    double *d_I, double *d_xy) {
+    ImageArgs a{};
+    SolveArgs &s = a.s;
+    s.n = ctx->n; s.R = ctx->R; s.P = ctx->P; s.L = ctx->n_lines; s.Q = ctx->Q;
+    s.ray_off = ctx->d_ray_off; s.cells = ctx->d_cells; s.xcum = ctx->d_xcum;
+    s.ds = ctx->d_ds; s.vpar = ctx->d_vpar; s.b = ctx->d_b; s.line = ctx->d_line; s.lc = ctx->d_lines;
+    s.chi_min = ctx->opt.chi_min; s.dtau_min = ctx->opt.dtau_min; s.T_cmb = ctx->opt.T_cmb;
+    s.kmax = (int32_t)ctx->max_pair_len;
+    s.err = ctx->d_err;
+    a.rf = ray;
+    a.rb = ctx->h_anti[ray];
+    a.n_ch = n_ch;
+    a.n_ov = n_ov;
+    a.u = d_u;
+    a.ov = d_ov;
+    a.vel = ctx->d_vel;
+    a.pos = ctx->d_pos;
+    const double *n = &ctx->h_dirs[3 * (size_t)ray];
+    a.n0 = n[0]; a.n1 = n[1]; a.n2 = n[2];
+    // e1 = (z x n)/|z x n| (x in place of z when |n_z| >= 0.9), e2 = n x e1
+    double ax[3] = {0.0, 0.0, 1.0};
+    if (std::fabs(n[2]) >= 0.9) { ax[0] = 1.0; ax[2] = 0.0; }
+    double e1[3] = {ax[1] * n[2] - ax[2] * n[1], ax[2] * n[0] - ax[0] * n[2], ax[0] * n[1] - ax[1] * n[0]};
+    const double l1 = std::sqrt(e1[0] * e1[0] + e1[1] * e1[1] + e1[2] * e1[2]);
+    for (double &v : e1) v /= l1;
+    a.e1[0] = e1[0]; a.e1[1] = e1[1]; a.e1[2] = e1[2];
+    a.e2[0] = n[1] * e1[2] - n[2] * e1[1];
+    a.e2[1] = n[2] * e1[0] - n[0] * e1[2];
+    a.e2[2] = n[0] * e1[1] - n[1] * e1[0];
+    a.nu_l = ctx->h_lines[line].nu;
+    a.I = d_I;
+    a.xy = d_xy;
+    const size_t smem = sizeof(double) * (size_t)s.kmax * 4 + sizeof(int32_t) * 2 * (size_t)s.kmax;
+    if (smem > 227 * 1024)
+        return mg_fail(ctx, MG_ERR_CAPACITY, "mg_image: longest ray pair does not fit in shared memory");
+    MG_CUDA(cudaFuncSetAttribute(k_image64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int threads = ((n_ch + 31) / 32) * 32;
+    if (threads > 256) threads = 256;
+    MG_CUDA(cudaMemsetAsync(ctx->d_err, 0, 4, ctx->stream));
+    {
+        MgTimed t(ctx, "image_fp64");
+        k_image64<<<(unsigned)ctx->n, threads, smem, ctx->stream>>>(a);
     }
     MG_CUDA(cudaGetLastError());
     return MG_OK;

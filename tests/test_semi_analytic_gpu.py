@@ -60,9 +60,9 @@ def test_hubble_3d_paper_size(precision):
     assert np.max(rel_err(Jnu[origins], Jo[:, 0, :])) < (TOL64 if precision == 0 else TOL_MIX)
     line = an.lte_line(m, o.width(0))
     e = np.concatenate([
-        rel_err(Jnu[s:s + 2000], an.hubble_J(m.pos[s:s + 2000], o.dirs, m.meta["R"], m.meta["c_dbeta"],
+        rel_err(Jnu[s:s + 1000], an.hubble_J(m.pos[s:s + 1000], o.dirs, m.meta["R"], m.meta["c_dbeta"],
                                              o.roots, line, float(m.n_spec[0])))
-        for s in range(0, m.n, 2000)])
+        for s in range(0, m.n, 1000)])
     interior = m.is_bdy == 0
     assert np.quantile(e[interior], 0.99) < 1e-4
     assert np.median(e) < 1e-5
