@@ -169,6 +169,26 @@ def time_oracle(model, target_s=15.0, seed=0):
     return solves / dt, threads, f"{k} of {model.n} origin points ({solves} solves, {dt:.1f} s)"
 
 
+def time_oracle_one_thread(model, target_s=5.0, seed=1):
+    """The same oracle timing on one host thread (a smaller sample)."""
+    from oracle import Oracle
+    o = Oracle(model, nthreads=1)
+    pops = o.lte()
+    rng = np.random.default_rng(seed)
+    P = o.dirs.shape[0] // 2
+    F = model.species.n_lines * o.Q
+    k = 2
+    while True:
+        origins = np.sort(rng.choice(model.n, k, replace=False))
+        t0 = time.perf_counter()
+        o.formal_solve(pops, origins)
+        dt = time.perf_counter() - t0
+        if dt > target_s / 4 or k >= model.n:
+            break
+        k = min(model.n, int(k * max(2.0, target_s / 4 / max(dt, 1e-3))))
+    return k * P * F / dt, f"{k} origin points, 1 thread, {dt:.1f} s"
+
+
 # ------------------------------------------------------------------ GPU arm
 def run_gpu(args):
     import torch
@@ -270,6 +290,7 @@ def run_gpu(args):
                 "hbm_algorithmic_GBps": round(st["n_elements"] * 16 / (k_avg * 1e-3) / 1e9, 2),
                 "hbm_algorithmic_frac_of_measured": round(st["n_elements"] * 16 / (k_avg * 1e-3) / 1e9 / pk["hbm_gbs"], 5)}
         cpu_v, cores, sample = time_oracle(model) if args.cpu_baseline else (None, None, None)
+        cpu_1 = time_oracle_one_thread(model) if args.cpu_baseline else None
         value = whole_job_rate(solves, args.steps, ws, ms_max)
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -287,7 +308,9 @@ def run_gpu(args):
             "clocks": clk,
             "roofline": roof,
             "cpu_baseline": None if cpu_v is None else {"value": cpu_v, "unit": UNIT, "cores": cores,
-                                                        "kind": "oracle", "sample": sample},
+                                                        "kind": "oracle", "sample": sample,
+                                                        "single_thread": {"value": cpu_1[0], "unit": UNIT,
+                                                                          "sample": cpu_1[1]}},
             "peaks_source": pk_kind,
         }
         print(json.dumps(line))
@@ -464,8 +487,9 @@ def run_disc(args):
 
 
 def run_image(args):
-    """Images of the Keplerian disc (Sec. 3.5): one FP64 image per step of the lowest
-    line along one ray direction, 63 channels over +-15 km/s, every point a pixel.
+    """Images of the Keplerian disc (Sec. 3.5): one image per step of the lowest line
+    along one ray direction, 63 channels over +-15 km/s, every point a pixel; FP32 in a
+    mixed-precision context, and FP64 in an FP64 context.
     value: pixel-channel intensities per second from the image kernel's CUDA-event time;
     e2e: the same through mg_image with the image copied back to host memory every step.
     The algorithmic work (points of the pairs along that direction x channels) is
@@ -475,51 +499,60 @@ def run_image(args):
     import paper_1912_08445_gb300 as mg
     import synthetic as syn
     m = syn.model_disc(n=args.disc_points, seed=0)
-    ctx = mg.Context(precision=mg.MG_MIXED, profile=1)
-    ctx.load_model(m)
-    ctx.trace_rays()
-    ctx.init_populations()
     ray, n_ch = 40, 63
     u = np.linspace(-15e3, 15e3, n_ch)
-    anti = ctx.get_directions()[1][ray]
-    rng = np.random.default_rng(0)
-    samp = rng.choice(m.n, min(4000, m.n), replace=False)
-    def half_points(o, r):
-        g = ctx.get_ray(int(o), r, cap=8192)
-        return len(g["cells"]) + int(g["nsub"].sum())
-    plen = [1 + half_points(o, ray) + half_points(o, anti) for o in samp]
-    mean_K = float(np.mean(plen))
-    dI = torch.empty((m.n, n_ch), dtype=torch.float64, device="cuda")
-    for _ in range(args.warmup):
-        ctx.image_dev(ray, 0, u, dI.data_ptr())
-    ctx.reset_kernel_times()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        ctx.image_dev(ray, 0, u, dI.data_ptr())
-    torch.cuda.synchronize()
-    wall_dev = (time.perf_counter() - t0) / args.steps
-    kt = ctx.kernel_times()
-    k_ms, k_n = kt["image_fp64"]
-    kernel_s = k_ms / k_n / 1e3
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        I, xy = ctx.image(ray, 0, u)
-    e2e_s = (time.perf_counter() - t0) / args.steps
     pix = m.n * n_ch
-    updates = mean_K * pix
-    # FP64 bound per point-channel update at the measured pipe rates of this GPU: three
-    # exponentials (profile, exp(-dtau), expm1), two divisions, ~30 DFMA-pipe operations
-    bound_s = updates * (3 / 31e9 + 2 / 66e9 + 30 / 0.50e12)
-    print(json.dumps({"metric": "image pixel-channel intensities/s", "unit": "intensities/s",
-                      "workload": f"Keplerian disc, {m.n} points, image along ray {ray} of 192, line 0, "
-                                  f"{n_ch} channels over +-15 km/s, FP64",
-                      "value": pix / kernel_s, "ms_per_image": kernel_s * 1e3, "wall_ms_per_image": wall_dev * 1e3,
-                      "e2e": {"value": pix / e2e_s, "unit": "intensities/s", "ms_per_image": e2e_s * 1e3,
-                              "d2h_bytes_per_step": int(pix * 8 + m.n * 16)},
-                      "mean_pair_points": mean_K, "cell_channel_updates_per_s": updates / kernel_s,
-                      "fp64_bound_ms": bound_s * 1e3, "fraction_of_fp64_bound": bound_s / kernel_s,
-                      "max_I": float(I.max()), "min_I": float(I.min())}))
+    imgs = {}
+    out = {"metric": "image pixel-channel intensities/s", "unit": "intensities/s",
+           "workload": f"Keplerian disc, {m.n} points, image along ray {ray} of 192, line 0, "
+                       f"{n_ch} channels over +-15 km/s"}
+    for prec, kname in ((mg.MG_MIXED, "image_fp32"), (mg.MG_FP64, "image_fp64")):
+        ctx = mg.Context(precision=prec, profile=1)
+        ctx.load_model(m)
+        ctx.trace_rays()
+        ctx.init_populations()
+        if "mean_pair_points" not in out:
+            anti = ctx.get_directions()[1][ray]
+            samp = np.random.default_rng(0).choice(m.n, min(4000, m.n), replace=False)
+
+            def half_points(o, r):
+                g = ctx.get_ray(int(o), r, cap=8192)
+                return len(g["cells"]) + int(g["nsub"].sum())
+            out["mean_pair_points"] = float(np.mean([1 + half_points(o, ray) + half_points(o, anti) for o in samp]))
+        updates = out["mean_pair_points"] * pix
+        dI = torch.empty((m.n, n_ch), dtype=torch.float64, device="cuda")
+        for _ in range(args.warmup):
+            ctx.image_dev(ray, 0, u, dI.data_ptr())
+        ctx.reset_kernel_times()
+        torch.cuda.synchronize()
+        for _ in range(args.steps):
+            ctx.image_dev(ray, 0, u, dI.data_ptr())
+        torch.cuda.synchronize()
+        k_ms, k_n = ctx.kernel_times()[kname]
+        kernel_s = k_ms / k_n / 1e3
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            I, xy = ctx.image(ray, 0, u)
+        e2e_s = (time.perf_counter() - t0) / args.steps
+        rec = {"value": pix / kernel_s, "ms_per_image": kernel_s * 1e3,
+               "e2e": {"value": pix / e2e_s, "unit": "intensities/s", "ms_per_image": e2e_s * 1e3,
+                       "d2h_bytes_per_step": int(pix * 8 + m.n * 16)},
+               "cell_channel_updates_per_s": updates / kernel_s, "max_I": float(I.max()), "min_I": float(I.min())}
+        imgs[prec] = I
+        if prec == mg.MG_FP64:
+            # FP64 bound per point-channel update at the measured pipe rates of this GPU: three
+            # exponentials (profile, exp(-dtau), expm1), two divisions, ~30 DFMA-pipe operations
+            bound_s = updates * (3 / 31e9 + 2 / 66e9 + 30 / 0.50e12)
+            rec.update(fp64_bound_ms=bound_s * 1e3, fraction_of_fp64_bound=bound_s / kernel_s)
+            out["fp64"] = rec
+        else:
+            out["fp32"] = rec
+            out["value"] = rec["value"]
+        ctx.close()
+        del dI
+    a, b = imgs[mg.MG_MIXED], imgs[mg.MG_FP64]
+    out["fp32_vs_fp64_max_rel_diff"] = float(np.max(2 * np.abs(a - b) / (np.abs(a) + np.abs(b))))
+    print(json.dumps(out))
 
 
 def run_learned(args):

@@ -199,7 +199,9 @@ int mg_get_spectrum(const mg_ctx *ctx, double *Jnu);
  * the far end of the n half with the first-order equation dI/dtau = S - I, the source
  * linear in tau between points (Olson & Kunasz 1987). At a point of velocity v the
  * comoving frequency is nu (1 - n.v/c). All lines whose profiles reach the channels add
- * to opacity and emissivity. FP64 in both precisions, from the current populations.
+ * to opacity and emissivity, from the current populations. An FP64 context computes
+ * in FP64; a mixed-precision context in FP32 (FP64 when more than 4 lines reach the
+ * channels or the FP32 staging does not fit in shared memory).
  * Requires traced rays and populations (MG_ERR_STATE otherwise); 1 <= n_ch <=
  * MG_IMAGE_MAX_CHANNELS (MG_ERR_ARG otherwise). Synchronises the context's stream. */
 #define MG_IMAGE_MAX_CHANNELS 4096

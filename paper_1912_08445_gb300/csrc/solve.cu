@@ -377,6 +377,142 @@ __global__ void k_image64(ImageArgs a) {
     }
 }
 
+// FP32 image of a mixed-precision context. The pair is staged once per point in shared
+// memory as FP32: path length, rest-frame line-of-sight velocity w, reciprocal width,
+// and the interpolated (eta, chi) of every line within reach (at most kImgLines); then
+// each thread carries one channel through the pair. The linear-source weights use their
+// Taylor series below dtau = 0.05 (4 terms: relative error below 2e-8 there), where
+// 1 - alpha would cancel in FP32.
+constexpr int kImgLines = 4;
+
+struct ImgSmem32 {
+    float *ds, *w, *ib, *lin;   // lin: [K][n_ov][2] (eta, chi)
+};
+
+__device__ void stage_half_img32(const ImageArgs &a, int64_t o, int r, int base, int dir, float nvo, float sgn,
+                                 const ImgSmem32 &S) {
+    const SolveArgs &sa = a.s;
+    const int64_t off = sa.ray_off[o * sa.R + r];
+    const int len = (int)(sa.ray_off[o * sa.R + r + 1] - off);
+    for (int e = threadIdx.x; e < len; e += blockDim.x) {
+        const int32_t c = sa.cells[off + e];
+        const int32_t prev = e ? sa.cells[off + e - 1] : (int32_t)o;
+        const int x0 = e ? sa.xcum[off + e - 1] : 0;
+        const int ns = sa.xcum[off + e] - x0 - 1;
+        const double pv = e ? sa.vpar[off + e - 1] : 0.0;
+        const double ve = sa.vpar[off + e], dse = sa.ds[off + e];
+        const double bp = sa.b[prev], bc = sa.b[c];
+        const double *pa = sa.line + (int64_t)prev * 2 * sa.L, *pb = sa.line + (int64_t)c * 2 * sa.L;
+        for (int j = 1; j <= ns + 1; j++) {
+            const double wt = (double)j / (double)(ns + 1);
+            const int idx = base + dir * (x0 + j - 1);
+            S.ds[dir < 0 ? idx : idx - 1] = (float)(dse / (double)(ns + 1));
+            S.w[idx] = nvo + sgn * (float)((1.0 - wt) * pv + wt * ve);
+            S.ib[idx] = (float)(1.0 / ((1.0 - wt) * bp + wt * bc));
+            for (int i = 0; i < a.n_ov; i++) {
+                const int l2 = a.ov[i].l2;
+                S.lin[(idx * a.n_ov + i) * 2] = (float)((1.0 - wt) * pa[2 * l2] + wt * pb[2 * l2]);
+                S.lin[(idx * a.n_ov + i) * 2 + 1] = (float)((1.0 - wt) * pa[2 * l2 + 1] + wt * pb[2 * l2 + 1]);
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ float ls_step32(float I, float d, float Sa, float Sb) {
+    const float e = __expf(-d);
+    float wa, wb;
+    if (d < 0.05f) {
+        wb = d * (0.5f - d * (1.0f / 6.0f - d * (1.0f / 24.0f - d * (1.0f / 120.0f))));
+        wa = d * (0.5f - d * (1.0f / 3.0f - d * (1.0f / 8.0f - d * (1.0f / 30.0f))));
+    } else {
+        const float alpha = (1.0f - e) / d;
+        wb = 1.0f - alpha;
+        wa = alpha - e;
+    }
+    return e * I + wa * Sa + wb * Sb;
+}
+
+__global__ void k_image32(ImageArgs a) {
+    extern __shared__ float smf[];
+    const SolveArgs &sa = a.s;
+    const int kmax = sa.kmax;
+    ImgSmem32 S;
+    S.ds = smf;
+    S.w = S.ds + kmax;
+    S.ib = S.w + kmax;
+    S.lin = S.ib + kmax;
+    const int64_t o = blockIdx.x;
+    const double *xo = a.pos + 3 * o, *vo = a.vel + 3 * o;
+    if (threadIdx.x == 0) {
+        a.xy[2 * o] = xo[0] * a.e1[0] + xo[1] * a.e1[1] + xo[2] * a.e1[2];
+        a.xy[2 * o + 1] = xo[0] * a.e2[0] + xo[1] * a.e2[1] + xo[2] * a.e2[2];
+    }
+    const double nvo_d = a.n0 * vo[0] + a.n1 * vo[1] + a.n2 * vo[2];
+    const float nvo = (float)nvo_d;
+    const int64_t ofb = sa.ray_off[o * sa.R + a.rb], ofl = sa.ray_off[o * sa.R + a.rf];
+    const int lb = (int)(sa.ray_off[o * sa.R + a.rb + 1] - ofb);
+    const int lf = (int)(sa.ray_off[o * sa.R + a.rf + 1] - ofl);
+    const int Kb = lb ? sa.xcum[ofb + lb - 1] : 0;
+    const int Kf = lf ? sa.xcum[ofl + lf - 1] : 0;
+    const int K = Kb + 1 + Kf;
+    if (K > kmax) {
+        if (threadIdx.x == 0) atomicOr(sa.err, 2);
+        return;
+    }
+    stage_half_img32(a, o, a.rb, Kb - 1, -1, nvo, -1.0f, S);
+    stage_half_img32(a, o, a.rf, Kb + 1, +1, nvo, +1.0f, S);
+    if (threadIdx.x == 0) {
+        S.w[Kb] = nvo;
+        S.ib[Kb] = (float)(1.0 / sa.b[o]);
+        const double *pl = sa.line + o * 2 * sa.L;
+        for (int i = 0; i < a.n_ov; i++) {
+            S.lin[(Kb * a.n_ov + i) * 2] = (float)pl[2 * a.ov[i].l2];
+            S.lin[(Kb * a.n_ov + i) * 2 + 1] = (float)pl[2 * a.ov[i].l2 + 1];
+        }
+    }
+    __syncthreads();
+    constexpr float kCspf = (float)(kC / kSqrtPi);
+    float dnl[kImgLines], rat[kImgLines], nrm[kImgLines];
+    for (int i = 0; i < kImgLines; i++) {
+        const bool on = i < a.n_ov;
+        dnl[i] = on ? (float)a.ov[i].dnl : 0.0f;
+        rat[i] = on ? (float)a.ov[i].rat : 0.0f;
+        nrm[i] = on ? (float)(a.ov[i].inv_nu2 * (double)kCspf) : 0.0f;
+    }
+    const float chi_min = (float)sa.chi_min, dtau_min = (float)sa.dtau_min;
+    for (int c = threadIdx.x; c < a.n_ch; c += blockDim.x) {
+        const double u_d = a.u[c];
+        const float u = (float)u_d;
+        const float k1 = (float)(1.0 + u_d / kC);
+        float I = 0.0f, chi_prev = 0.0f, S_prev = 0.0f;
+        for (int k = 0; k < K; k++) {
+            const float w = S.w[k], ibk = S.ib[k];
+            const float base = u - w * k1;
+            float eta = 0.0f, chi = 0.0f;
+#pragma unroll
+            for (int i = 0; i < kImgLines; i++) {
+                if (i < a.n_ov) {
+                    const float x = (dnl[i] + rat[i] * base) * ibk;
+                    const float phi = __expf(-x * x) * (nrm[i] * ibk);
+                    eta += S.lin[(k * a.n_ov + i) * 2] * phi;
+                    chi += S.lin[(k * a.n_ov + i) * 2 + 1] * phi;
+                }
+            }
+            chi = fmaxf(chi, chi_min);
+            const float Sk = eta / chi;
+            if (k == 0) {
+                I = (float)planck_d(a.nu_l * (1.0 + u_d / kC) * (1.0 - (double)w / kC), sa.T_cmb);
+            } else {
+                const float dt = fmaxf(0.5f * (chi_prev + chi) * S.ds[k - 1], dtau_min);
+                I = ls_step32(I, dt, S_prev, Sk);
+            }
+            chi_prev = chi;
+            S_prev = Sk;
+        }
+        a.I[o * a.n_ch + c] = (double)I;
+    }
+}
+
 }  // namespace
 
 int mg_launch_line_data(mg_ctx *ctx) {
@@ -492,14 +628,20 @@ int mg_launch_image(mg_ctx *ctx, int ray, int line, int n_ch, const double *d_u,
     a.nu_l = ctx->h_lines[line].nu;
     a.I = d_I;
     a.xy = d_xy;
-    const size_t smem = sizeof(double) * (size_t)s.kmax * 4 + sizeof(int32_t) * 2 * (size_t)s.kmax;
-    if (smem > 227 * 1024)
-        return mg_fail(ctx, MG_ERR_CAPACITY, "mg_image: longest ray pair does not fit in shared memory");
-    MG_CUDA(cudaFuncSetAttribute(k_image64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int threads = ((n_ch + 31) / 32) * 32;
     if (threads > 256) threads = 256;
     MG_CUDA(cudaMemsetAsync(ctx->d_err, 0, 4, ctx->stream));
-    {
+    // FP32 in a mixed-precision context when the lines within reach fit the staging
+    const size_t smem32 = sizeof(float) * (size_t)s.kmax * (3 + 2 * (size_t)n_ov);
+    if (ctx->opt.precision == MG_MIXED && n_ov <= kImgLines && smem32 <= 227 * 1024) {
+        MG_CUDA(cudaFuncSetAttribute(k_image32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem32));
+        MgTimed t(ctx, "image_fp32");
+        k_image32<<<(unsigned)ctx->n, threads, smem32, ctx->stream>>>(a);
+    } else {
+        const size_t smem = sizeof(double) * (size_t)s.kmax * 4 + sizeof(int32_t) * 2 * (size_t)s.kmax;
+        if (smem > 227 * 1024)
+            return mg_fail(ctx, MG_ERR_CAPACITY, "mg_image: longest ray pair does not fit in shared memory");
+        MG_CUDA(cudaFuncSetAttribute(k_image64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         MgTimed t(ctx, "image_fp64");
         k_image64<<<(unsigned)ctx->n, threads, smem, ctx->stream>>>(a);
     }

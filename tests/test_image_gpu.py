@@ -1,6 +1,6 @@
 """Images (Sec. 3.5, 'Imaging the model') through the CUDA library against the oracle:
-intensity per point and channel within 1e-10 relative, sky-plane coordinates within
-1e-12, in FP64 and mixed-precision contexts (the image kernel is FP64 in both)."""
+intensity per point and channel within 1e-10 relative in FP64 contexts and 1e-4 in
+mixed-precision contexts (FP32 image kernel), sky-plane coordinates within 1e-12."""
 import numpy as np
 import pytest
 
@@ -12,6 +12,7 @@ from paper_1912_08445_gb300.binding import MG_ERR_ARG, MG_ERR_STATE
 
 pytestmark = pytest.mark.gpu
 TOL = 1e-10
+TOL_MIX = 1e-4
 
 
 def _lattice_flow():
@@ -31,7 +32,7 @@ CASES = {
 }
 
 
-def _compare(m, o, ctx, rays, origins, pops=None, n_ch=41):
+def _compare(m, o, ctx, rays, origins, pops=None, n_ch=41, tol=TOL):
     pops = o.lte() if pops is None else pops
     for r in rays:
         for line in range(m.species.n_lines):
@@ -40,7 +41,7 @@ def _compare(m, o, ctx, rays, origins, pops=None, n_ch=41):
             I, xy = ctx.image(r, line, u)
             Io, xyo = o.image(pops, r, line, u, origins=origins)
             sel = slice(None) if origins is None else origins
-            assert np.max(rel_err(I[sel], Io)) < TOL, (r, line)
+            assert np.max(rel_err(I[sel], Io)) < tol, (r, line)
             scale = np.abs(m.pos).max()
             assert np.max(np.abs(xy[sel] - xyo)) <= 1e-12 * scale
             if line >= 1:
@@ -57,7 +58,7 @@ def test_image_matches_oracle(name, precision):
     ctx.trace_rays()
     ctx.init_populations()
     origins = None if n_orig is None else np.sort(np.random.default_rng(2).choice(m.n, n_orig, replace=False))
-    _compare(m, o, ctx, rays, origins)
+    _compare(m, o, ctx, rays, origins, tol=TOL if precision == 0 else TOL_MIX)
 
 
 def test_image_uses_current_populations():
@@ -70,19 +71,20 @@ def test_image_uses_current_populations():
     ctx.iterate(allow_not_converged=True)
     pops = ctx.get_populations()
     origins = np.sort(np.random.default_rng(4).choice(m.n, 100, replace=False))
-    _compare(m, o, ctx, [7], origins, pops=pops)
+    _compare(m, o, ctx, [7], origins, pops=pops, tol=TOL_MIX)
     u = np.linspace(-10, 10, 41) * o.width(0)
     I_lte, _ = o.image(o.lte(), 7, 0, u, origins=origins)
     I, _ = ctx.image(7, 0, u)
     assert np.max(rel_err(I[origins], I_lte)) > 1e-3
 
 
-def test_image_disc_200k_sampled():
+@pytest.mark.parametrize("precision", [0, 1])
+def test_image_disc_200k_sampled(precision):
     """Full-size Keplerian disc (200k points, 192 rays, 20-level rotor): one image of the
     lowest line with 63 channels, checked against the oracle on 60 sampled points."""
     m = syn.model_disc()
     o = Oracle(m, nthreads=16)
-    ctx = gpu_context(m, precision=1)
+    ctx = gpu_context(m, precision=precision, profile=1)
     ctx.trace_rays()
     ctx.init_populations()
     origins = np.sort(np.random.default_rng(5).choice(m.n, 60, replace=False))
@@ -90,8 +92,9 @@ def test_image_disc_200k_sampled():
     ray = 40
     I, xy = ctx.image(ray, 0, u)
     Io, xyo = o.image(o.lte(), ray, 0, u, origins=origins)
-    assert np.max(rel_err(I[origins], Io)) < TOL
+    assert np.max(rel_err(I[origins], Io)) < (TOL if precision == 0 else TOL_MIX)
     assert np.all(np.isfinite(I)) and np.all(I > 0)
+    assert ("image_fp64" if precision == 0 else "image_fp32") in ctx.kernel_times()
 
 
 def test_image_dev_equals_host():
