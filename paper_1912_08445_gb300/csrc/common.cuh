@@ -144,6 +144,7 @@ struct mg_ctx {
     // ---- images: channel offsets, candidate lines, output buffers (grow-only)
     double *d_uch = nullptr, *d_img = nullptr, *d_imgxy = nullptr;
     mg::Overlap *d_imgov = nullptr;
+    float *d_imglf = nullptr;      // [n][L][2] FP32 (eta_int, chi_int) for the FP32 image kernel
     int64_t img_cap = 0;
     int32_t uch_cap = 0;
 
@@ -193,7 +194,7 @@ struct MgTimed {
 int mg_launch_trace(mg_ctx *ctx);
 int mg_launch_line_data(mg_ctx *ctx);
 int mg_launch_line_data_mixed(mg_ctx *ctx);
-int mg_launch_line_data64(mg_ctx *ctx, unsigned long long *neg);
+int mg_launch_line_data64(mg_ctx *ctx, float *linef, unsigned long long *neg);
 int mg_launch_image(mg_ctx *ctx, int ray, int line, int n_ch, const double *d_u, const mg::Overlap *d_ov,
                     int n_ov, double *d_I, double *d_xy);
 int mg_launch_feautrier(mg_ctx *ctx);

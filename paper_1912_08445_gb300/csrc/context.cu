@@ -119,7 +119,7 @@ extern "C" int mg_destroy(mg_ctx *ctx) {
     mg_free(ctx->d_line); mg_free(ctx->d_linef); mg_free(ctx->d_J); mg_free(ctx->d_L);
     mg_free(ctx->d_Jeff); mg_free(ctx->d_Lc); mg_free(ctx->d_Jnu); mg_free(ctx->d_scal);
     mg_free(ctx->d_err);
-    mg_free(ctx->d_uch); mg_free(ctx->d_img); mg_free(ctx->d_imgxy); mg_free(ctx->d_imgov);
+    mg_free(ctx->d_uch); mg_free(ctx->d_img); mg_free(ctx->d_imgxy); mg_free(ctx->d_imgov); mg_free(ctx->d_imglf);
     if (ctx->h_scal) cudaFreeHost(ctx->h_scal);
     if (ctx->ev0) cudaEventDestroy(ctx->ev0);
     if (ctx->ev1) cudaEventDestroy(ctx->ev1);
@@ -757,9 +757,10 @@ static int image_common(mg_ctx *ctx, int32_t ray, int32_t line, int32_t n_ch, co
     }
     if (!ctx->d_imgov && (rc = mg_alloc(ctx, &ctx->d_imgov, ctx->n_lines))) return rc;
     if (!ctx->d_imgxy && (rc = mg_alloc(ctx, &ctx->d_imgxy, 2 * ctx->n))) return rc;
+    if (!ctx->d_imglf && (rc = mg_alloc(ctx, &ctx->d_imglf, 2 * ctx->n * ctx->n_lines))) return rc;
     MG_CUDA(cudaMemcpyAsync(ctx->d_uch, u_ch, 8 * (size_t)n_ch, cudaMemcpyHostToDevice, ctx->stream));
     MG_CUDA(cudaMemcpyAsync(ctx->d_imgov, ov.data(), sizeof(Overlap) * ov.size(), cudaMemcpyHostToDevice, ctx->stream));
-    if ((rc = mg_launch_line_data64(ctx, ctx->d_scal + 6))) return rc;
+    if ((rc = mg_launch_line_data64(ctx, ctx->d_imglf, ctx->d_scal + 6))) return rc;
     double *d_I = dev ? I : ctx->d_img;
     double *d_xy = dev ? xy : ctx->d_imgxy;
     if (!d_xy) d_xy = ctx->d_imgxy;

@@ -288,6 +288,7 @@ struct ImageArgs {
     double nu_l;              // reference line frequency
     double *I;                // [n][n_ch]
     double *xy;               // [n][2]
+    const float *dsf, *vparf, *bf, *linef;   // FP32 copies for the FP32 kernel
 };
 
 __device__ __forceinline__ double ls_step(double I, double d, double Sa, double Sb) {
@@ -378,41 +379,54 @@ __global__ void k_image64(ImageArgs a) {
 }
 
 // FP32 image of a mixed-precision context. The pair is staged once per point in shared
-// memory as FP32: path length, rest-frame line-of-sight velocity w, reciprocal width,
-// and the interpolated (eta, chi) of every line within reach (at most kImgLines); then
-// each thread carries one channel through the pair. The linear-source weights use their
-// Taylor series below dtau = 0.05 (4 terms: relative error below 2e-8 there), where
-// 1 - alpha would cancel in FP32.
+// memory in FP32 (from the FP32 ray store, widths and line data): path length,
+// rest-frame line-of-sight velocity w, reciprocal width, and the interpolated (eta, chi)
+// of the NOV lines within reach; then each thread carries one channel through the pair.
+// The linear-source weights use their Taylor series below dtau = 0.05 (4 terms: relative
+// error below 2e-8 there), where 1 - alpha would cancel in FP32; divisions are the fast
+// approximate ones (2 ulp).
 constexpr int kImgLines = 4;
 
 struct ImgSmem32 {
-    float *ds, *w, *ib, *lin;   // lin: [K][n_ov][2] (eta, chi)
+    float *ds, *w, *ib, *lin;   // lin: [K][NOV][2] (eta, chi)
 };
 
+template <int NOV>
 __device__ void stage_half_img32(const ImageArgs &a, int64_t o, int r, int base, int dir, float nvo, float sgn,
                                  const ImgSmem32 &S) {
     const SolveArgs &sa = a.s;
     const int64_t off = sa.ray_off[o * sa.R + r];
     const int len = (int)(sa.ray_off[o * sa.R + r + 1] - off);
+    int l2[NOV];
+#pragma unroll
+    for (int i = 0; i < NOV; i++) l2[i] = a.ov[i].l2;
     for (int e = threadIdx.x; e < len; e += blockDim.x) {
         const int32_t c = sa.cells[off + e];
         const int32_t prev = e ? sa.cells[off + e - 1] : (int32_t)o;
         const int x0 = e ? sa.xcum[off + e - 1] : 0;
         const int ns = sa.xcum[off + e] - x0 - 1;
-        const double pv = e ? sa.vpar[off + e - 1] : 0.0;
-        const double ve = sa.vpar[off + e], dse = sa.ds[off + e];
-        const double bp = sa.b[prev], bc = sa.b[c];
-        const double *pa = sa.line + (int64_t)prev * 2 * sa.L, *pb = sa.line + (int64_t)c * 2 * sa.L;
+        const float pv = e ? a.vparf[off + e - 1] : 0.0f;
+        const float ve = a.vparf[off + e];
+        const float inv = 1.0f / (float)(ns + 1);
+        const float dse = a.dsf[off + e] * inv;
+        const float bp = a.bf[prev], bc = a.bf[c];
+        const float *pa = a.linef + (int64_t)prev * 2 * sa.L, *pb = a.linef + (int64_t)c * 2 * sa.L;
+        float la[NOV][2], lb[NOV][2];
+#pragma unroll
+        for (int i = 0; i < NOV; i++) {
+            la[i][0] = pa[2 * l2[i]]; la[i][1] = pa[2 * l2[i] + 1];
+            lb[i][0] = pb[2 * l2[i]]; lb[i][1] = pb[2 * l2[i] + 1];
+        }
         for (int j = 1; j <= ns + 1; j++) {
-            const double wt = (double)j / (double)(ns + 1);
+            const float wt = (float)j * inv;
             const int idx = base + dir * (x0 + j - 1);
-            S.ds[dir < 0 ? idx : idx - 1] = (float)(dse / (double)(ns + 1));
-            S.w[idx] = nvo + sgn * (float)((1.0 - wt) * pv + wt * ve);
-            S.ib[idx] = (float)(1.0 / ((1.0 - wt) * bp + wt * bc));
-            for (int i = 0; i < a.n_ov; i++) {
-                const int l2 = a.ov[i].l2;
-                S.lin[(idx * a.n_ov + i) * 2] = (float)((1.0 - wt) * pa[2 * l2] + wt * pb[2 * l2]);
-                S.lin[(idx * a.n_ov + i) * 2 + 1] = (float)((1.0 - wt) * pa[2 * l2 + 1] + wt * pb[2 * l2 + 1]);
+            S.ds[dir < 0 ? idx : idx - 1] = dse;
+            S.w[idx] = nvo + sgn * ((1.0f - wt) * pv + wt * ve);
+            S.ib[idx] = 1.0f / ((1.0f - wt) * bp + wt * bc);
+#pragma unroll
+            for (int i = 0; i < NOV; i++) {
+                S.lin[(idx * NOV + i) * 2] = (1.0f - wt) * la[i][0] + wt * lb[i][0];
+                S.lin[(idx * NOV + i) * 2 + 1] = (1.0f - wt) * la[i][1] + wt * lb[i][1];
             }
         }
     }
@@ -425,13 +439,21 @@ __device__ __forceinline__ float ls_step32(float I, float d, float Sa, float Sb)
         wb = d * (0.5f - d * (1.0f / 6.0f - d * (1.0f / 24.0f - d * (1.0f / 120.0f))));
         wa = d * (0.5f - d * (1.0f / 3.0f - d * (1.0f / 8.0f - d * (1.0f / 30.0f))));
     } else {
-        const float alpha = (1.0f - e) / d;
+        const float alpha = __fdividef(1.0f - e, d);
         wb = 1.0f - alpha;
         wa = alpha - e;
     }
     return e * I + wa * Sa + wb * Sb;
 }
 
+// B_nu(T) in FP32, ordered so that no intermediate leaves the FP32 range.
+__device__ __forceinline__ float planck_f(float nu, float T) {
+    constexpr float k2h = (float)(2.0 * kH), kic = (float)(1.0 / kC), khk = (float)(kH / kKB);
+    const float nc = nu * kic;
+    return k2h * nc * nc * nu / expm1f(khk * nu / T);
+}
+
+template <int NOV>
 __global__ void k_image32(ImageArgs a) {
     extern __shared__ float smf[];
     const SolveArgs &sa = a.s;
@@ -447,8 +469,7 @@ __global__ void k_image32(ImageArgs a) {
         a.xy[2 * o] = xo[0] * a.e1[0] + xo[1] * a.e1[1] + xo[2] * a.e1[2];
         a.xy[2 * o + 1] = xo[0] * a.e2[0] + xo[1] * a.e2[1] + xo[2] * a.e2[2];
     }
-    const double nvo_d = a.n0 * vo[0] + a.n1 * vo[1] + a.n2 * vo[2];
-    const float nvo = (float)nvo_d;
+    const float nvo = (float)a.n0 * (float)vo[0] + (float)a.n1 * (float)vo[1] + (float)a.n2 * (float)vo[2];
     const int64_t ofb = sa.ray_off[o * sa.R + a.rb], ofl = sa.ray_off[o * sa.R + a.rf];
     const int lb = (int)(sa.ray_off[o * sa.R + a.rb + 1] - ofb);
     const int lf = (int)(sa.ray_off[o * sa.R + a.rf + 1] - ofl);
@@ -459,49 +480,48 @@ __global__ void k_image32(ImageArgs a) {
         if (threadIdx.x == 0) atomicOr(sa.err, 2);
         return;
     }
-    stage_half_img32(a, o, a.rb, Kb - 1, -1, nvo, -1.0f, S);
-    stage_half_img32(a, o, a.rf, Kb + 1, +1, nvo, +1.0f, S);
+    stage_half_img32<NOV>(a, o, a.rb, Kb - 1, -1, nvo, -1.0f, S);
+    stage_half_img32<NOV>(a, o, a.rf, Kb + 1, +1, nvo, +1.0f, S);
     if (threadIdx.x == 0) {
         S.w[Kb] = nvo;
-        S.ib[Kb] = (float)(1.0 / sa.b[o]);
-        const double *pl = sa.line + o * 2 * sa.L;
-        for (int i = 0; i < a.n_ov; i++) {
-            S.lin[(Kb * a.n_ov + i) * 2] = (float)pl[2 * a.ov[i].l2];
-            S.lin[(Kb * a.n_ov + i) * 2 + 1] = (float)pl[2 * a.ov[i].l2 + 1];
+        S.ib[Kb] = 1.0f / a.bf[o];
+        const float *pl = a.linef + o * 2 * sa.L;
+#pragma unroll
+        for (int i = 0; i < NOV; i++) {
+            S.lin[(Kb * NOV + i) * 2] = pl[2 * a.ov[i].l2];
+            S.lin[(Kb * NOV + i) * 2 + 1] = pl[2 * a.ov[i].l2 + 1];
         }
     }
     __syncthreads();
     constexpr float kCspf = (float)(kC / kSqrtPi);
-    float dnl[kImgLines], rat[kImgLines], nrm[kImgLines];
-    for (int i = 0; i < kImgLines; i++) {
-        const bool on = i < a.n_ov;
-        dnl[i] = on ? (float)a.ov[i].dnl : 0.0f;
-        rat[i] = on ? (float)a.ov[i].rat : 0.0f;
-        nrm[i] = on ? (float)(a.ov[i].inv_nu2 * (double)kCspf) : 0.0f;
+    float dnl[NOV], rat[NOV], nrm[NOV];
+#pragma unroll
+    for (int i = 0; i < NOV; i++) {
+        dnl[i] = (float)a.ov[i].dnl;
+        rat[i] = (float)a.ov[i].rat;
+        nrm[i] = (float)a.ov[i].inv_nu2 * kCspf;
     }
-    const float chi_min = (float)sa.chi_min, dtau_min = (float)sa.dtau_min;
+    const float chi_min = (float)sa.chi_min, dtau_min = (float)sa.dtau_min, T_cmb = (float)sa.T_cmb;
+    const float nu_l = (float)a.nu_l, kic = (float)(1.0 / kC);
     for (int c = threadIdx.x; c < a.n_ch; c += blockDim.x) {
-        const double u_d = a.u[c];
-        const float u = (float)u_d;
-        const float k1 = (float)(1.0 + u_d / kC);
+        const float u = (float)a.u[c];
+        const float k1 = 1.0f + u * kic;
         float I = 0.0f, chi_prev = 0.0f, S_prev = 0.0f;
         for (int k = 0; k < K; k++) {
             const float w = S.w[k], ibk = S.ib[k];
             const float base = u - w * k1;
             float eta = 0.0f, chi = 0.0f;
 #pragma unroll
-            for (int i = 0; i < kImgLines; i++) {
-                if (i < a.n_ov) {
-                    const float x = (dnl[i] + rat[i] * base) * ibk;
-                    const float phi = __expf(-x * x) * (nrm[i] * ibk);
-                    eta += S.lin[(k * a.n_ov + i) * 2] * phi;
-                    chi += S.lin[(k * a.n_ov + i) * 2 + 1] * phi;
-                }
+            for (int i = 0; i < NOV; i++) {
+                const float x = (dnl[i] + rat[i] * base) * ibk;
+                const float phi = __expf(-x * x) * (nrm[i] * ibk);
+                eta += S.lin[(k * NOV + i) * 2] * phi;
+                chi += S.lin[(k * NOV + i) * 2 + 1] * phi;
             }
             chi = fmaxf(chi, chi_min);
-            const float Sk = eta / chi;
+            const float Sk = __fdividef(eta, chi);
             if (k == 0) {
-                I = (float)planck_d(a.nu_l * (1.0 + u_d / kC) * (1.0 - (double)w / kC), sa.T_cmb);
+                I = planck_f(nu_l * k1 * (1.0f - w * kic), T_cmb);
             } else {
                 const float dt = fmaxf(0.5f * (chi_prev + chi) * S.ds[k - 1], dtau_min);
                 I = ls_step32(I, dt, S_prev, Sk);
@@ -586,11 +606,12 @@ static int launch_fp64(mg_ctx *ctx, const int32_t *olist, const int32_t *ocount,
     return MG_OK;
 }
 
-// FP64 line data from the current populations (the images need it in either precision).
-int mg_launch_line_data64(mg_ctx *ctx, unsigned long long *neg) {
+// FP64 line data (and its plain FP32 copy when linef is given) from the current
+// populations, for the images in either precision.
+int mg_launch_line_data64(mg_ctx *ctx, float *linef, unsigned long long *neg) {
     const int64_t m = ctx->n * ctx->n_lines;
     k_line_data<<<(unsigned)((m + 255) / 256), 256, 0, ctx->stream>>>(
-        ctx->n, ctx->n_lines, ctx->n_lev, ctx->d_pops, ctx->d_lines, ctx->d_line, nullptr, neg);
+        ctx->n, ctx->n_lines, ctx->n_lev, ctx->d_pops, ctx->d_lines, ctx->d_line, linef, neg);
     MG_CUDA(cudaGetLastError());
     return MG_OK;
 }
@@ -632,11 +653,14 @@ int mg_launch_image(mg_ctx *ctx, int ray, int line, int n_ch, const double *d_u,
     if (threads > 256) threads = 256;
     MG_CUDA(cudaMemsetAsync(ctx->d_err, 0, 4, ctx->stream));
     // FP32 in a mixed-precision context when the lines within reach fit the staging
+    a.dsf = ctx->d_dsf; a.vparf = ctx->d_vparf; a.bf = ctx->d_bf; a.linef = ctx->d_imglf;
     const size_t smem32 = sizeof(float) * (size_t)s.kmax * (3 + 2 * (size_t)n_ov);
-    if (ctx->opt.precision == MG_MIXED && n_ov <= kImgLines && smem32 <= 227 * 1024) {
-        MG_CUDA(cudaFuncSetAttribute(k_image32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem32));
+    if (ctx->opt.precision == MG_MIXED && n_ov <= kImgLines && smem32 <= 227 * 1024 && a.linef) {
+        void (*kern)(ImageArgs) = n_ov == 1 ? k_image32<1> : n_ov == 2 ? k_image32<2> : n_ov == 3 ? k_image32<3>
+                                                                                                  : k_image32<4>;
+        MG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem32));
         MgTimed t(ctx, "image_fp32");
-        k_image32<<<(unsigned)ctx->n, threads, smem32, ctx->stream>>>(a);
+        kern<<<(unsigned)ctx->n, threads, smem32, ctx->stream>>>(a);
     } else {
         const size_t smem = sizeof(double) * (size_t)s.kmax * 4 + sizeof(int32_t) * 2 * (size_t)s.kmax;
         if (smem > 227 * 1024)
