@@ -148,6 +148,48 @@ def test_trace_invariants_random_mesh():
     assert dead < 0.05 * 40 * o.dirs.shape[0]
 
 
+def _walk_exact(m, dirs, o, r):
+    """The neighbour walk of Sec. 3.2 by exhaustive search in exact rational arithmetic:
+    at each step, among all neighbours of the current cell whose projection on the ray
+    exceeds the current one, the one closest to the ray (ties: smaller projection, then
+    smaller index); stop after a boundary cell, or at a cell with no farther neighbour."""
+    from fractions import Fraction as Fr
+    n = [Fr(float(x)) for x in dirs[r]]
+    xo = [Fr(float(x)) for x in m.pos[o]]
+    cur, s_cur, cells = o, Fr(0), []
+    while True:
+        best = None
+        for c in m.nbr_idx[m.nbr_off[cur]:m.nbr_off[cur + 1]]:
+            d = [Fr(float(m.pos[c][i])) - xo[i] for i in range(3)]
+            s = sum(d[i] * n[i] for i in range(3))
+            if not s > s_cur:
+                continue
+            d2 = sum((d[i] - s * n[i]) ** 2 for i in range(3))
+            key = (d2, s, int(c))
+            if best is None or key < best[0]:
+                best = (key, int(c), s)
+        if best is None:
+            return cells, True
+        cells.append(best[1])
+        s_cur, cur = best[2], best[1]
+        if m.is_bdy[cur]:
+            return cells, False
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_trace_brute_force_exact_arithmetic(seed):
+    """On 20-point meshes every half-ray of the oracle equals the exhaustive walk done in
+    exact rational arithmetic, dead ends included."""
+    m = syn.model_tiny_3d(seed=seed, n=20)
+    o = Oracle(m)
+    for p in range(m.n):
+        for r in range(o.dirs.shape[0]):
+            t = o.trace(p, r)
+            cells, dead = _walk_exact(m, o.dirs, p, r)
+            assert t["cells"].tolist() == cells, (p, r)
+            assert t["dead_end"] == dead, (p, r)
+
+
 def test_trace_sphere_chord_length():
     """Spherically symmetric shells: the path length to the boundary along a ray equals
     the paper's l(r, theta) = r cos(theta) + sqrt(R^2 - r^2 sin^2(theta)) (Sec. 4.1.1,
