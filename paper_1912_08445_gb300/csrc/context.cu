@@ -101,6 +101,9 @@ static void drop_state(mg_ctx *ctx) {
     mg_free(ctx->d_J); mg_free(ctx->d_L); mg_free(ctx->d_Jeff); mg_free(ctx->d_Lc); mg_free(ctx->d_Jnu);
     for (auto &h : ctx->d_hist) mg_free(h);
     mg_free(ctx->d_ng_tmp); mg_free(ctx->d_ng_part); mg_free(ctx->d_promo);
+    // image buffers are sized by the point and line counts
+    mg_free(ctx->d_img); mg_free(ctx->d_imgxy); mg_free(ctx->d_imgov); mg_free(ctx->d_imglf);
+    ctx->img_cap = 0;
 }
 
 extern "C" int mg_destroy(mg_ctx *ctx) {

@@ -128,3 +128,23 @@ def test_image_bad_calls():
         assert e.value.code == MG_ERR_ARG
     I, xy = ctx.image(0, 0, u)
     assert np.all(np.isfinite(I))
+
+
+def test_image_after_mesh_change():
+    """A context reloaded with a larger mesh (and another species) images the new model:
+    the image buffers follow the point and line counts."""
+    import paper_1912_08445_gb300 as mgp
+    small = syn.model_clumpy_3d(n=600, seed=8)
+    big = syn.model_clumpy_3d(n=3000, seed=9, n_lev=7)
+    ctx = mgp.Context(precision=1)
+    u = np.linspace(-3e3, 3e3, 9)
+    for m in (small, big):
+        o = Oracle(m, nthreads=16)
+        ctx.load_model(m, dirs=o.dirs)
+        ctx.trace_rays()
+        ctx.init_populations()
+        I, xy = ctx.image(5, 1, u)
+        assert I.shape == (m.n, 9)
+        origins = np.arange(0, m.n, 37)
+        Io, _ = o.image(o.lte(), 5, 1, u, origins=origins)
+        assert np.max(rel_err(I[origins], Io)) < TOL_MIX
