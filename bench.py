@@ -555,6 +555,67 @@ def run_image(args):
     print(json.dumps(out))
 
 
+def run_sphere1d(args):
+    """1D spherically symmetric cloud (200 log-spaced shells, 2-level species, 12 rays,
+    31 bins, FP64): formal-solve throughput of one ALI step, and the ALI from LTE to a
+    1e-6 relative change (Ng off and on) on the GPU and with the FP64 oracle on the host
+    cores (all threads and one thread), with the converged populations compared."""
+    import numpy as np
+    import torch
+    import paper_1912_08445_gb300 as mg
+    import synthetic as syn
+    from oracle import Oracle
+    m = syn.model_sphere_1d(n=200, seed=0)
+    threads = os.cpu_count() or 1
+    out = {"metric": "ALI time to converge (max relative population change < 1e-6)", "unit": "s",
+           "workload": "1D spherical cloud, 200 shells, 2-level species, 12 rays (nside=1), 1 line x 31 bins, FP64",
+           "runs": []}
+    ctx = mg.Context(precision=mg.MG_FP64, profile=1)
+    ctx.load_model(m)
+    ctx.trace_rays()
+    ctx.init_populations()
+    solves, updates = ctx.work_counts()
+    for _ in range(args.warmup):
+        ctx.formal_solve()
+        ctx.update_populations()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        ctx.formal_solve()
+        ctx.update_populations()
+    torch.cuda.synchronize()
+    step_s = (time.perf_counter() - t0) / args.steps
+    out["solves_per_step"] = solves
+    out["gpu_solves_per_s"] = solves / step_s
+    out["gpu_ms_per_step"] = step_s * 1e3
+    ctx.close()
+    o_all = Oracle(m, nthreads=threads)
+    o_one = Oracle(m, nthreads=1)
+    for ng in (0, 4):
+        c = mg.Context(precision=mg.MG_FP64, tol=1e-6, max_iter=400, ng_period=ng)
+        c.load_model(m, dirs=o_all.dirs)
+        c.trace_rays()
+        c.init_populations()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rep, rc = c.iterate(allow_not_converged=True)
+        torch.cuda.synchronize()
+        gpu_s = time.perf_counter() - t0
+        pops = c.get_populations()
+        c.close()
+        rec = {"ng_period": ng, "gpu_seconds": gpu_s, "gpu_iterations": rep["iterations"],
+               "gpu_converged": bool(rep["converged"])}
+        for name, o in (("oracle", o_all), ("oracle_1thread", o_one)):
+            t0 = time.perf_counter()
+            ref, ch, conv = o.ali(tol=1e-6, max_iter=400, ng_period=ng)
+            rec[name + "_seconds"] = time.perf_counter() - t0
+            rec[name + "_iterations"] = len(ch)
+        rec["max_rel_diff_gpu_vs_oracle"] = float(np.max(2 * np.abs(pops - ref) / (np.abs(pops) + np.abs(ref))))
+        out["runs"].append(rec)
+    out["oracle_threads"] = threads
+    print(json.dumps(out))
+
+
 def run_learned(args):
     """Learned initial populations (20-level rotor): trains the network on converged
     populations of seeded cloud/disc models, then compares on held-out seeds the ALI to
@@ -615,7 +676,7 @@ def main():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--ali", action="store_true", help="measure ALI time to converge instead")
-    ap.add_argument("--workload", default="clumpy", choices=["clumpy", "batch", "disc", "learned", "image"])
+    ap.add_argument("--workload", default="clumpy", choices=["clumpy", "batch", "disc", "learned", "image", "sphere1d"])
     ap.add_argument("--corpus", type=int, default=200)
     ap.add_argument("--corpus-points", type=int, default=3000)
     ap.add_argument("--epochs", type=int, default=30)
@@ -634,6 +695,8 @@ def main():
         run_learned(args)
     elif args.workload == "image":
         run_image(args)
+    elif args.workload == "sphere1d":
+        run_sphere1d(args)
     elif args.ali:
         run_ali(args)
     elif args.impl == "reference":
