@@ -47,6 +47,7 @@ struct SolveArgs {
     int32_t *err;
     const int32_t *olist;    // optional list of origins (FP64 promotion), count in *ocount
     const int32_t *ocount;
+    int32_t groups;          // FP64 kernel: warps that solve different ray pairs of a point (1: the whole CTA per pair)
 };
 
 __device__ __forceinline__ double planck_d(double nu, double T) {
@@ -63,10 +64,12 @@ struct PairSmem64 {
     int32_t *ca, *cb;
 };
 
-__device__ void stage_half64(const SolveArgs &a, int64_t o, int r, int base, int dir, const PairSmem64 &S) {
+// Threads tid = 0..nth-1 share the work.
+__device__ void stage_half64(const SolveArgs &a, int64_t o, int r, int base, int dir, const PairSmem64 &S, int tid,
+                             int nth) {
     const int64_t off = a.ray_off[o * a.R + r];
     const int len = (int)(a.ray_off[o * a.R + r + 1] - off);
-    for (int e = threadIdx.x; e < len; e += blockDim.x) {
+    for (int e = tid; e < len; e += nth) {
         const int32_t c = a.cells[off + e];
         const int32_t prev = e ? a.cells[off + e - 1] : (int32_t)o;
         const int x0 = e ? a.xcum[off + e - 1] : 0;
@@ -172,22 +175,30 @@ __global__ void k_feautrier64(SolveArgs a) {
     extern __shared__ double smem[];
     const int L = a.L, Q = a.Q, F = L * Q;
     const int kmax = a.kmax;
+    // G groups of TG threads; with G > 1 each group is one warp and solves the pairs
+    // p = g, g + G, ... of the point on its own staging buffers and partial sums (for
+    // small F, so that a point keeps several warps busy); the partial sums are added in
+    // group order at the end.
+    const int G = a.groups;
+    const int TG = blockDim.x / G;
+    const int g = threadIdx.x / TG, t = threadIdx.x - g * TG;
     PairSmem64 S;
-    S.ds = smem;
+    S.ds = smem + (size_t)g * 4 * kmax;
     S.v = S.ds + kmax;
     S.ib = S.v + kmax;
     S.w = S.ib + kmax;
-    double *acc = S.w + kmax;   // [F][4]
-    S.ca = reinterpret_cast<int32_t *>(acc + 4 * F);
+    double *acc_all = smem + (size_t)G * 4 * kmax;   // [G][F][4]
+    double *acc = acc_all + (size_t)g * 4 * F;
+    S.ca = reinterpret_cast<int32_t *>(acc_all + (size_t)G * 4 * F) + (size_t)g * 2 * kmax;
     S.cb = S.ca + kmax;
     int64_t o = blockIdx.x;
     if (a.olist) {
         if ((int)blockIdx.x >= *a.ocount) return;
         o = a.olist[blockIdx.x];
     }
-    for (int f = threadIdx.x; f < 4 * F; f += blockDim.x) acc[f] = 0.0;
+    for (int f = t; f < 4 * F; f += TG) acc[f] = 0.0;
     const double bo = a.b[o];
-    for (int p = 0; p < a.P; p++) {
+    for (int p = g; p < a.P; p += G) {
         const int rf = a.pf[p], rb = a.pb[p];
         const int64_t ofb = a.ray_off[o * a.R + rb], ofl = a.ray_off[o * a.R + rf];
         const int lb = (int)(a.ray_off[o * a.R + rb + 1] - ofb);
@@ -196,21 +207,21 @@ __global__ void k_feautrier64(SolveArgs a) {
         const int Kf = lf ? a.xcum[ofl + lf - 1] : 0;
         const int K = Kb + 1 + Kf;
         if (K > kmax) {
-            if (threadIdx.x == 0) atomicOr(a.err, 2);
+            if (t == 0) atomicOr(a.err, 2);
             continue;
         }
-        __syncthreads();
-        stage_half64(a, o, rb, Kb - 1, -1, S);
-        stage_half64(a, o, rf, Kb + 1, +1, S);
-        if (threadIdx.x == 0) {
+        if (G > 1) __syncwarp(); else __syncthreads();
+        stage_half64(a, o, rb, Kb - 1, -1, S, t, TG);
+        stage_half64(a, o, rf, Kb + 1, +1, S, t, TG);
+        if (t == 0) {
             S.v[Kb] = 0.0;
             S.ib[Kb] = 1.0 / bo;
             S.w[Kb] = 0.0;
             S.ca[Kb] = (int32_t)o;
             S.cb[Kb] = (int32_t)o;
         }
-        __syncthreads();
-        for (int f = threadIdx.x; f < F; f += blockDim.x) {
+        if (G > 1) __syncwarp(); else __syncthreads();
+        for (int f = t; f < F; f += TG) {
             const int l = f / Q, q = f - l * Q;
             const double aq = a.roots[q] * bo;
             const double k1 = 1.0 + aq / kC;
@@ -250,16 +261,24 @@ __global__ void k_feautrier64(SolveArgs a) {
     }
     __syncthreads();
     const double invP = 1.0 / a.P;
-    for (int t = threadIdx.x; t < 4 * L; t += blockDim.x) {
-        const int l = t >> 2, k = t & 3;
+    for (int tt = threadIdx.x; tt < 4 * L; tt += blockDim.x) {
+        const int l = tt >> 2, k = tt & 3;
         double s = 0.0;
-        for (int q = 0; q < Q; q++) s += a.weights[q] * acc[4 * (l * Q + q) + k];
+        for (int q = 0; q < Q; q++) {
+            double v = acc_all[4 * (l * Q + q) + k];
+            for (int gg = 1; gg < G; gg++) v += acc_all[(size_t)gg * 4 * F + 4 * (l * Q + q) + k];
+            s += a.weights[q] * v;
+        }
         s *= invP;
         double *dst = k == 0 ? a.J : (k == 1 ? a.Lout : (k == 2 ? a.Jeff : a.Lc));
         dst[o * L + l] = s;
     }
     if (a.Jnu)
-        for (int f = threadIdx.x; f < F; f += blockDim.x) a.Jnu[o * F + f] = acc[4 * f] * invP;
+        for (int f = threadIdx.x; f < F; f += blockDim.x) {
+            double v = acc_all[4 * f];
+            for (int gg = 1; gg < G; gg++) v += acc_all[(size_t)gg * 4 * F + 4 * f];
+            a.Jnu[o * F + f] = v * invP;
+        }
 }
 
 // ---------------------------------------------------------------- images
@@ -333,8 +352,8 @@ __global__ void k_image64(ImageArgs a) {
         if (threadIdx.x == 0) atomicOr(sa.err, 2);
         return;
     }
-    stage_half64(sa, o, a.rb, Kb - 1, -1, S);
-    stage_half64(sa, o, a.rf, Kb + 1, +1, S);
+    stage_half64(sa, o, a.rb, Kb - 1, -1, S, threadIdx.x, blockDim.x);
+    stage_half64(sa, o, a.rf, Kb + 1, +1, S, threadIdx.x, blockDim.x);
     if (threadIdx.x == 0) {
         S.v[Kb] = 0.0;
         S.ib[Kb] = 1.0 / sa.b[o];
@@ -591,11 +610,24 @@ static int launch_fp64(mg_ctx *ctx, const int32_t *olist, const int32_t *ocount,
     a.olist = olist;
     a.ocount = ocount;
     const int F = a.L * a.Q;
-    size_t smem = sizeof(double) * ((size_t)a.kmax * 4 + 4 * (size_t)F) + sizeof(int32_t) * 2 * (size_t)a.kmax;
+    auto smem_for = [&](int G) {
+        return (size_t)G * (sizeof(double) * ((size_t)a.kmax * 4 + 4 * (size_t)F) + sizeof(int32_t) * 2 * (size_t)a.kmax);
+    };
+    size_t smem = smem_for(1);
     if (smem > 227 * 1024)
         return mg_fail(ctx, MG_ERR_CAPACITY, "FP64 formal solve: longest ray pair does not fit in shared memory");
+    // up to 8 warps per point solve different ray pairs when one warp covers all bins,
+    // as many as two CTAs per SM leave room for, balanced over the pairs
+    a.groups = 1;
+    if (F <= 32) {
+        int gmax = 1;
+        while (gmax < 8 && gmax < a.P && smem_for(gmax + 1) <= 113 * 1024) gmax++;
+        const int rounds = (a.P + gmax - 1) / gmax;
+        a.groups = (a.P + rounds - 1) / rounds;
+    }
+    smem = smem_for(a.groups);
     MG_CUDA(cudaFuncSetAttribute(k_feautrier64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    int threads = ((F + 31) / 32) * 32;
+    int threads = a.groups > 1 ? 32 * a.groups : ((F + 31) / 32) * 32;
     if (threads > 256) threads = 256;
     if (!olist) MG_CUDA(cudaMemsetAsync(ctx->d_err, 0, 4, ctx->stream));
     {
