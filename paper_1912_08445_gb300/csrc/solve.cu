@@ -116,8 +116,9 @@ __device__ __forceinline__ Pt64 point64(const SolveArgs &a, int l, double aq, do
     return p;
 }
 
-// One CTA per origin point; the CTA loops over the ray pairs, staging each expanded pair
-// in shared memory, and each thread solves its frequency bins.
+// One CTA per origin point; the CTA (or, for few bins, each of its warps) loops over the
+// ray pairs, staging each expanded pair in shared memory, and each thread solves its
+// frequency bins.
 //
 // Sweep in rescaled Rybicki-Hummer variables from a far end towards the origin: with
 // dtau_k between points k and k+1, F_k = dtau_k Phi_k and z_k = dtau_k psi_k,
