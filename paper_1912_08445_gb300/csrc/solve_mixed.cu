@@ -215,6 +215,12 @@ __device__ __forceinline__ Side32 sweep32(const MixArgs &a, int l, float aq, flo
     return Side32{Phi * iota, psi, dt_p};
 }
 
+// Shared memory of the CTA kernel: pt [kmax] float4, ln [kmax][L] float2, then acc
+// [L][Q] float4 at the next 16-byte boundary.
+__host__ __device__ __forceinline__ size_t mixed_acc_offset(int kmax, int L) {
+    return (16 * (size_t)kmax + 8 * (size_t)kmax * L + 15) & ~(size_t)15;
+}
+
 template <bool OVL>
 __global__ void __launch_bounds__(256) k_feautrier_mixed(MixArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -222,7 +228,8 @@ __global__ void __launch_bounds__(256) k_feautrier_mixed(MixArgs a) {
     const int kmax = a.kmax;
     float4 *pt = reinterpret_cast<float4 *>(smem_raw);
     float2 *ln = reinterpret_cast<float2 *>(pt + kmax);
-    float4 *acc = reinterpret_cast<float4 *>(ln + (size_t)kmax * L);   // [L*Q]: (sum u, L, Jeff, 1-L)
+    // [L*Q]: (sum u, L, Jeff, 1-L); starts on a 16-byte boundary (kmax * L may be odd)
+    float4 *acc = reinterpret_cast<float4 *>(smem_raw + mixed_acc_offset(kmax, L));
     const int64_t o = blockIdx.x;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
     for (int f = threadIdx.x; f < L * Q; f += blockDim.x) acc[f] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -1000,7 +1007,7 @@ static int launch_mixed(mg_ctx *ctx, int variant) {
     a.kmax = (int32_t)ctx->max_pair_len;
     a.overlap = overlap;
     a.err = ctx->d_err;
-    size_t smem = (size_t)a.kmax * (16 + 8 * (size_t)L) + 16 * (size_t)L * Q;
+    size_t smem = mixed_acc_offset(a.kmax, L) + 16 * (size_t)L * Q;
     if ((overlap || Q > 128) && smem > 227 * 1024) {
         return mg_fail(ctx, MG_ERR_CAPACITY, "mixed formal solve: longest ray pair does not fit in shared memory");
     }

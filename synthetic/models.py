@@ -87,6 +87,23 @@ def species_two_level(A21=1.0e-4, K21=2.0e-16, dE_cm=6.0, g_ratio=3.0, mass_amu=
                    lo=np.array([0], np.int32), A=np.array([A21]), T_grid=T_grid, K_down=K_down)
 
 
+def species_ladder(n_lev, dE_cm=6.0, A1=1.0e-5, K0=1.0e-16, mass_amu=28.0):
+    """Equally spaced levels E_i = i dE, g_i = 2i + 1, radiative lines i -> i-1 only, all
+    at the same frequency: every line overlaps every other one, so a frequency bin sums
+    all their profiles. A_i = A1 i; collisional de-excitation K0 / 10^(i-j-1), constant
+    in T."""
+    h, c = CODATA["h"], CODATA["c"]
+    E = np.arange(n_lev) * h * c * dE_cm * 100.0
+    g = 2.0 * np.arange(n_lev) + 1.0
+    up = np.arange(1, n_lev, dtype=np.int32)
+    lo = up - 1
+    A = A1 * up.astype(np.float64)
+    T_grid = np.array([5.0, 1000.0])
+    K = [K0 / 10.0 ** (i - j - 1) for i in range(1, n_lev) for j in range(i)]
+    K_down = np.repeat(np.array(K)[:, None], 2, axis=1)
+    return Species(E=E, g=g, mass=mass_amu * CODATA["amu"], up=up, lo=lo, A=A, T_grid=T_grid, K_down=K_down)
+
+
 def species_rotor(n_lev, rng, mass_amu=28.0, B_range=(40e9, 60e9), A1_scale=1e-7,
                   a_range=(1e-17, 1e-16), b_range=(0.0, 0.5), dj_decay=10.0):
     """Seeded linear-rotor ladder: E_J = h B J(J+1), g_J = 2J+1, radiative lines
