@@ -422,6 +422,52 @@ def test_powerlaw_1d_analytic():
     assert errs[400].max() < errs[100].max() / 8
 
 
+def test_overlapping_lines_sum_their_opacities():
+    """Static uniform line of points with an equally spaced ladder (3 lines at one
+    frequency) in LTE: every bin's opacity is the sum of the three lines' (Sec. 2.2.1)
+    and S = B_nu(T), so J = S + (B_cmb - S)(exp(-tau+) + exp(-tau-))/2 with
+    tau = sum_l chi_l phi l. The oracle's J of every line matches it, converging at
+    second order; with one line's opacity alone the closed form misses by far more."""
+    import analytic as an
+    sp = syn.species_ladder(4)
+    R, T = 1e13, 30.0
+    errs, miss = {}, 0.0
+    for nc in (100, 400):
+        x = np.linspace(-R, R, nc)
+        m = syn.model_line_1d(x, 0.0, 1e11, T, 150.0, 1e-6, sp, 31)
+        o = Oracle(m)
+        pops = o.lte()
+        nu = (sp.E[1] - sp.E[0]) / h
+        dnu = nu * o.width(0) / c
+        chi_l = []
+        for l in range(sp.n_lines):
+            u, lo = sp.up[l], sp.lo[l]
+            Bul = sp.A[l] * c ** 2 / (2 * h * nu ** 3)
+            Blu = sp.g[u] / sp.g[lo] * Bul
+            chi_l.append(h * nu / (4 * math.pi) * (pops[0, lo] * Blu - pops[0, u] * Bul))
+        S = an.planck(nu, T)
+        picks = np.array([nc // 4, nc // 2, 3 * nc // 4])
+        _, _, _, Jnu = o.formal_solve(pops, picks, spectrum=True)
+        e = []
+        for i, p in enumerate(picks):
+            for q in range(o.Q):
+                nuq = nu + o.roots[q] * dnu
+                phi = math.exp(-o.roots[q] ** 2) / (dnu * math.sqrt(math.pi))
+                Bc = an.planck(nuq, an.T_CMB)
+                for chi in (sum(chi_l), chi_l[0]):
+                    tp, tm = chi * phi * (R - x[p]), chi * phi * (R + x[p])
+                    Jan = S + 0.5 * (Bc - S) * (math.exp(-tp) + math.exp(-tm))
+                    r = [2 * abs(Jnu[i, l, q] - Jan) / (Jnu[i, l, q] + Jan) for l in range(sp.n_lines)]
+                    if chi is chi_l[0]:
+                        miss = max(miss, max(r))
+                    else:
+                        e.extend(r)
+        errs[nc] = max(e)
+    assert errs[100] < 2e-4
+    assert errs[400] < errs[100] / 10
+    assert miss > 100 * errs[100]
+
+
 # ------------------------------------------------------------------ statistical equilibrium
 def _two_cell_model(n_coll, T=30.0):
     sp = syn.species_two_level(A21=1e-5)
