@@ -217,9 +217,11 @@ __device__ __forceinline__ Side32 sweep32(const MixArgs &a, int l, float aq, flo
 
 // Shared memory of the CTA kernel: pt [kmax] float4, ln [kmax][L] float2, then acc
 // [L][Q] float4 at the next 16-byte boundary.
-__host__ __device__ __forceinline__ size_t mixed_acc_offset(int kmax, int L) {
+__host__ __device__ constexpr size_t mixed_acc_offset(int kmax, int L) {
     return (16 * (size_t)kmax + 8 * (size_t)kmax * L + 15) & ~(size_t)15;
 }
+static_assert(mixed_acc_offset(3, 3) % 16 == 0 && mixed_acc_offset(3, 3) >= 16 * 3 + 8 * 9, "acc alignment");
+static_assert(mixed_acc_offset(4, 2) == 16 * 4 + 8 * 8, "no padding when kmax * L is even");
 
 template <bool OVL>
 __global__ void __launch_bounds__(256) k_feautrier_mixed(MixArgs a) {
