@@ -491,6 +491,30 @@ def test_stateq_two_level_closed_form():
         assert nf == 0
 
 
+def test_stateq_validity_fallback():
+    """Validity check (Sec. 6.1): a cell whose ALO-corrected rates give a negative
+    population (here an effective intensity J_eff far below zero) is solved again without
+    the ALO (L = 0, J_eff = J) and counted; the other cell keeps its ALO solution. Both
+    match the 2-level closed form with the rates each one used."""
+    m = _two_cell_model(1e9)
+    o = Oracle(m)
+    sp = m.species
+    nu = (sp.E[1] - sp.E[0]) / h
+    Bul = sp.A[0] * c ** 2 / (2 * h * nu ** 3); Blu = 3 * Bul
+    Cd = 2e-16 * 1e9; Cu = Cd * 3 * math.exp(-h * nu / (kB * 30.0))
+    Jv, Lv = 1e-16, 0.9
+    J = np.full((2, 1), Jv)
+    L = np.full((2, 1), Lv)
+    E = np.array([[0.5 * Jv], [-0.03 * Jv]])   # cell 1: B_lu J_eff + C_lu < 0 < A (1 - L) + B_ul J_eff + C_ul
+    pops, nf = o.stateq(J, L, E)
+    assert nf == 1
+    r0 = (Blu * E[0, 0] + Cu) / (sp.A[0] * (1 - Lv) + Bul * E[0, 0] + Cd)
+    r1 = (Blu * Jv + Cu) / (sp.A[0] + Bul * Jv + Cd)
+    assert abs(pops[0, 1] / pops[0, 0] - r0) <= 1e-12 * r0
+    assert abs(pops[1, 1] / pops[1, 0] - r1) <= 1e-12 * r1
+    assert np.all(pops >= 0)
+
+
 def test_stateq_detailed_balance_and_high_density():
     """J = B_nu(T) gives Boltzmann populations at any density (detailed balance), and a
     very high density thermalises to Boltzmann whatever J. Fails with the excitation
