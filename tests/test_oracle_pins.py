@@ -515,6 +515,20 @@ def test_stateq_validity_fallback():
     assert np.all(pops >= 0)
 
 
+def test_max_rel_change_ignores_negligible_levels():
+    """Convergence measure: the largest |n_new - n_old| / n_new over levels holding at
+    least 1e-10 of the cell's species: a 10% change counts, a 50% change of a level at
+    1e-12 of the cell does not."""
+    m = _two_cell_model(1e9)
+    o = Oracle(m)
+    ns = m.n_spec
+    new = np.array([[0.9 * ns[0], 0.1 * ns[0]], [ns[1] * (1 - 1e-12), ns[1] * 1e-12]])
+    old = new.copy()
+    old[0, 1] = 0.09 * ns[0]            # 10% below the new value
+    old[1, 1] = 0.5 * new[1, 1]         # 50%, but negligible
+    assert abs(o.max_rel_change(old, new) - 0.1) < 1e-12
+
+
 def test_stateq_detailed_balance_and_high_density():
     """J = B_nu(T) gives Boltzmann populations at any density (detailed balance), and a
     very high density thermalises to Boltzmann whatever J. Fails with the excitation
