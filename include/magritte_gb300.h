@@ -179,6 +179,13 @@ int mg_formal_solve(mg_ctx *ctx);
 /* Copies J, L, Jeff, each [n][n_lines], to host buffers (any may be NULL). */
 int mg_get_radiation(const mg_ctx *ctx, double *J, double *L, double *Jeff);
 int mg_get_radiation_dev(const mg_ctx *ctx, double *d_J, double *d_L, double *d_Jeff);
+/* Replaces the radiation field that mg_update_populations reads: J, L and Jeff, each
+ * [n][n_lines] host buffers (all three required), stand for the result of a formal solve
+ * (eq. 'L_operator', 'ourJeff'), e.g. a field computed elsewhere or one saved with
+ * mg_get_radiation; 1 - L is formed from L. Requires populations (MG_ERR_STATE);
+ * MG_ERR_ARG for a null buffer or a non-finite value. Clears the negative-opacity count
+ * of the last formal solve. Synchronises. */
+int mg_set_radiation(mg_ctx *ctx, const double *J, const double *L, const double *Jeff);
 /* Per-bin mean intensity (1/P) sum_pairs u, [n][n_lines][n_q]; needs opt.spectrum = 1. */
 int mg_get_spectrum(const mg_ctx *ctx, double *Jnu);
 
@@ -225,15 +232,20 @@ int mg_update_populations(mg_ctx *ctx, double *max_rel_change);
  * budget). The paper has no counterpart: it is an interface addition only.
  * d_pops_old [n][n_lev] (read) and d_pops_new [n][n_lev] (written) are caller-owned
  * device buffers on the context's device; the radiation field is the one left by the
- * last mg_formal_solve (MG_ERR_STATE otherwise). Computes the same statistical
- * equilibrium, validity fallback and convergence measure as mg_update_populations,
- * without touching the context's populations. *max_rel_change and *n_fallback (either
- * may be NULL) receive the convergence measure and the number of fallback cells.
+ * last mg_formal_solve or mg_set_radiation (MG_ERR_STATE otherwise). Computes the same
+ * statistical equilibrium, validity fallback and convergence measure as
+ * mg_update_populations, with the same return codes (MG_WARN_NEG_POP_FALLBACK, else
+ * MG_WARN_NEG_OPACITY after a formal solve that met a negative opacity integral), without
+ * touching the context's populations. *max_rel_change and *n_fallback (either may be
+ * NULL) receive the convergence measure and the number of fallback cells.
  * Scratch: a static 512 KiB device array per GPU that loads the library (held until
- * exit); at most 2,097,152 cells per call (MG_ERR_CAPACITY beyond). The first call on a
- * device looks up that array's device address; make that first call before any stream
- * capture. The call allocates nothing and synchronises the context's stream. Calls that
- * overlap on the GPU (other streams, threads or contexts) race on the shared scratch. */
+ * exit); at most 2,097,152 cells per call (MG_ERR_CAPACITY beyond). Everything that may
+ * allocate -- loading the kernels and the array on the device, looking up the array's
+ * device address, and reserving the kernel's local memory with a warm-up launch -- is
+ * done by mg_set_species; if that set-up failed, this call returns MG_ERR_CUDA with the
+ * reason. The call itself allocates nothing. It ends by synchronising the context's
+ * stream, so it cannot be used inside a stream capture. Calls that overlap on the GPU
+ * (other streams, threads or contexts) race on the shared scratch. */
 int mg_update_populations_noalloc(mg_ctx *ctx, const double *d_pops_old, double *d_pops_new,
                                   double *max_rel_change, int64_t *n_fallback);
 

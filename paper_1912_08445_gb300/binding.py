@@ -82,6 +82,7 @@ _SIGS = {
     "mg_formal_solve": (C.c_int, [_P]),
     "mg_get_radiation": (C.c_int, [_P, _P, _P, _P]),
     "mg_get_radiation_dev": (C.c_int, [_P, _P, _P, _P]),
+    "mg_set_radiation": (C.c_int, [_P, _P, _P, _P]),
     "mg_get_spectrum": (C.c_int, [_P, _P]),
     "mg_image": (C.c_int, [_P, C.c_int32, C.c_int32, C.c_int32, _P, _P, _P]),
     "mg_image_dev": (C.c_int, [_P, C.c_int32, C.c_int32, C.c_int32, _P, _P, _P]),
@@ -292,6 +293,11 @@ class Context:
         J = np.empty((self.n, self.n_lines)); L = np.empty_like(J); E = np.empty_like(J)
         self._chk(self.lib.mg_get_radiation(self.h, _ptr(J), _ptr(L), _ptr(E)), "mg_get_radiation")
         return J, L, E
+
+    def set_radiation(self, J, L, Jeff):
+        """Replaces the radiation field read by update_populations (mg_set_radiation)."""
+        J, L, E = _c(J, np.float64), _c(L, np.float64), _c(Jeff, np.float64)
+        self._chk(self.lib.mg_set_radiation(self.h, _ptr(J), _ptr(L), _ptr(E)), "mg_set_radiation")
 
     def get_spectrum(self):
         out = np.empty((self.n, self.n_lines, self.Q))

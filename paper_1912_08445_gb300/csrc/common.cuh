@@ -151,6 +151,11 @@ struct mg_ctx {
     // ---- launch variant of the mixed formal solve (-1: default for the model)
     int mixed_variant = -1;
 
+    // ---- allocation-free update: set-up done at mg_set_species (stateq_noalloc.cu)
+    bool na_ready = false;
+    std::string na_error;
+    unsigned long long *na_scratch = nullptr;   // device address of the static scratch
+
     // ---- profiling
     std::vector<mg::KernelTimer> timers;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -207,6 +212,7 @@ int mg_launch_ng(mg_ctx *ctx, int *accepted);
 int mg_launch_push_history(mg_ctx *ctx);
 int mg_launch_stateq_into(mg_ctx *ctx, const double *pops_old, double *pops_new, const int32_t *active);
 int mg_ensure_solve_state(mg_ctx *ctx);   // state buffers, overlaps and collision rates ready
+void mg_noalloc_prepare(mg_ctx *ctx);     // set-up of mg_update_populations_noalloc
 // batch helpers (solve_mixed.cu)
 size_t mg_mixargs_size();
 int mg_fill_mixargs(mg_ctx *ctx, void *out);

@@ -356,6 +356,7 @@ extern "C" int mg_set_species(mg_ctx *ctx, int32_t n_lev, const double *E, const
     free_rays(ctx);
     if ((rc = refresh_widths(ctx))) return rc;
     MG_CUDA(cudaStreamSynchronize(ctx->stream));
+    mg_noalloc_prepare(ctx);   // records its own failure; the update reports it
     return MG_OK;
 }
 
@@ -692,6 +693,30 @@ extern "C" int mg_get_radiation(const mg_ctx *cctx, double *J, double *L, double
     if (L) MG_CUDA(cudaMemcpyAsync(L, ctx->d_L, b, cudaMemcpyDeviceToHost, ctx->stream));
     if (Jeff) MG_CUDA(cudaMemcpyAsync(Jeff, ctx->d_Jeff, b, cudaMemcpyDeviceToHost, ctx->stream));
     MG_CUDA(cudaStreamSynchronize(ctx->stream));
+    return MG_OK;
+}
+
+extern "C" int mg_set_radiation(mg_ctx *ctx, const double *J, const double *L, const double *Jeff) {
+    if (!ctx) return MG_ERR_ARG;
+    if (!J || !L || !Jeff) return mg_fail(ctx, MG_ERR_ARG, "mg_set_radiation: null buffer");
+    int rc;
+    if ((rc = need_species_model(ctx, "mg_set_radiation"))) return rc;
+    if (!ctx->have_pops) return mg_fail(ctx, MG_ERR_STATE, "mg_set_radiation: set or initialise populations first");
+    const size_t m = (size_t)ctx->n * ctx->n_lines;
+    for (size_t i = 0; i < m; i++)
+        if (!std::isfinite(J[i]) || !std::isfinite(L[i]) || !std::isfinite(Jeff[i]))
+            return mg_fail(ctx, MG_ERR_ARG, "mg_set_radiation: non-finite value");
+    cudaSetDevice(ctx->device);
+    if ((rc = ensure_state(ctx))) return rc;
+    std::vector<double> oml(m);
+    for (size_t i = 0; i < m; i++) oml[i] = 1.0 - L[i];
+    MG_CUDA(cudaMemcpyAsync(ctx->d_J, J, 8 * m, cudaMemcpyHostToDevice, ctx->stream));
+    MG_CUDA(cudaMemcpyAsync(ctx->d_L, L, 8 * m, cudaMemcpyHostToDevice, ctx->stream));
+    MG_CUDA(cudaMemcpyAsync(ctx->d_Jeff, Jeff, 8 * m, cudaMemcpyHostToDevice, ctx->stream));
+    MG_CUDA(cudaMemcpyAsync(ctx->d_Lc, oml.data(), 8 * m, cudaMemcpyHostToDevice, ctx->stream));
+    MG_CUDA(cudaMemsetAsync(ctx->d_scal + 4, 0, sizeof(unsigned long long), ctx->stream));
+    MG_CUDA(cudaStreamSynchronize(ctx->stream));
+    ctx->have_rad = true;
     return MG_OK;
 }
 

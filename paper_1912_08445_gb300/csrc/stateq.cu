@@ -3,6 +3,7 @@
 #include <cmath>
 #include <cstring>
 #include "common.cuh"
+#include "stateq_common.cuh"
 
 using namespace mg;
 
@@ -35,49 +36,10 @@ __global__ void k_collision_rates(int64_t n, int nlev, int nT, const double *E, 
     while ((i + 1) * i / 2 <= pr) i++;
     const int j = pr - i * (i - 1) / 2;
     const double Tc = T[c];
-    const double *k = K + (size_t)pr * nT;
-    double kd;
-    if (nT == 1 || Tc <= Tg[0]) kd = k[0];
-    else if (Tc >= Tg[nT - 1]) kd = k[nT - 1];
-    else {
-        int a = 0;
-        while (Tg[a + 1] < Tc) a++;
-        const double w = (Tc - Tg[a]) / (Tg[a + 1] - Tg[a]);
-        kd = k[a] + w * (k[a + 1] - k[a]);
-    }
-    const double Cd = kd * ncoll[c];
+    double Cd, Cu;
+    collision_rates_pair(collision_k_down(K, pr, nT, Tg, Tc), ncoll[c], g[i], g[j], E[i], E[j], Tc, Cd, Cu);
     coll[2 * t] = Cd;
-    coll[2 * t + 1] = Cd * g[i] / g[j] * exp(-(E[i] - E[j]) / (kKB * Tc));
-}
-
-// Stationary state of the level system by Grassmann-Taksar-Heyman state reduction:
-// rates q[i][j] (i -> j) are all non-negative, so every step adds non-negative terms and
-// the populations come out non-negative. Returns false on a zero exit rate.
-template <int MAXLEV>
-__device__ bool gth_solve(int n, double (&q)[MAXLEV][MAXLEV], double (&pi)[MAXLEV]) {
-    double ex[MAXLEV];
-    for (int k = n - 1; k >= 1; k--) {
-        double s = 0.0;
-        for (int j = 0; j < k; j++) s += q[k][j];
-        ex[k] = s;
-        if (!(s > 0.0)) return false;
-        const double is = 1.0 / s;
-        for (int i = 0; i < k; i++) {
-            const double f = q[i][k] * is;
-            if (f == 0.0) continue;
-            for (int j = 0; j < k; j++) q[i][j] += f * q[k][j];
-        }
-    }
-    pi[0] = 1.0;
-    double tot = 1.0;
-    for (int k = 1; k < n; k++) {
-        double s = 0.0;
-        for (int i = 0; i < k; i++) s += pi[i] * q[i][k];
-        pi[k] = s / ex[k];
-        tot += pi[k];
-    }
-    for (int k = 0; k < n; k++) pi[k] /= tot;
-    return true;
+    coll[2 * t + 1] = Cu;
 }
 
 struct StateqArgs {
@@ -100,13 +62,7 @@ __device__ void build_rates(const StateqArgs &a, int64_t c, bool plain, double (
     const int n = a.nlev;
     for (int i = 0; i < n; i++)
         for (int j = 0; j < n; j++) q[i][j] = 0.0;
-    for (int l = 0; l < a.L; l++) {
-        const LineConst k = a.lc[l];
-        const double je = plain ? a.J[c * a.L + l] : a.Jeff[c * a.L + l];
-        const double oml = plain ? 1.0 : a.Lc[c * a.L + l];
-        q[k.up][k.lo] += k.A * oml + k.Bul * je;
-        q[k.lo][k.up] += k.Blu * je;
-    }
+    line_rates<MAXLEV>(a.L, a.lc, a.J, a.Lc, a.Jeff, c, plain, q);
     const int npairs = n * (n - 1) / 2;
     const double *cr = a.coll + (size_t)c * npairs * 2;
     int pr = 0;
@@ -127,13 +83,11 @@ __global__ void k_stateq(StateqArgs a) {
         const int n = a.nlev;
         double q[MAXLEV][MAXLEV], pi[MAXLEV];
         build_rates<MAXLEV>(a, c, false, q);
-        bool ok = gth_solve<MAXLEV>(n, q, pi);
-        for (int i = 0; i < n && ok; i++) ok = isfinite(pi[i]) && pi[i] >= 0.0;
+        bool ok = gth_solve<MAXLEV>(n, q, pi) && valid_fractions<MAXLEV>(n, pi);
         if (!ok) {
             fb = 1;
             build_rates<MAXLEV>(a, c, true, q);
-            ok = gth_solve<MAXLEV>(n, q, pi);
-            for (int i = 0; i < n && ok; i++) ok = isfinite(pi[i]) && pi[i] >= 0.0;
+            ok = gth_solve<MAXLEV>(n, q, pi) && valid_fractions<MAXLEV>(n, pi);
             if (!ok) bad = 1;
         }
         const double ns = a.nspec[c];

@@ -10,13 +10,22 @@
 // a file-scope static __device__ array. That array exists on every GPU that loads this
 // library, from load until process exit.
 //
-// The collision rates are evaluated inside the kernel (same formulas and operation
-// order as the context's collision-rate table), so the call depends only on the
-// radiation field left by the last mg_formal_solve and on the model, species and
-// quadrature already in the context.
+// Everything that could allocate happens once, when the species is set
+// (mg_noalloc_prepare, called by mg_set_species): loading this file's kernels and the
+// static array on the device (lazy module loading allocates device memory for them),
+// looking up the array's device address, and one warm-up launch of the kernel instance
+// the species needs, so that its local-memory reservation (the rate matrix of up to 64
+// levels lives in local memory) is made there. The update itself then allocates nothing.
+//
+// The collision rates are evaluated inside the kernel with the same device functions as
+// the context's collision-rate table, and the rates and the GTH solve are those of the
+// regular update (stateq_common.cuh), so the call depends only on the radiation field
+// left by the last mg_formal_solve (or mg_set_radiation) and on the model and species.
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include "common.cuh"
+#include "stateq_common.cuh"
 
 using namespace mg;
 
@@ -42,62 +51,23 @@ struct NaArgs {
     unsigned long long *scratch;
 };
 
-template <int MAXLEV>
-__device__ bool na_gth(int n, double (&q)[MAXLEV][MAXLEV], double (&pi)[MAXLEV]) {
-    double ex[MAXLEV];
-    for (int k = n - 1; k >= 1; k--) {
-        double s = 0.0;
-        for (int j = 0; j < k; j++) s += q[k][j];
-        ex[k] = s;
-        if (!(s > 0.0)) return false;
-        const double is = 1.0 / s;
-        for (int i = 0; i < k; i++) {
-            const double f = q[i][k] * is;
-            if (f == 0.0) continue;
-            for (int j = 0; j < k; j++) q[i][j] += f * q[k][j];
-        }
-    }
-    pi[0] = 1.0;
-    double tot = 1.0;
-    for (int k = 1; k < n; k++) {
-        double s = 0.0;
-        for (int i = 0; i < k; i++) s += pi[i] * q[i][k];
-        pi[k] = s / ex[k];
-        tot += pi[k];
-    }
-    for (int k = 0; k < n; k++) pi[k] /= tot;
-    return true;
-}
-
+// Rates of eq. 'ourALI' (or without the ALO when `plain`), the collision part evaluated
+// in place from the tabulated coefficients.
 template <int MAXLEV>
 __device__ void na_rates(const NaArgs &a, int64_t c, bool plain, double (&q)[MAXLEV][MAXLEV]) {
     const int n = a.nlev;
     for (int i = 0; i < n; i++)
         for (int j = 0; j < n; j++) q[i][j] = 0.0;
-    for (int l = 0; l < a.L; l++) {
-        const LineConst k = a.lc[l];
-        const double je = plain ? a.J[c * a.L + l] : a.Jeff[c * a.L + l];
-        const double oml = plain ? 1.0 : a.Lc[c * a.L + l];
-        q[k.up][k.lo] += k.A * oml + k.Bul * je;
-        q[k.lo][k.up] += k.Blu * je;
-    }
+    line_rates<MAXLEV>(a.L, a.lc, a.J, a.Lc, a.Jeff, c, plain, q);
     const double Tc = a.T[c];
     int pr = 0;
     for (int i = 1; i < n; i++)
         for (int j = 0; j < i; j++, pr++) {
-            const double *k = a.K + (size_t)pr * a.nT;
-            double kd;
-            if (a.nT == 1 || Tc <= a.Tg[0]) kd = k[0];
-            else if (Tc >= a.Tg[a.nT - 1]) kd = k[a.nT - 1];
-            else {
-                int s = 0;
-                while (a.Tg[s + 1] < Tc) s++;
-                const double w = (Tc - a.Tg[s]) / (a.Tg[s + 1] - a.Tg[s]);
-                kd = k[s] + w * (k[s + 1] - k[s]);
-            }
-            const double Cd = kd * a.ncoll[c];
+            double Cd, Cu;
+            collision_rates_pair(collision_k_down(a.K, pr, a.nT, a.Tg, Tc), a.ncoll[c], a.g[i], a.g[j], a.E[i],
+                                 a.E[j], Tc, Cd, Cu);
             q[i][j] += Cd;
-            q[j][i] += Cd * a.g[i] / a.g[j] * exp(-(a.E[i] - a.E[j]) / (kKB * Tc));
+            q[j][i] += Cu;
         }
 }
 
@@ -110,13 +80,11 @@ __global__ void __launch_bounds__(kNaThreads) k_stateq_noalloc(NaArgs a) {
         const int n = a.nlev;
         double q[MAXLEV][MAXLEV], pi[MAXLEV];
         na_rates<MAXLEV>(a, c, false, q);
-        bool ok = na_gth<MAXLEV>(n, q, pi);
-        for (int i = 0; i < n && ok; i++) ok = isfinite(pi[i]) && pi[i] >= 0.0;
+        bool ok = gth_solve<MAXLEV>(n, q, pi) && valid_fractions<MAXLEV>(n, pi);
         if (!ok) {
             fb = 1;
             na_rates<MAXLEV>(a, c, true, q);
-            ok = na_gth<MAXLEV>(n, q, pi);
-            for (int i = 0; i < n && ok; i++) ok = isfinite(pi[i]) && pi[i] >= 0.0;
+            ok = gth_solve<MAXLEV>(n, q, pi) && valid_fractions<MAXLEV>(n, pi);
             if (!ok) bad = 1;
         }
         const double ns = a.nspec[c];
@@ -178,11 +146,83 @@ __global__ void k_noalloc_finish(const unsigned long long *part, int64_t nblocks
     }
 }
 
-// Device address of g_na_scratch per device ordinal, looked up once per device.
+// Device address of g_na_scratch per device ordinal, looked up once per device under a
+// lock (two threads setting up contexts on the same device do not race on it).
 constexpr int kNaMaxDevices = 64;
+std::mutex g_na_mu;
 unsigned long long *g_na_ptr[kNaMaxDevices] = {nullptr};
 
+template <int MAXLEV>
+int na_launch(const NaArgs &a, int64_t nb, cudaStream_t s) {
+    k_stateq_noalloc<MAXLEV><<<(unsigned)nb, kNaThreads, 0, s>>>(a);
+    return cudaGetLastError() == cudaSuccess ? MG_OK : MG_ERR_CUDA;
+}
+
+int na_dispatch(int nlev, const NaArgs &a, int64_t nb, cudaStream_t s) {
+    if (nlev <= 8) return na_launch<8>(a, nb, s);
+    if (nlev <= 24) return na_launch<24>(a, nb, s);
+    return na_launch<64>(a, nb, s);
+}
+
+template <int MAXLEV>
+cudaError_t na_attributes() {
+    cudaFuncAttributes fa;
+    return cudaFuncGetAttributes(&fa, k_stateq_noalloc<MAXLEV>);
+}
+
 }  // namespace
+
+// Set-up for mg_update_populations_noalloc on the context's device and species (called
+// by mg_set_species with the device current): the static scratch's device address, the
+// kernels loaded, and one warm-up launch over no cells (one block that only writes its
+// partial-result slot) so that the instance's local memory is reserved now. Failures are
+// kept in the context and reported by the update; mg_set_species itself does not fail.
+void mg_noalloc_prepare(mg_ctx *ctx) {
+    ctx->na_ready = false;
+    ctx->na_error.clear();
+    if (ctx->device < 0 || ctx->device >= kNaMaxDevices) {
+        ctx->na_error = "device ordinal out of range";
+        return;
+    }
+    unsigned long long *scratch = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_na_mu);
+        if (!g_na_ptr[ctx->device]) {
+            void *p = nullptr;
+            cudaError_t e = cudaGetSymbolAddress(&p, g_na_scratch);
+            if (e != cudaSuccess) {
+                ctx->na_error = std::string("cudaGetSymbolAddress(g_na_scratch): ") + cudaGetErrorString(e);
+                return;
+            }
+            g_na_ptr[ctx->device] = static_cast<unsigned long long *>(p);
+        }
+        scratch = g_na_ptr[ctx->device];
+    }
+    cudaFuncAttributes fa;
+    cudaError_t e = ctx->n_lev <= 8 ? na_attributes<8>() : (ctx->n_lev <= 24 ? na_attributes<24>() : na_attributes<64>());
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_noalloc_finish);
+    if (e != cudaSuccess) {
+        ctx->na_error = std::string("cudaFuncGetAttributes: ") + cudaGetErrorString(e);
+        return;
+    }
+    NaArgs a{};
+    a.n = 0;
+    a.nlev = ctx->n_lev;
+    a.scratch = scratch;
+    if (na_dispatch(ctx->n_lev, a, 1, ctx->stream) != MG_OK) {
+        ctx->na_error = "warm-up launch failed";
+        return;
+    }
+    k_noalloc_finish<<<1, 256, 0, ctx->stream>>>(scratch, 1, scratch + 4 * kNaMaxBlocks);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) {
+        ctx->na_error = std::string("warm-up: ") + cudaGetErrorString(e);
+        return;
+    }
+    ctx->na_scratch = scratch;
+    ctx->na_ready = true;
+}
 
 extern "C" int mg_update_populations_noalloc(mg_ctx *ctx, const double *d_pops_old, double *d_pops_new,
                                              double *max_rel_change, int64_t *n_fallback) {
@@ -193,16 +233,10 @@ extern "C" int mg_update_populations_noalloc(mg_ctx *ctx, const double *d_pops_o
     if (ctx->n > kNaMaxCells)
         return mg_fail(ctx, MG_ERR_CAPACITY,
                        "mg_update_populations_noalloc: at most 2097152 cells per call (static scratch of 512 KiB)");
-    if (ctx->device < 0 || ctx->device >= kNaMaxDevices)
-        return mg_fail(ctx, MG_ERR_ARG, "mg_update_populations_noalloc: device ordinal out of range");
+    if (!ctx->na_ready)
+        return mg_fail(ctx, MG_ERR_CUDA, "mg_update_populations_noalloc: set-up at mg_set_species failed: " + ctx->na_error);
     MG_CUDA(cudaSetDevice(ctx->device));
-    if (!g_na_ptr[ctx->device]) {
-        void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_na_scratch);
-        if (e != cudaSuccess) return mg_cuda_check(ctx, e, "cudaGetSymbolAddress(g_na_scratch)");
-        g_na_ptr[ctx->device] = static_cast<unsigned long long *>(p);
-    }
-    unsigned long long *scratch = g_na_ptr[ctx->device];
+    unsigned long long *scratch = ctx->na_scratch;
     NaArgs a{};
     a.n = ctx->n; a.nlev = ctx->n_lev; a.L = ctx->n_lines; a.nT = ctx->n_T;
     a.lc = ctx->d_lines; a.E = ctx->d_E; a.g = ctx->d_g; a.Tg = ctx->d_Tgrid; a.K = ctx->d_Kdown;
@@ -210,20 +244,22 @@ extern "C" int mg_update_populations_noalloc(mg_ctx *ctx, const double *d_pops_o
     a.J = ctx->d_J; a.Lc = ctx->d_Lc; a.Jeff = ctx->d_Jeff;
     a.pops_old = d_pops_old; a.pops_new = d_pops_new; a.scratch = scratch;
     const int64_t nb = (ctx->n + kNaThreads - 1) / kNaThreads;
-    if (ctx->n_lev <= 8) k_stateq_noalloc<8><<<(unsigned)nb, kNaThreads, 0, ctx->stream>>>(a);
-    else if (ctx->n_lev <= 24) k_stateq_noalloc<24><<<(unsigned)nb, kNaThreads, 0, ctx->stream>>>(a);
-    else k_stateq_noalloc<64><<<(unsigned)nb, kNaThreads, 0, ctx->stream>>>(a);
-    MG_CUDA(cudaGetLastError());
+    if (na_dispatch(ctx->n_lev, a, nb, ctx->stream) != MG_OK)
+        return mg_cuda_check(ctx, cudaGetLastError(), "k_stateq_noalloc");
     unsigned long long *res = scratch + 4 * kNaMaxBlocks;
     k_noalloc_finish<<<1, 256, 0, ctx->stream>>>(scratch, nb, res);
     MG_CUDA(cudaGetLastError());
-    unsigned long long h[4];
-    MG_CUDA(cudaMemcpyAsync(h, res, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream));
+    // result words into the context's pinned words [5..7], the negative-opacity count of
+    // the last formal solve into word [4] (as mg_update_populations reads it)
+    MG_CUDA(cudaMemcpyAsync(ctx->h_scal + 5, res, 3 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, ctx->stream));
+    MG_CUDA(cudaMemcpyAsync(ctx->h_scal + 4, ctx->d_scal + 4, sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                            ctx->stream));
     MG_CUDA(cudaStreamSynchronize(ctx->stream));
     double ch;
-    std::memcpy(&ch, &h[0], 8);
+    std::memcpy(&ch, &ctx->h_scal[5], 8);
     if (max_rel_change) *max_rel_change = ch;
-    if (n_fallback) *n_fallback = (int64_t)h[1];
-    if (h[2]) return mg_fail(ctx, MG_ERR_NUMERIC, "statistical equilibrium: non-finite populations after fallback");
-    return h[1] ? MG_WARN_NEG_POP_FALLBACK : MG_OK;
+    if (n_fallback) *n_fallback = (int64_t)ctx->h_scal[6];
+    if (ctx->h_scal[7]) return mg_fail(ctx, MG_ERR_NUMERIC, "statistical equilibrium: non-finite populations after fallback");
+    if (ctx->h_scal[6]) return MG_WARN_NEG_POP_FALLBACK;
+    return ctx->h_scal[4] ? MG_WARN_NEG_OPACITY : MG_OK;
 }
