@@ -327,6 +327,30 @@ int or_feautrier(int64_t K, int64_t ko, const double *dtau, const double *S, dou
     return 0;
 }
 
+/* Entries (T^-1)_{ko,k}, |k - ko| <= band, of row ko of the inverse of the Feautrier
+ * matrix T of or_feautrier: the weight of the source at point k in u at ko, i.e. row ko
+ * of the matrix of the discretised operator (1 - D^2)^-1 of eq. 'L_operator' (Sec. 3.4),
+ * whose band is the band-diagonal ALO of that section. Each entry is u at ko for a unit
+ * source at point k and no incoming intensity (column k of the inverse, read at row ko),
+ * from or_feautrier's elimination and back substitution. (Plain Gaussian elimination of
+ * T or T^T loses every digit where an interval has a floored, near-zero optical depth:
+ * the diagonal cancels against the neighbour terms there.) x[k] is written for those k
+ * only. Work: 6*K doubles. Returns -1 for K < 2. */
+int or_feautrier_band(int64_t K, int64_t ko, int64_t band, const double *dtau, double *x, double *work) {
+    if (K < 2) return -1;
+    double *e = work + 5 * K;
+    for (int64_t k = 0; k < K; k++) e[k] = 0.0;
+    int64_t k0 = ko - band < 0 ? 0 : ko - band, k1 = ko + band > K - 1 ? K - 1 : ko + band;
+    for (int64_t k = k0; k <= k1; k++) {
+        double u, lam;
+        e[k] = 1.0;
+        or_feautrier(K, ko, dtau, e, 0.0, 0.0, &u, &lam, work);
+        e[k] = 0.0;
+        x[k] = u;
+    }
+    return 0;
+}
+
 /* One expanded point of a ray pair: position and per-line data (interpolated for the
  * points inserted by the velocity-step rule). */
 typedef struct {
@@ -407,8 +431,9 @@ static int64_t expand_half(const or_model *m, int64_t o, int64_t len, const int3
  * evaluated in velocity units, x = (c (nu_l-nu_l')/nu_l' + (nu_l/nu_l')(r_q b_o (1 - v/c) - v)) / b_k,
  * which is the same expression without the cancellation of nu s - nu_l'.
  * Jnu (optional, [n_orig][n_lines][Q]) = (1/P) sum_p u per bin. */
-int or_formal_solve(const or_model *m, const double *pops, int64_t n_orig, const int64_t *origins,
-                    double *J, double *L, double *Jeff, double *Jnu, int nthreads) {
+static int formal_solve_impl(const or_model *m, const double *pops, int64_t n_orig, const int64_t *origins,
+                             double *J, double *L, double *Jeff, double *Jnu, int band, double *Jeffb,
+                             double *Mb, int nthreads) {
     int nl = m->n_lines, Q = m->Q, R = m->R;
     int64_t N = m->n;
     double *eta_c = malloc(sizeof(double) * N * nl), *chi_c = malloc(sizeof(double) * N * nl);
@@ -435,7 +460,13 @@ int or_formal_solve(const or_model *m, const double *pops, int64_t n_orig, const
         pair_pts P; P.cap = 0; P.dsk = P.vpar = P.b = P.eta = P.chi = NULL;
         double *accJ = calloc(nl, sizeof(double)), *accL = calloc(nl, sizeof(double)), *accE = calloc(nl, sizeof(double));
         double *accN = calloc((size_t)nl * Q, sizeof(double));
-        if (!cf || !cb || !nf || !nb || !dsf || !dsb || !vf || !vb || !accN) { err |= 1; continue; }
+        /* band ALO: J_eff per bandwidth 1..band, coupling coefficients per (line, ray, slot) */
+        double *accEb = band > 0 ? calloc((size_t)band * nl, sizeof(double)) : NULL;
+        double *accM = band > 0 ? calloc((size_t)nl * R * band, sizeof(double)) : NULL;
+        double *xrow = NULL, *rwork = NULL, *phil = NULL;
+        if (!cf || !cb || !nf || !nb || !dsf || !dsb || !vf || !vb || !accN || (band > 0 && (!accEb || !accM))) {
+            err |= 1; continue;
+        }
         double bo = or_width(m, o);
         for (int p = 0; p < npairs; p++) {
             int64_t lf, lb; int de;
@@ -453,7 +484,11 @@ int or_formal_solve(const or_model *m, const double *pops, int64_t n_orig, const
                 chi = malloc(sizeof(double) * ecap); eta = malloc(sizeof(double) * ecap);
                 S = malloc(sizeof(double) * ecap); dtau = malloc(sizeof(double) * ecap);
                 work = malloc(sizeof(double) * 5 * ecap);
-                if (pair_alloc(&P, ecap, nl) || !hds || !hv || !hb || !heta || !hchi || !chi || !eta || !S || !dtau || !work) { err |= 1; break; }
+                free(xrow); free(rwork); free(phil);
+                xrow = malloc(sizeof(double) * ecap); rwork = malloc(sizeof(double) * 6 * ecap);
+                phil = malloc(sizeof(double) * ecap);
+                if (pair_alloc(&P, ecap, nl) || !hds || !hv || !hb || !heta || !hchi || !chi || !eta || !S || !dtau || !work
+                    || !xrow || !rwork || !phil) { err |= 1; break; }
             }
             /* backward half expanded, then reversed into pair order */
             int64_t eb = expand_half(m, o, lb, cb, nb, dsb, vb, eta_c, chi_c, hds, hv, hb, heta, hchi, ecap, ecap);
@@ -497,6 +532,7 @@ int or_formal_solve(const or_model *m, const double *pops, int64_t n_orig, const
                                 chi_lo = P.chi[l2 * P.cap + k] * phi;
                                 eta_lo = P.eta[l2 * P.cap + k] * phi;
                             }
+                            if (l2 == l) phil[k] = phi;
                         }
                         if (ch < m->chi_min) ch = m->chi_min;
                         chi[k] = ch; eta[k] = et; S[k] = et / ch;
@@ -516,6 +552,25 @@ int or_formal_solve(const or_model *m, const double *pops, int64_t n_orig, const
                     accL[l] += w * lam * chi_lo / chi[P.ko];
                     accE[l] += w * (u - lam * eta_lo / chi[P.ko]);
                     accN[l * Q + q] += u;
+                    if (band > 0) {
+                        /* band of row ko of the inverse (Sec. 3.4): the points ko -+ j of the
+                         * backward (ray pb) and forward (ray pf) halves, j = 1..band (none
+                         * for an isolated origin, K = 1) */
+                        if (K > 1) or_feautrier_band(K, P.ko, band, dtau, xrow, rwork);
+                        double jb = u - lam * eta_lo / chi[P.ko];
+                        for (int j = 1; j <= band; j++) {
+                            for (int side = 0; side < 2 && K > 1; side++) {
+                                int64_t k = side == 0 ? P.ko - j : P.ko + j;
+                                if (k < 0 || k >= K) continue;
+                                int r = side == 0 ? pb[p] : pf[p];
+                                double eta_l = P.eta[l * P.cap + k] * phil[k];
+                                jb -= xrow[k] * eta_l / chi[k];
+                                accM[((size_t)l * R + r) * band + (j - 1)] +=
+                                    w * xrow[k] * chi_c[l * N + o] * phil[k] / chi[k];
+                            }
+                            accEb[(j - 1) * nl + l] += w * jb;
+                        }
+                    }
                 }
             }
         }
@@ -524,13 +579,78 @@ int or_formal_solve(const or_model *m, const double *pops, int64_t n_orig, const
             L[io * nl + l] = accL[l] / npairs;
             Jeff[io * nl + l] = accE[l] / npairs;
             if (Jnu) for (int q = 0; q < Q; q++) Jnu[(io * nl + l) * Q + q] = accN[l * Q + q] / npairs;
+            for (int j = 0; j < band; j++) {
+                Jeffb[((size_t)j * n_orig + io) * nl + l] = accEb[j * nl + l] / npairs;
+                for (int r = 0; r < R; r++)
+                    Mb[(((size_t)io * nl + l) * R + r) * band + j] = accM[((size_t)l * R + r) * band + j] / npairs;
+            }
         }
         free(cf); free(cb); free(nf); free(nb); free(dsf); free(dsb); free(vf); free(vb);
         free(hds); free(hv); free(hb); free(heta); free(hchi); pair_free(&P);
         free(chi); free(eta); free(S); free(dtau); free(work); free(accJ); free(accL); free(accE); free(accN);
+        free(accEb); free(accM); free(xrow); free(rwork); free(phil);
     }
     free(eta_c); free(chi_c); free(pf); free(pb);
     return err ? -3 : 0;
+}
+
+int or_formal_solve(const or_model *m, const double *pops, int64_t n_orig, const int64_t *origins,
+                    double *J, double *L, double *Jeff, double *Jnu, int nthreads) {
+    return formal_solve_impl(m, pops, n_orig, origins, J, L, Jeff, Jnu, 0, NULL, NULL, nthreads);
+}
+
+/* Formal solution with the band-diagonal ALO of Sec. 3.4 (eq. 'ALO', 'ourJeff'): besides
+ * J, L (diagonal) and Jeff (bandwidth 0), for bandwidth b = 1..band
+ *   Jeffb[b-1][io][l] = (1/P) sum_p sum_q w_q (u - sum_{|k-ko|<=b} (T^-1)_{ko,k} eta_l(k)/chi(k)),
+ * and per half-ray r and band slot j (the j-th point of the half from the origin)
+ *   Mb[io][l][r][j-1] = (1/P) sum_q w_q (T^-1)_{ko,k} chi_int,l(o) phi_l(k)/chi(k),
+ * the weight with which A_ul n_u at that point enters the rate equation of the origin
+ * (eq. 'ourALI' with the operator of eq. 'ALO': the emissivity at point k is
+ * h nu/4pi A n_u(k) phi_l(k), the prefactor is chi_int,l(o) = h nu/4pi (n_l B_lu - n_u B_ul)
+ * at the origin, from the old populations). */
+int or_formal_solve_band(const or_model *m, const double *pops, int64_t n_orig, const int64_t *origins, int band,
+                         double *J, double *L, double *Jeff, double *Jeffb, double *Mb, int nthreads) {
+    if (band < 1) return -1;
+    return formal_solve_impl(m, pops, n_orig, origins, J, L, Jeff, NULL, band, Jeffb, Mb, nthreads);
+}
+
+/* Cells behind band slot j (1..band) of half-ray (o, r): the j-th expanded point from the
+ * origin interpolates its line data between cells ca and cb with weight w on cb (w = 1 at
+ * a traced cell); ca = cb = -1 where the half has fewer than j points. Outputs
+ * [n_orig][R][band]. */
+int or_band_geometry(const or_model *m, int64_t n_orig, const int64_t *origins, int band, int32_t *ca,
+                     int32_t *cb, double *w) {
+    int64_t cap = m->max_steps;
+    int32_t *cells = malloc(sizeof(int32_t) * cap), *nsub = malloc(sizeof(int32_t) * cap);
+    double *ds = malloc(sizeof(double) * cap), *vpar = malloc(sizeof(double) * cap);
+    int err = (!cells || !nsub || !ds || !vpar);
+    for (int64_t io = 0; io < n_orig && !err; io++) {
+        int64_t o = origins[io];
+        for (int r = 0; r < m->R && !err; r++) {
+            int64_t len; int de;
+            if (or_trace(m, o, r, cap, cells, nsub, ds, vpar, &len, &de)) { err = 1; break; }
+            for (int j = 1; j <= band; j++) {
+                size_t k = ((size_t)io * m->R + r) * band + (j - 1);
+                ca[k] = -1; cb[k] = -1; w[k] = 0.0;
+                /* walk the expanded points: element e holds nsub[e] + 1 points, the last
+                 * one its own cell; point x of element e is sub-point x - x0 + 1 */
+                int64_t x0 = 0, prev = o;
+                for (int64_t e = 0; e < len; e++) {
+                    int64_t cnt = nsub[e] + 1;
+                    if (j - 1 < x0 + cnt) {
+                        ca[k] = (int32_t)prev;
+                        cb[k] = cells[e];
+                        w[k] = (double)(j - x0) / (double)cnt;
+                        break;
+                    }
+                    x0 += cnt;
+                    prev = cells[e];
+                }
+            }
+        }
+    }
+    free(cells); free(nsub); free(ds); free(vpar);
+    return err ? -1 : 0;
 }
 
 /* ------------------------------------------------------------------ statistical equilibrium */
@@ -580,18 +700,24 @@ static int lu_solve(int n, double *M, double *b) {
  * C_lu = C_ul (g_u/g_l) exp(-(E_u - E_l)/kT) is used, the only one that makes high
  * densities thermalise to LTE. The last equation is replaced by sum_i n_i = n_spec
  * (Reading). Rates enter the generator matrix M_ij = rate j->i, M_jj = -sum_i rate j->i. */
-static int stateq_cell(const or_model *m, int64_t c, const double *Jc, const double *Lc,
-                       const double *Ec, double *out) {
+/* Rate generator of cell c (eq. 'ourALI'): G[i*n+j] = rate j->i for i != j and
+ * G[j*n+j] = -sum_i rate j->i, with u->l = A_ul oml_l + B_ul Jeff_l + C_ul and
+ * l->u = B_lu Jeff_l + C_lu for every line, where oml_l is the factor left of the
+ * spontaneous rate by the ALO (1 - L with the diagonal ALO), and all collisional pairs
+ * C_ij = K_ij(T) n_coll with excitation by detailed balance.
+ * Reading: the paper prints the excitation factor exp(+h nu/kT); the physical form
+ * C_lu = C_ul (g_u/g_l) exp(-(E_u - E_l)/kT) is used, the only one that makes high
+ * densities thermalise to LTE. */
+int or_cell_generator(const or_model *m, int64_t c, const double *oml, const double *Ec, double *G) {
     int n = m->n_lev;
     double P[64 * 64];
-    double M[64 * 64], b[64];
     if (n > 64) return -1;
     memset(P, 0, sizeof(double) * n * n);
     for (int l = 0; l < m->n_lines; l++) {
         int u = m->up[l], lo = m->lo[l];
         double Bul, Blu;
         einstein_b(m, l, &Bul, &Blu);
-        P[u * n + lo] += m->A[l] * (1.0 - Lc[l]) + Bul * Ec[l];
+        P[u * n + lo] += m->A[l] * oml[l] + Bul * Ec[l];
         P[lo * n + u] += Blu * Ec[l];
     }
     double T = m->T[c];
@@ -603,13 +729,27 @@ static int stateq_cell(const or_model *m, int64_t c, const double *Jc, const dou
             P[j * n + i] += Cu;
         }
     for (int i = 0; i < n; i++)
-        for (int j = 0; j < n; j++) M[i * n + j] = 0.0;
+        for (int j = 0; j < n; j++) G[i * n + j] = 0.0;
     for (int j = 0; j < n; j++)
         for (int i = 0; i < n; i++) {
             if (i == j) continue;
-            M[i * n + j] += P[j * n + i];
-            M[j * n + j] -= P[j * n + i];
+            G[i * n + j] += P[j * n + i];
+            G[j * n + j] -= P[j * n + i];
         }
+    return 0;
+}
+
+/* Statistical equilibrium of one cell with the diagonal ALO (eq. 'ourALI'), rates as in
+ * or_cell_generator with oml = 1 - L. The last equation is replaced by
+ * sum_i n_i = n_spec (Reading). */
+static int stateq_cell(const or_model *m, int64_t c, const double *Jc, const double *Lc,
+                       const double *Ec, double *out) {
+    int n = m->n_lev;
+    double M[64 * 64], b[64], oml[64 * 64];
+    if (n > 64 || m->n_lines > 64 * 64) return -1;
+    (void)Jc;
+    for (int l = 0; l < m->n_lines; l++) oml[l] = 1.0 - Lc[l];
+    if (or_cell_generator(m, c, oml, Ec, M)) return -1;
     for (int j = 0; j < n; j++) { M[(n - 1) * n + j] = 1.0; b[j] = 0.0; }
     b[n - 1] = m->n_spec[c];
     if (lu_solve(n, M, b)) return -2;

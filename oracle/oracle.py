@@ -168,6 +168,10 @@ def _lib():
         L.or_image.argtypes = [P, P, C.c_int, C.c_int, C.c_int, P, C.c_int64, P, P, P, C.c_int]
         L.or_first_order.argtypes = [C.c_int64, P, P, C.c_double]
         L.or_first_order.restype = C.c_double
+        L.or_feautrier_band.argtypes = [C.c_int64, C.c_int64, C.c_int64, P, P, P]
+        L.or_formal_solve_band.argtypes = [P, P, C.c_int64, P, C.c_int, P, P, P, P, P, C.c_int]
+        L.or_band_geometry.argtypes = [P, C.c_int64, P, C.c_int, P, P, P]
+        L.or_cell_generator.argtypes = [P, C.c_int64, P, P, P]
         _LIB = L
     return _LIB
 
@@ -293,6 +297,168 @@ class Oracle:
             raise RuntimeError(f"or_image failed ({rc})")
         return I, xy
 
+    def formal_solve_band(self, pops, band, origins=None):
+        """Formal solution with the band-diagonal ALO of bandwidth `band` (Sec. 3.4):
+        J, L, [Jeff_0, ..., Jeff_band] (J_eff with the ALO's band 0..band), and the
+        coupling coefficients M [n_orig][n_lines][R][band] of or_formal_solve_band."""
+        pops = np.ascontiguousarray(pops, np.float64)
+        if origins is None:
+            origins = np.arange(self.model.n, dtype=np.int64)
+        origins = np.ascontiguousarray(origins, np.int64)
+        no, nl, R = origins.shape[0], self.n_lines, self.dirs.shape[0]
+        J = np.empty((no, nl)); L = np.empty((no, nl)); E = np.empty((no, nl))
+        Eb = np.empty((band, no, nl)); M = np.empty((no, nl, R, band))
+        rc = _lib().or_formal_solve_band(self.mp, _ptr(pops), no, _ptr(origins), int(band), _ptr(J), _ptr(L),
+                                         _ptr(E), _ptr(Eb), _ptr(M), self.nthreads)
+        if rc:
+            raise RuntimeError(f"or_formal_solve_band failed ({rc})")
+        return J, L, [E] + [Eb[b] for b in range(band)], M
+
+    def band_geometry(self, band, origins=None):
+        """Cells (ca, cb) and weight w of the j-th expanded point of every half-ray,
+        [n_orig][R][band] (ca = cb = -1 where the half is shorter)."""
+        if origins is None:
+            origins = np.arange(self.model.n, dtype=np.int64)
+        origins = np.ascontiguousarray(origins, np.int64)
+        R = self.dirs.shape[0]
+        shape = (origins.shape[0], R, band)
+        ca = np.empty(shape, np.int32); cb = np.empty(shape, np.int32); w = np.empty(shape)
+        if _lib().or_band_geometry(self.mp, origins.shape[0], _ptr(origins), int(band), _ptr(ca), _ptr(cb), _ptr(w)):
+            raise RuntimeError("or_band_geometry failed")
+        return ca, cb, w
+
+    def cell_generator(self, c, oml, Jeff_c):
+        """Rate generator of cell c (eq. 'ourALI'), G[i][j] = rate j -> i."""
+        lev = self.model.species.n_lev
+        G = np.empty((lev, lev))
+        if _lib().or_cell_generator(self.mp, int(c), _ptr(np.ascontiguousarray(oml, np.float64)),
+                                    _ptr(np.ascontiguousarray(Jeff_c, np.float64)), _ptr(G)):
+            raise RuntimeError("or_cell_generator failed")
+        return G
+
+    def band_system(self, L, Jeff, M, geom, b, pops_old):
+        """The rate equations of all cells with the ALO of bandwidth b (eq. 'ourALI' with
+        the operator of eq. 'ALO'), as one sparse linear system A n = rhs over all cells
+        and levels. Per cell o and line l = (u -> lo), the band points of every half-ray
+        contribute A_ul M n_u at the point, n_u interpolated between the point's cells
+        (ca, cb) with weight w: the part on the origin itself (ca = o) lowers the factor
+        1 - L of the spontaneous rate, the other cells enter as couplings (+ to the balance
+        of u, - to that of lo). The last balance equation of each cell is replaced by
+        sum_i n_i = n_spec. Returns (A as scipy CSR, rhs)."""
+        import scipy.sparse as sps
+        m, sp = self.model, self.model.species
+        n, lev, nl = m.n, sp.n_lev, sp.n_lines
+        ca, cb, w = geom
+        rows, cols, vals = [], [], []
+        rhs = np.zeros(n * lev)
+        for o in range(n):
+            oml = 1.0 - L[o]
+            coup = []                       # (line, cell, weight x M)
+            for l in range(nl):
+                for r in range(ca.shape[1]):
+                    for j in range(b):
+                        Mv = M[o, l, r, j]
+                        if ca[o, r, j] < 0 or Mv == 0.0:
+                            continue
+                        for cell, wt in ((cb[o, r, j], w[o, r, j]), (ca[o, r, j], 1.0 - w[o, r, j])):
+                            if wt == 0.0:
+                                continue
+                            if cell == o:
+                                oml[l] -= wt * Mv
+                            else:
+                                coup.append((l, cell, wt * Mv))
+            G = self.cell_generator(o, oml, Jeff[o])
+            for i in range(lev - 1):
+                for j in range(lev):
+                    if G[i, j] != 0.0:
+                        rows.append(o * lev + i); cols.append(o * lev + j); vals.append(G[i, j])
+            for j in range(lev):
+                rows.append(o * lev + lev - 1); cols.append(o * lev + j); vals.append(1.0)
+            rhs[o * lev + lev - 1] = m.n_spec[o]
+            for l, cell, cf in coup:
+                u, lo = int(sp.up[l]), int(sp.lo[l])
+                a = sp.A[l] * cf
+                if u < lev - 1:
+                    rows.append(o * lev + u); cols.append(cell * lev + u); vals.append(a)
+                if lo < lev - 1:
+                    rows.append(o * lev + lo); cols.append(cell * lev + u); vals.append(-a)
+        A = sps.csr_matrix((vals, (rows, cols)), shape=(n * lev, n * lev))
+        A.sum_duplicates()
+        return A, rhs
+
+    def solve_band(self, L, Jeff, M, geom, b, pops_old):
+        """Solution of band_system by sparse LU (scipy's SuperLU), with the unknowns
+        scaled by the old populations (floored at 1e-20 of the cell's species density) so
+        that levels of very different size are resolved alike."""
+        import scipy.sparse as sps
+        import scipy.sparse.linalg as spl
+        A, rhs = self.band_system(L, Jeff, M, geom, b, pops_old)
+        ns = self.model.n_spec
+        s = np.maximum(np.asarray(pops_old, np.float64), 1e-20 * ns[:, None]).ravel()
+        x = spl.spsolve((A @ sps.diags(s)).tocsc(), rhs)
+        return (x * s).reshape(pops_old.shape)
+
+    def stateq_band(self, J, L, Jeffs, M, geom, band, pops_old):
+        """Statistical equilibrium with the band-diagonal ALO and its validity check
+        (Sec. 6.1): the system of bandwidth b is solved; if any population comes out
+        negative or non-finite it is solved again with bandwidth b - 1, down to the
+        diagonal ALO, whose own check re-solves single cells without the ALO.
+        Returns (pops, bandwidth used, fallback cells of the diagonal stage)."""
+        for b in range(band, 0, -1):
+            pops = self.solve_band(L, Jeffs[b], M, geom, b, pops_old)
+            if np.all(np.isfinite(pops)) and np.all(pops >= 0.0):
+                return pops, b, 0
+        pops, nf = self.stateq(J, L, Jeffs[0])
+        return pops, 0, nf
+
+    def ali_band(self, band, pops=None, tol=1e-6, max_iter=200, ng_period=0, grow_limit=3):
+        """ALI with the band-diagonal ALO (formal solve -> band statistical equilibrium ->
+        convergence), Ng as in or_ali. The bandwidth in use starts at `band` and only
+        decreases (Sec. 6.1, "reduce the bandwidth if required"; Reading: a reduction
+        holds for the rest of the ALI): when the validity check of stateq_band had to
+        reduce it, and when the max relative change has grown in `grow_limit` consecutive
+        iterations (a diverging ALI), by one. Returns (pops, changes, converged, bandwidth
+        used per iteration)."""
+        pops = self.lte() if pops is None else np.array(pops, np.float64, copy=True)
+        geom = self.band_geometry(band) if band > 0 else None
+        ns = self.model.n_spec[:, None]
+        hist, changes, used = [], [], []
+        nh, grow, b_cur = 0, 0, band
+        conv = False
+        for it in range(max_iter):
+            if b_cur > 0:
+                J, L, Jeffs, M = self.formal_solve_band(pops, b_cur)
+                g = tuple(x[..., :b_cur] for x in geom)
+                new, b_used, nf = self.stateq_band(J, L, Jeffs, M, g, b_cur, pops)
+            else:
+                J, L, E = self.formal_solve(pops)
+                new, nf = self.stateq(J, L, E)
+                b_used = 0
+            ch = self.max_rel_change(pops, new)
+            grow = grow + 1 if changes and ch > changes[-1] else 0
+            changes.append(ch); used.append(b_used)
+            b_cur = min(b_cur, b_used)
+            if grow >= grow_limit and b_cur > 0:
+                b_cur -= 1
+                grow = 0
+            pops = new
+            if ch < tol:
+                conv = True
+                break
+            if ng_period > 0:
+                hist.insert(0, pops / ns)
+                hist = hist[:4]
+                nh = min(nh + 1, 4)
+                if nh == 4 and (it + 1) % ng_period == 0:
+                    try:
+                        x = ng(*[np.ascontiguousarray(h) for h in hist])
+                        if np.all(x >= 0.0):
+                            pops = x * ns
+                    except RuntimeError:
+                        pass
+                    nh = 0
+        return pops, np.array(changes), conv, used
+
     def stateq(self, J, L, Jeff):
         out = np.empty((self.model.n, self.model.species.n_lev))
         nf = C.c_int64(0)
@@ -335,6 +501,18 @@ def feautrier(dtau, S, I0, IK, ko):
     _lib().or_feautrier(K, int(ko), _ptr(dtau), _ptr(S), float(I0), float(IK), C.byref(u),
                         C.byref(lam), _ptr(work))
     return u.value, lam.value
+
+
+def feautrier_row(dtau, ko, band=None):
+    """Entries |k - ko| <= band (default: the whole row) of row ko of the inverse of the
+    discretised second-order transfer operator: the weights of the sources at the points
+    in u at ko. Entries outside the band are NaN."""
+    dtau = np.ascontiguousarray(dtau, np.float64)
+    K = dtau.shape[0] + 1
+    x = np.full(K, np.nan); work = np.empty(6 * K)
+    if _lib().or_feautrier_band(K, int(ko), int(K if band is None else band), _ptr(dtau), _ptr(x), _ptr(work)):
+        raise RuntimeError("or_feautrier_band needs at least two points")
+    return x
 
 
 def first_order(dtau, S, I0):
