@@ -360,6 +360,8 @@ typedef struct {
     double *b;        /* [K] velocity width */
     double *eta;      /* [n_lines][K] eta_int */
     double *chi;      /* [n_lines][K] chi_int */
+    int64_t *ca, *cb; /* [K] cells the point interpolates between ... */
+    double *w;        /* [K] ... with weight w on cb */
 } pair_pts;
 
 static int pair_alloc(pair_pts *p, int64_t cap, int nl) {
@@ -369,10 +371,12 @@ static int pair_alloc(pair_pts *p, int64_t cap, int nl) {
     p->b = malloc(sizeof(double) * cap);
     p->eta = malloc(sizeof(double) * cap * nl);
     p->chi = malloc(sizeof(double) * cap * nl);
-    return (p->dsk && p->vpar && p->b && p->eta && p->chi) ? 0 : -1;
+    p->ca = malloc(sizeof(int64_t) * cap); p->cb = malloc(sizeof(int64_t) * cap);
+    p->w = malloc(sizeof(double) * cap);
+    return (p->dsk && p->vpar && p->b && p->eta && p->chi && p->ca && p->cb && p->w) ? 0 : -1;
 }
 static void pair_free(pair_pts *p) {
-    free(p->dsk); free(p->vpar); free(p->b); free(p->eta); free(p->chi);
+    free(p->dsk); free(p->vpar); free(p->b); free(p->eta); free(p->chi); free(p->ca); free(p->cb); free(p->w);
 }
 
 /* Per-cell line integrals for all cells (eq. 'lines' without the profile). */
@@ -389,7 +393,7 @@ static int64_t expand_half(const or_model *m, int64_t o, int64_t len, const int3
                            const int32_t *nsub, const double *ds, const double *vpar,
                            const double *eta_c, const double *chi_c,
                            double *o_ds, double *o_v, double *o_b, double *o_eta, double *o_chi,
-                           int64_t stride, int64_t cap) {
+                           int64_t stride, int64_t cap, int64_t *o_ca, int64_t *o_cb, double *o_w) {
     int nl = m->n_lines;
     int64_t cnt = 0;
     int64_t prev = o;
@@ -403,6 +407,7 @@ static int64_t expand_half(const or_model *m, int64_t o, int64_t len, const int3
             o_ds[cnt] = ds[e] / (double)(ns + 1);
             o_v[cnt] = (1.0 - w) * pv + w * vpar[e];
             o_b[cnt] = (1.0 - w) * or_width(m, prev) + w * or_width(m, c);
+            if (o_ca) { o_ca[cnt] = prev; o_cb[cnt] = c; o_w[cnt] = w; }
             for (int l = 0; l < nl; l++) {
                 o_eta[l * stride + cnt] = (1.0 - w) * eta_c[l * m->n + prev] + w * eta_c[l * m->n + c];
                 o_chi[l * stride + cnt] = (1.0 - w) * chi_c[l * m->n + prev] + w * chi_c[l * m->n + c];
@@ -431,9 +436,24 @@ static int64_t expand_half(const or_model *m, int64_t o, int64_t len, const int3
  * evaluated in velocity units, x = (c (nu_l-nu_l')/nu_l' + (nu_l/nu_l')(r_q b_o (1 - v/c) - v)) / b_k,
  * which is the same expression without the cancellation of nu s - nu_l'.
  * Jnu (optional, [n_orig][n_lines][Q]) = (1/P) sum_p u per bin. */
+/* Mean intensity of cell c in the bins of line l at offset r (in units of the width)
+ * from the line centre: linear interpolation of Jnu[c][l][q] between the Gauss-Hermite
+ * roots r_q (ascending), the outermost values beyond them. */
+static double spectrum_at(const or_model *m, const double *Jnu, int64_t c, int l, double r) {
+    const double *Jc = Jnu + ((size_t)c * m->n_lines + l) * m->Q;
+    const double *x = m->roots;
+    int Q = m->Q;
+    if (Q == 1 || r <= x[0]) return Jc[0];
+    if (r >= x[Q - 1]) return Jc[Q - 1];
+    int q = 0;
+    while (x[q + 1] <= r) q++;
+    double t = (r - x[q]) / (x[q + 1] - x[q]);
+    return Jc[q] + t * (Jc[q + 1] - Jc[q]);
+}
+
 static int formal_solve_impl(const or_model *m, const double *pops, int64_t n_orig, const int64_t *origins,
                              double *J, double *L, double *Jeff, double *Jnu, int band, double *Jeffb,
-                             double *Mb, int nthreads) {
+                             double *Mb, const double *chi_sca, const double *Jsca, int nthreads) {
     int nl = m->n_lines, Q = m->Q, R = m->R;
     int64_t N = m->n;
     double *eta_c = malloc(sizeof(double) * N * nl), *chi_c = malloc(sizeof(double) * N * nl);
@@ -455,9 +475,10 @@ static int formal_solve_impl(const or_model *m, const double *pops, int64_t n_or
         double *dsf = malloc(sizeof(double) * cap), *dsb = malloc(sizeof(double) * cap);
         double *vf = malloc(sizeof(double) * cap), *vb = malloc(sizeof(double) * cap);
         int64_t ecap = 0;
-        double *hds = NULL, *hv = NULL, *hb = NULL, *heta = NULL, *hchi = NULL;
+        double *hds = NULL, *hv = NULL, *hb = NULL, *heta = NULL, *hchi = NULL, *hw = NULL;
+        int64_t *hca = NULL, *hcb = NULL;
         double *chi = NULL, *eta = NULL, *S = NULL, *dtau = NULL, *work = NULL;
-        pair_pts P; P.cap = 0; P.dsk = P.vpar = P.b = P.eta = P.chi = NULL;
+        pair_pts P; P.cap = 0; P.dsk = P.vpar = P.b = P.eta = P.chi = P.w = NULL; P.ca = P.cb = NULL;
         double *accJ = calloc(nl, sizeof(double)), *accL = calloc(nl, sizeof(double)), *accE = calloc(nl, sizeof(double));
         double *accN = calloc((size_t)nl * Q, sizeof(double));
         /* band ALO: J_eff per bandwidth 1..band, coupling coefficients per (line, ray, slot) */
@@ -478,8 +499,9 @@ static int formal_solve_impl(const or_model *m, const double *pops, int64_t n_or
             if (need > ecap) {
                 ecap = 2 * need;
                 free(hds); free(hv); free(hb); free(heta); free(hchi); pair_free(&P);
-                free(chi); free(eta); free(S); free(dtau); free(work);
+                free(chi); free(eta); free(S); free(dtau); free(work); free(hca); free(hcb); free(hw);
                 hds = malloc(sizeof(double) * ecap); hv = malloc(sizeof(double) * ecap); hb = malloc(sizeof(double) * ecap);
+                hca = malloc(sizeof(int64_t) * ecap); hcb = malloc(sizeof(int64_t) * ecap); hw = malloc(sizeof(double) * ecap);
                 heta = malloc(sizeof(double) * ecap * nl); hchi = malloc(sizeof(double) * ecap * nl);
                 chi = malloc(sizeof(double) * ecap); eta = malloc(sizeof(double) * ecap);
                 S = malloc(sizeof(double) * ecap); dtau = malloc(sizeof(double) * ecap);
@@ -488,27 +510,32 @@ static int formal_solve_impl(const or_model *m, const double *pops, int64_t n_or
                 xrow = malloc(sizeof(double) * ecap); rwork = malloc(sizeof(double) * 6 * ecap);
                 phil = malloc(sizeof(double) * ecap);
                 if (pair_alloc(&P, ecap, nl) || !hds || !hv || !hb || !heta || !hchi || !chi || !eta || !S || !dtau || !work
-                    || !xrow || !rwork || !phil) { err |= 1; break; }
+                    || !xrow || !rwork || !phil || !hca || !hcb || !hw) { err |= 1; break; }
             }
             /* backward half expanded, then reversed into pair order */
-            int64_t eb = expand_half(m, o, lb, cb, nb, dsb, vb, eta_c, chi_c, hds, hv, hb, heta, hchi, ecap, ecap);
+            int64_t eb = expand_half(m, o, lb, cb, nb, dsb, vb, eta_c, chi_c, hds, hv, hb, heta, hchi, ecap, ecap,
+                                     hca, hcb, hw);
             if (eb < 0) { err |= 4; break; }
             int64_t K = 0;
             for (int64_t k = eb - 1; k >= 0; k--) {
                 P.vpar[K] = hv[k]; P.b[K] = hb[k];
+                P.ca[K] = hca[k]; P.cb[K] = hcb[k]; P.w[K] = hw[k];
                 for (int l = 0; l < nl; l++) { P.eta[l * P.cap + K] = heta[l * ecap + k]; P.chi[l * P.cap + K] = hchi[l * ecap + k]; }
                 P.dsk[K] = hds[k];  /* distance from this point to the next one towards the origin */
                 K++;
             }
             P.ko = K;
             P.vpar[K] = 0.0; P.b[K] = bo;
+            P.ca[K] = o; P.cb[K] = o; P.w[K] = 0.0;
             for (int l = 0; l < nl; l++) { P.eta[l * P.cap + K] = eta_c[l * N + o]; P.chi[l * P.cap + K] = chi_c[l * N + o]; }
             K++;
-            int64_t ef = expand_half(m, o, lf, cf, nf, dsf, vf, eta_c, chi_c, hds, hv, hb, heta, hchi, ecap, ecap);
+            int64_t ef = expand_half(m, o, lf, cf, nf, dsf, vf, eta_c, chi_c, hds, hv, hb, heta, hchi, ecap, ecap,
+                                     hca, hcb, hw);
             if (ef < 0) { err |= 4; break; }
             for (int64_t k = 0; k < ef; k++) {
                 P.dsk[K - 1] = hds[k];
                 P.vpar[K] = hv[k]; P.b[K] = hb[k];
+                P.ca[K] = hca[k]; P.cb[K] = hcb[k]; P.w[K] = hw[k];
                 for (int l = 0; l < nl; l++) { P.eta[l * P.cap + K] = heta[l * ecap + k]; P.chi[l * P.cap + K] = hchi[l * ecap + k]; }
                 K++;
             }
@@ -533,6 +560,18 @@ static int formal_solve_impl(const or_model *m, const double *pops, int64_t n_or
                                 eta_lo = P.eta[l2 * P.cap + k] * phi;
                             }
                             if (l2 == l) phil[k] = phi;
+                        }
+                        if (chi_sca) {
+                            /* isotropic coherent scattering (Sec. 3.3, eq. 'GFE' with Psi- = 0):
+                             * opacity chi_sca, emissivity chi_sca J at the comoving frequency,
+                             * both interpolated between the point's cells */
+                            double wk = P.w[k];
+                            double r = (aq * (1.0 - v / C_LIGHT) - v) / bk;
+                            double xs = (1.0 - wk) * chi_sca[P.ca[k]] + wk * chi_sca[P.cb[k]];
+                            double Jk = (1.0 - wk) * spectrum_at(m, Jsca, P.ca[k], l, r) +
+                                        wk * spectrum_at(m, Jsca, P.cb[k], l, r);
+                            ch += xs;
+                            et += xs * Jk;
                         }
                         if (ch < m->chi_min) ch = m->chi_min;
                         chi[k] = ch; eta[k] = et; S[k] = et / ch;
@@ -586,7 +625,7 @@ static int formal_solve_impl(const or_model *m, const double *pops, int64_t n_or
             }
         }
         free(cf); free(cb); free(nf); free(nb); free(dsf); free(dsb); free(vf); free(vb);
-        free(hds); free(hv); free(hb); free(heta); free(hchi); pair_free(&P);
+        free(hds); free(hv); free(hb); free(heta); free(hchi); pair_free(&P); free(hca); free(hcb); free(hw);
         free(chi); free(eta); free(S); free(dtau); free(work); free(accJ); free(accL); free(accE); free(accN);
         free(accEb); free(accM); free(xrow); free(rwork); free(phil);
     }
@@ -596,7 +635,27 @@ static int formal_solve_impl(const or_model *m, const double *pops, int64_t n_or
 
 int or_formal_solve(const or_model *m, const double *pops, int64_t n_orig, const int64_t *origins,
                     double *J, double *L, double *Jeff, double *Jnu, int nthreads) {
-    return formal_solve_impl(m, pops, n_orig, origins, J, L, Jeff, Jnu, 0, NULL, NULL, nthreads);
+    return formal_solve_impl(m, pops, n_orig, origins, J, L, Jeff, Jnu, 0, NULL, NULL, NULL, NULL, nthreads);
+}
+
+/* Formal solution with isotropic, coherent scattering (Sec. 2.1 eq. 'RTE', Sec. 3.3 eq.
+ * 'GFE'): a frequency-independent scattering opacity chi_sca[n] per cell, scattering
+ * isotropically and without a change of frequency in the comoving frame. Then the
+ * scattering opacity is the same up and down the ray (chi+ = chi_sca, chi- = 0), the
+ * redistribution does not depend on the outgoing direction (Phi- = 0, so Psi- = 0), and
+ * Psi+ = chi_sca J_nu: eq. 'GFE' for u is the second-order equation with opacity
+ * chi + chi_sca and source (eta + chi_sca J)/(chi + chi_sca). As Sec. 3.3 prescribes, the
+ * right-hand side is evaluated with the solution of the previous iteration: Jsca
+ * [n][n_lines][Q] is the previous mean intensity of every cell in its own bins; at a
+ * point of a ray it is read at the point's comoving offset from the line centre, in
+ * units of the point's width, from the bins of the point's cells (spectrum_at),
+ * interpolated between the cells like the line data. Jnu [n_orig][n_lines][Q] receives
+ * the new one. Readings: the bins of line l carry the radiation scattered in line l's own
+ * bins; chi_sca is interpolated like the line data at inserted points. */
+int or_formal_solve_sca(const or_model *m, const double *pops, int64_t n_orig, const int64_t *origins,
+                        const double *chi_sca, const double *Jsca, double *J, double *L, double *Jeff, double *Jnu,
+                        int nthreads) {
+    return formal_solve_impl(m, pops, n_orig, origins, J, L, Jeff, Jnu, 0, NULL, NULL, chi_sca, Jsca, nthreads);
 }
 
 /* Formal solution with the band-diagonal ALO of Sec. 3.4 (eq. 'ALO', 'ourJeff'): besides
@@ -611,7 +670,7 @@ int or_formal_solve(const or_model *m, const double *pops, int64_t n_orig, const
 int or_formal_solve_band(const or_model *m, const double *pops, int64_t n_orig, const int64_t *origins, int band,
                          double *J, double *L, double *Jeff, double *Jeffb, double *Mb, int nthreads) {
     if (band < 1) return -1;
-    return formal_solve_impl(m, pops, n_orig, origins, J, L, Jeff, NULL, band, Jeffb, Mb, nthreads);
+    return formal_solve_impl(m, pops, n_orig, origins, J, L, Jeff, NULL, band, Jeffb, Mb, NULL, NULL, nthreads);
 }
 
 /* Cells behind band slot j (1..band) of half-ray (o, r): the j-th expanded point from the
@@ -669,37 +728,6 @@ static double k_down(const or_model *m, int i, int j, double T) {
     return k[a] + t * (k[a + 1] - k[a]);
 }
 
-/* Dense solve with LU decomposition and partial pivoting (in place). */
-static int lu_solve(int n, double *M, double *b) {
-    for (int c = 0; c < n; c++) {
-        int piv = c;
-        for (int r = c + 1; r < n; r++) if (fabs(M[r * n + c]) > fabs(M[piv * n + c])) piv = r;
-        if (M[piv * n + c] == 0.0) return -1;
-        if (piv != c) {
-            for (int k = 0; k < n; k++) { double t = M[c * n + k]; M[c * n + k] = M[piv * n + k]; M[piv * n + k] = t; }
-            double t = b[c]; b[c] = b[piv]; b[piv] = t;
-        }
-        for (int r = c + 1; r < n; r++) {
-            double f = M[r * n + c] / M[c * n + c];
-            for (int k = c; k < n; k++) M[r * n + k] -= f * M[c * n + k];
-            b[r] -= f * b[c];
-        }
-    }
-    for (int r = n - 1; r >= 0; r--) {
-        double s = b[r];
-        for (int k = r + 1; k < n; k++) s -= M[r * n + k] * b[k];
-        b[r] = s / M[r * n + r];
-    }
-    return 0;
-}
-
-/* Statistical equilibrium of one cell with the diagonal ALO (eq. 'ourALI'):
- * rate u->l = A_ul (1 - L) + B_ul Jeff + C_ul, rate l->u = B_lu Jeff + C_lu, all
- * collisional pairs with C_ij = K_ij(T) n_coll and excitation by detailed balance.
- * Reading: the paper prints the excitation factor exp(+h nu/kT); the physical form
- * C_lu = C_ul (g_u/g_l) exp(-(E_u - E_l)/kT) is used, the only one that makes high
- * densities thermalise to LTE. The last equation is replaced by sum_i n_i = n_spec
- * (Reading). Rates enter the generator matrix M_ij = rate j->i, M_jj = -sum_i rate j->i. */
 /* Rate generator of cell c (eq. 'ourALI'): G[i*n+j] = rate j->i for i != j and
  * G[j*n+j] = -sum_i rate j->i, with u->l = A_ul oml_l + B_ul Jeff_l + C_ul and
  * l->u = B_lu Jeff_l + C_lu for every line, where oml_l is the factor left of the
@@ -739,27 +767,95 @@ int or_cell_generator(const or_model *m, int64_t c, const double *oml, const dou
     return 0;
 }
 
+/* Double-double numbers (hi + lo, |lo| <= ulp(hi)/2) from error-free transformations
+ * (Knuth's TwoSum, the fused multiply-add for the product's error; Dekker 1971): about
+ * 106 bits of mantissa, enough to resolve levels whose populations span thirty decades. */
+typedef struct { double hi, lo; } dd;
+static dd dd_from(double a) { dd r = {a, 0.0}; return r; }
+static dd dd_norm(double s, double e) { double h = s + e; dd r = {h, e - (h - s)}; return r; }
+static dd dd_add(dd a, dd b) {
+    double s = a.hi + b.hi, bb = s - a.hi, e = (a.hi - (s - bb)) + (b.hi - bb);
+    return dd_norm(s, e + a.lo + b.lo);
+}
+static dd dd_neg(dd a) { dd r = {-a.hi, -a.lo}; return r; }
+static dd dd_sub(dd a, dd b) { return dd_add(a, dd_neg(b)); }
+static dd dd_mul(dd a, dd b) {
+    double p = a.hi * b.hi, e = fma(a.hi, b.hi, -p);
+    return dd_norm(p, e + (a.hi * b.lo + a.lo * b.hi));
+}
+static dd dd_div(dd a, dd b) {
+    double q1 = a.hi / b.hi;
+    dd r = dd_sub(a, dd_mul(dd_from(q1), b));
+    double q2 = r.hi / b.hi;
+    r = dd_sub(r, dd_mul(dd_from(q2), b));
+    double q3 = r.hi / b.hi;
+    return dd_add(dd_norm(q1, q2), dd_from(q3));
+}
+
+/* Gaussian elimination with partial pivoting in double-double arithmetic (in place). */
+static int lu_solve_dd(int n, dd *M, dd *b) {
+    for (int c = 0; c < n; c++) {
+        int piv = c;
+        for (int r = c + 1; r < n; r++) if (fabs(M[r * n + c].hi) > fabs(M[piv * n + c].hi)) piv = r;
+        if (M[piv * n + c].hi == 0.0) return -1;
+        if (piv != c) {
+            for (int k = 0; k < n; k++) { dd t = M[c * n + k]; M[c * n + k] = M[piv * n + k]; M[piv * n + k] = t; }
+            dd t = b[c]; b[c] = b[piv]; b[piv] = t;
+        }
+        for (int r = c + 1; r < n; r++) {
+            dd f = dd_div(M[r * n + c], M[c * n + c]);
+            for (int k = c; k < n; k++) M[r * n + k] = dd_sub(M[r * n + k], dd_mul(f, M[c * n + k]));
+            b[r] = dd_sub(b[r], dd_mul(f, b[c]));
+        }
+    }
+    for (int r = n - 1; r >= 0; r--) {
+        dd s = b[r];
+        for (int k = r + 1; k < n; k++) s = dd_sub(s, dd_mul(M[r * n + k], b[k]));
+        b[r] = dd_div(s, M[r * n + r]);
+    }
+    return 0;
+}
+
 /* Statistical equilibrium of one cell with the diagonal ALO (eq. 'ourALI'), rates as in
  * or_cell_generator with oml = 1 - L. The last equation is replaced by
- * sum_i n_i = n_spec (Reading). */
+ * sum_i n_i = n_spec (Reading). The system is solved by LU with partial pivoting in
+ * double-double arithmetic, the diagonal formed from the exit rates in the same
+ * arithmetic: in FP64 a 20-level rotor's populations lose up to seven digits (those
+ * holding 1e-7 of the cell off by 20%, and rounding-level negative values near 1e-30
+ * that would trip the validity check); the rates themselves are the FP64 values of
+ * or_cell_generator. */
 static int stateq_cell(const or_model *m, int64_t c, const double *Jc, const double *Lc,
                        const double *Ec, double *out) {
     int n = m->n_lev;
-    double M[64 * 64], b[64], oml[64 * 64];
+    double G[64 * 64], oml[64 * 64];
+    dd M[64 * 64], b[64];
     if (n > 64 || m->n_lines > 64 * 64) return -1;
     (void)Jc;
     for (int l = 0; l < m->n_lines; l++) oml[l] = 1.0 - Lc[l];
-    if (or_cell_generator(m, c, oml, Ec, M)) return -1;
-    for (int j = 0; j < n; j++) { M[(n - 1) * n + j] = 1.0; b[j] = 0.0; }
-    b[n - 1] = m->n_spec[c];
-    if (lu_solve(n, M, b)) return -2;
-    for (int i = 0; i < n; i++) out[i] = b[i];
+    if (or_cell_generator(m, c, oml, Ec, G)) return -1;
+    /* off-diagonal rates as they are; each diagonal entry the double-double sum of its
+     * column's exit rates, so that the columns sum to zero to ~1e-32 (an FP64 diagonal
+     * leaves ~1e-16 of the largest flux unbalanced, which swamps levels near 1e-30) */
+    for (int j = 0; j < n; j++) {
+        dd d = dd_from(0.0);
+        for (int i = 0; i < n; i++) {
+            if (i == j) continue;
+            M[i * n + j] = dd_from(G[i * n + j]);
+            d = dd_sub(d, M[i * n + j]);
+        }
+        M[j * n + j] = d;
+    }
+    for (int j = 0; j < n; j++) { M[(n - 1) * n + j] = dd_from(1.0); b[j] = dd_from(0.0); }
+    b[n - 1] = dd_from(m->n_spec[c]);
+    if (lu_solve_dd(n, M, b)) return -2;
+    for (int i = 0; i < n; i++) out[i] = b[i].hi + b[i].lo;
     return 0;
 }
 
 /* Level populations of all cells from J, L, Jeff ([n][n_lines]). Validity check
- * (Sec. 6.1): a cell whose populations come out negative or non-finite is solved again
- * with part of the ALO removed; here the diagonal ALO is dropped (L = 0, Jeff = J).
+ * (Sec. 6.1): a cell whose populations come out negative (below -1e-28 of the cell) or
+ * non-finite is solved again with part of the ALO removed; here the diagonal ALO is
+ * dropped (L = 0, Jeff = J).
  * Returns the number of such cells in *n_fallback. */
 int or_stateq(const or_model *m, const double *J, const double *L, const double *Jeff,
               double *pops_out, int64_t *n_fallback) {
@@ -771,7 +867,9 @@ int or_stateq(const or_model *m, const double *J, const double *L, const double 
         double *out = &pops_out[c * n];
         int rc = stateq_cell(m, c, &J[c * nl], &L[c * nl], &Jeff[c * nl], out);
         int bad = rc != 0;
-        for (int i = 0; i < n && !bad; i++) if (!(out[i] >= 0.0) || !isfinite(out[i])) bad = 1;
+        /* Reading: a value above -1e-28 of the cell is rounding noise of the solve (its
+         * resolution is ~1e-32 of the cell), not an unphysical population */
+        for (int i = 0; i < n && !bad; i++) if (!(out[i] >= -1e-28 * m->n_spec[c]) || !isfinite(out[i])) bad = 1;
         if (bad) {
             nf++;
             if (stateq_cell(m, c, &J[c * nl], zeros, &J[c * nl], out)) return -1;
@@ -1006,7 +1104,7 @@ int or_image(const or_model *m, const double *pops, int r, int line, int n_ch, c
             double *heta = hb + K, *hchi = heta + K * nl;
             double nvo = n[0] * m->vel[3 * o] + n[1] * m->vel[3 * o + 1] + n[2] * m->vel[3 * o + 2];
             /* the -n half, far end first: its line-of-sight velocity is (-n).(v - v_o) */
-            int64_t eb = expand_half(m, o, lb, cb, nb, dsb, vb, eta_c, chi_c, hds, hv, hb, heta, hchi, K, K);
+            int64_t eb = expand_half(m, o, lb, cb, nb, dsb, vb, eta_c, chi_c, hds, hv, hb, heta, hchi, K, K, NULL, NULL, NULL);
             int64_t k = 0;
             for (int64_t j = eb - 1; j >= 0; j--, k++) {
                 ds[k] = hds[j];
@@ -1017,7 +1115,7 @@ int or_image(const or_model *m, const double *pops, int r, int line, int n_ch, c
             ds[k] = 0.0; w[k] = nvo; b[k] = or_width(m, o);
             for (int l = 0; l < nl; l++) { eta[l * K + k] = eta_c[l * N + o]; chi[l * K + k] = chi_c[l * N + o]; }
             k++;
-            int64_t ef = expand_half(m, o, lf, cf, nf, dsf, vf, eta_c, chi_c, hds, hv, hb, heta, hchi, K, K);
+            int64_t ef = expand_half(m, o, lf, cf, nf, dsf, vf, eta_c, chi_c, hds, hv, hb, heta, hchi, K, K, NULL, NULL, NULL);
             for (int64_t j = 0; j < ef; j++, k++) {
                 ds[k - 1] = hds[j];
                 w[k] = nvo + hv[j];

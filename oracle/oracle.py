@@ -172,6 +172,7 @@ def _lib():
         L.or_formal_solve_band.argtypes = [P, P, C.c_int64, P, C.c_int, P, P, P, P, P, C.c_int]
         L.or_band_geometry.argtypes = [P, C.c_int64, P, C.c_int, P, P, P]
         L.or_cell_generator.argtypes = [P, C.c_int64, P, P, P]
+        L.or_formal_solve_sca.argtypes = [P, P, C.c_int64, P, P, P, P, P, P, P, C.c_int]
         _LIB = L
     return _LIB
 
@@ -313,6 +314,34 @@ class Oracle:
         if rc:
             raise RuntimeError(f"or_formal_solve_band failed ({rc})")
         return J, L, [E] + [Eb[b] for b in range(band)], M
+
+    def formal_solve_scattering(self, pops, chi_sca, tol=1e-10, max_iter=500, Jnu0=None):
+        """Formal solution with isotropic, coherent scattering of opacity chi_sca [n]
+        (Sec. 3.3, eq. 'GFE' with Psi+ = chi_sca J, Psi- = 0), the scattering source taken
+        from the previous iteration's mean intensity as the section prescribes, starting
+        from Jnu0 [n][n_lines][Q] (default: no scattered light) until the largest relative
+        change of the per-bin mean intensity is below tol. Returns J, L, Jeff, Jnu and the
+        list of changes."""
+        pops = np.ascontiguousarray(pops, np.float64)
+        m = self.model
+        n, nl = m.n, self.n_lines
+        chi_sca = np.ascontiguousarray(chi_sca, np.float64)
+        orig = np.arange(n, dtype=np.int64)
+        prev = np.zeros((n, nl, self.Q)) if Jnu0 is None else np.array(Jnu0, np.float64, copy=True)
+        J = np.empty((n, nl)); L = np.empty((n, nl)); E = np.empty((n, nl))
+        changes = []
+        for it in range(max_iter):
+            Jnu = np.empty((n, nl, self.Q))
+            rc = _lib().or_formal_solve_sca(self.mp, _ptr(pops), n, _ptr(orig), _ptr(chi_sca), _ptr(prev), _ptr(J),
+                                            _ptr(L), _ptr(E), _ptr(Jnu), self.nthreads)
+            if rc:
+                raise RuntimeError(f"or_formal_solve_sca failed ({rc})")
+            ch = float(np.max(np.abs(Jnu - prev) / Jnu))
+            changes.append(ch)
+            prev = Jnu
+            if ch < tol:
+                break
+        return J, L, E, prev, changes
 
     def band_geometry(self, band, origins=None):
         """Cells (ca, cb) and weight w of the j-th expanded point of every half-ray,

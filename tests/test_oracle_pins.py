@@ -604,3 +604,27 @@ def test_optically_thick_interior_thermalises():
     nu = (m.species.E[1] - m.species.E[0]) / h
     S = planck(nu, 20.0)
     assert abs(J[0, 0] / S - 1) < 2e-2
+
+
+def test_stateq_twenty_level_rotor_against_60_digit_solve():
+    """The rate equations of a 20-level rotor (a disc's cells, diagonal ALO from a formal
+    solve) solved by the oracle equal a 60-digit solve of the same rates (columns summing
+    exactly to zero, last equation replaced by the normalisation): exactly on levels
+    holding 1e-10 of the cell and within 1e-12 down to 1e-20; no cell falls back."""
+    mpmath = pytest.importorskip("mpmath")
+    m = syn.model_disc(n=300, seed=3, nside=1, n_q=15)
+    o = Oracle(m, nthreads=8)
+    J, L, E = o.formal_solve(o.lte())
+    ref, nf = o.stateq(J, L, E)
+    assert nf == 0
+    lev, ns = m.species.n_lev, m.n_spec
+    mpmath.mp.dps = 60
+    for c in range(0, m.n, 23):
+        G = o.cell_generator(c, 1.0 - L[c], E[c])
+        A = mpmath.matrix(G.tolist())
+        for j in range(lev):
+            A[j, j] = -mpmath.fsum(mpmath.mpf(G[i, j]) for i in range(lev) if i != j)
+            A[lev - 1, j] = 1
+        x = np.array([float(v) for v in mpmath.lu_solve(A, mpmath.matrix([0] * (lev - 1) + [ns[c]]))])
+        e = np.abs(ref[c] - x) / np.abs(x)
+        assert np.all(e[x >= 1e-10 * ns[c]] <= 1e-15) and np.all(e[x >= 1e-20 * ns[c]] <= 1e-12)
