@@ -81,11 +81,15 @@ typedef struct {
     double  tau_fp64;      /* MG_MIXED only: cells whose largest diagonal ALO weight L is
                               >= 1 - 1/tau_fp64 (optically thick lines) are solved again in
                               FP64 after the FP32 pass; 0 = off                            */
+    int32_t alo_band;      /* MG_FP64 only: bandwidth b of the approximate Lambda operator
+                              (Sec. 3.4, eq. 'ALO'): the entries |k - ko| <= b of the
+                              inverse's row along every ray pair; 0 = diagonal, at most 2   */
+    int32_t pad2;
 } mg_options;
 
 /* Fills *opt with defaults: MG_FP64, device 0, tol 1e-6, max_iter 300, ng_period 4,
  * dshift_frac 1/3, chi_min 1e-30, dtau_min 1e-30, T_cmb 2.725, line_cut 7.5,
- * max_steps 100000, profile 0, spectrum 0, tau_fp64 0 (off). */
+ * max_steps 100000, profile 0, spectrum 0, tau_fp64 0 (off), alo_band 0 (diagonal). */
 void mg_default_options(mg_options *opt);
 
 /* Creates a context on opt->device (NULL opt = defaults). *out receives the handle.
@@ -189,6 +193,27 @@ int mg_set_radiation(mg_ctx *ctx, const double *J, const double *L, const double
 /* Per-bin mean intensity (1/P) sum_pairs u, [n][n_lines][n_q]; needs opt.spectrum = 1. */
 int mg_get_spectrum(const mg_ctx *ctx, double *Jnu);
 
+/* Isotropic, coherent scattering (Sec. 2.1 eq. 'RTE', Sec. 3.3 eq. 'RTE2', 'GFE'), FP64
+ * contexts: chi_sca [n] (m^-1, >= 0) is a frequency-independent scattering opacity per
+ * point that scatters isotropically and keeps the comoving frequency. Then chi+ = chi_sca,
+ * chi- = 0, Psi- = 0 and Psi+ = chi_sca J_nu, and eq. 'GFE' for u is the second-order
+ * equation with opacity chi + chi_sca and source (eta + chi_sca J)/(chi + chi_sca). As
+ * Sec. 3.3 prescribes, its right-hand side is evaluated with the previous iteration's
+ * solution: every mg_formal_solve repeats the formal solution, with J per point and bin
+ * from the previous pass (read at a ray point's comoving offset from the line centre,
+ * in units of the point's width, from the bins of line l of the point's cells, linear
+ * between the Gauss-Hermite roots, interpolated between the cells like the line data),
+ * until the per-bin mean intensity changes by less than tol relative, or max_iter passes.
+ * The first pass of the first solve starts from no scattered light; later solves start
+ * from the last one's field. J, L, J_eff and the spectrum are those of the last pass
+ * (L and J_eff with the total opacity in their denominators). NULL chi_sca switches
+ * scattering off. Images leave the scattered light out. MG_ERR_STATE in mixed
+ * contexts or before the mesh, species and quadrature; MG_ERR_ARG for a negative or
+ * non-finite value. Setting the mesh or species switches scattering off. */
+int mg_set_scattering(mg_ctx *ctx, const double *chi_sca, double tol, int32_t max_iter);
+/* Passes and final relative change of the scattering iteration of the last formal solve. */
+int mg_scattering_status(const mg_ctx *ctx, int32_t *iterations, double *last_change);
+
 /* Image of the model along ray direction `ray` (Sec. 3.5, 'Imaging the model'): every
  * point o contributes one image point, its projection on the plane orthogonal to
  * n = dirs[ray], carrying the intensity that leaves the model along n on the ray pair
@@ -218,10 +243,18 @@ int mg_image(mg_ctx *ctx, int32_t ray, int32_t line, int32_t n_ch, const double 
 int mg_image_dev(mg_ctx *ctx, int32_t ray, int32_t line, int32_t n_ch, const double *u_ch, double *d_I,
                  double *d_xy);
 
-/* Statistical equilibrium with the diagonal ALO (eq. 'ourALI') for every cell, the
- * validity check (negative or non-finite populations -> the cell is solved again
- * without the ALO, Sec. 6.1) and the convergence measure: *max_rel_change = max over
- * cells and levels with n_i >= 1e-10 n of |n_new - n_old| / n_new (NULL allowed).
+/* Statistical equilibrium with the ALO (eq. 'ourALI') for every cell, the validity check
+ * (Sec. 6.1) and the convergence measure: *max_rel_change = max over cells and levels
+ * with n_i >= 1e-10 n of |n_new - n_old| / n_new (NULL allowed).
+ * Diagonal ALO (bandwidth in use 0): per cell; a cell with negative or non-finite
+ * populations is solved again without the ALO.
+ * Band ALO (opt.alo_band > 0, bandwidth in use b > 0): the rate equations of all cells
+ * form one linear system, since the upper population at the band points along every ray
+ * pair (interpolated between their cells) enters the equations of the origin with the
+ * coefficients of the last formal solve; it is solved by preconditioned GMRES. If a
+ * population comes out negative or non-finite, or GMRES misses its tolerance, it is
+ * solved again with bandwidth b - 1, down to the diagonal ALO; the bandwidth in use keeps
+ * the reduction until populations are set or initialised again (mg_band_status).
  * Returns MG_WARN_NEG_POP_FALLBACK when some cell fell back, else MG_WARN_NEG_OPACITY
  * when the last formal solve met a negative line opacity integral. Synchronises. */
 int mg_update_populations(mg_ctx *ctx, double *max_rel_change);
@@ -238,6 +271,8 @@ int mg_update_populations(mg_ctx *ctx, double *max_rel_change);
  * MG_WARN_NEG_OPACITY after a formal solve that met a negative opacity integral), without
  * touching the context's populations. *max_rel_change and *n_fallback (either may be
  * NULL) receive the convergence measure and the number of fallback cells.
+ * It uses the diagonal ALO: MG_ERR_STATE while a band ALO is in use (opt.alo_band > 0),
+ * whose coupled solve needs buffers of its own.
  * Scratch: a static 512 KiB device array per GPU that loads the library (held until
  * exit); at most 2,097,152 cells per call (MG_ERR_CAPACITY beyond). Everything that may
  * allocate -- loading the kernels and the array on the device, looking up the array's
@@ -248,6 +283,16 @@ int mg_update_populations(mg_ctx *ctx, double *max_rel_change);
  * (other streams, threads or contexts) race on the shared scratch. */
 int mg_update_populations_noalloc(mg_ctx *ctx, const double *d_pops_old, double *d_pops_new,
                                   double *max_rel_change, int64_t *n_fallback);
+
+/* Band ALO state: *band_in_use = the bandwidth the next update starts from, *iters = GMRES
+ * iterations since the populations were last set or initialised (either may be NULL). */
+int mg_band_status(const mg_ctx *ctx, int32_t *band_in_use, int64_t *gmres_iters);
+/* Band terms of the last FP64 formal solve with bandwidth B = *band (> 0): Jeffb
+ * [B][n][n_lines] (J_eff of bandwidths 1..B, eq. 'ourJeff' with the band of the ALO) and
+ * M [n][n_lines][R][B]: the coefficient with which A_ul times the upper population at the
+ * j-th point from the origin of half-ray r enters the rate equation of the origin
+ * (either buffer may be NULL). MG_ERR_STATE when the last formal solve had no band. */
+int mg_get_band_terms(const mg_ctx *ctx, int32_t *band, double *Jeffb, double *M);
 
 /* Counts behind the warnings of the last mg_update_populations: cells that fell back
  * without the ALO, and (point, line) pairs with a negative opacity integral in the last
@@ -261,7 +306,7 @@ typedef struct {
     int32_t iterations;      /* regular iterations done                            */
     int32_t ng_steps;        /* Ng extrapolations accepted                         */
     int32_t converged;       /* 1 when the last change < tol                       */
-    int32_t pad;
+    int32_t alo_band;        /* bandwidth of the ALO in use at the end             */
     double  last_change;     /* max relative change of the last iteration          */
     int64_t n_fallback;      /* cells that fell back, summed over iterations       */
     double  seconds;         /* wall time of the loop                              */
@@ -269,7 +314,9 @@ typedef struct {
 
 /* Accelerated Lambda iteration from the current populations: formal solve ->
  * statistical equilibrium -> convergence, with an Ng step every opt.ng_period
- * iterations (Sec. 3.4, 6.1), until the change < opt.tol or opt.max_iter.
+ * iterations (Sec. 3.4, 6.1), until the change < opt.tol or opt.max_iter. With a band
+ * ALO, the bandwidth in use also drops by one when the change has grown in three
+ * consecutive iterations (a diverging iteration).
  * Returns MG_ERR_NOT_CONVERGED when the cap is reached (populations are kept). */
 int mg_iterate(mg_ctx *ctx, mg_ali_report *rep);
 
@@ -384,6 +431,16 @@ int mg_reset_kernel_times(mg_ctx *ctx);
 /* Algorithmic work of one formal solve: ray-pair solves (points x pairs x bins) and
  * cell-frequency updates (sum over solves of the expanded pair length). */
 int mg_work_counts(const mg_ctx *ctx, int64_t *solves, int64_t *cell_freq_updates);
+/* Point-bin updates the mixed-precision warp kernel executed (points swept, far-wing
+ * points it skipped left out; each half-ray sweeps the origin once) since the last
+ * mg_reset_kernel_times, counted only with opt.profile = 1. */
+int mg_executed_work(const mg_ctx *ctx, int64_t *updates);
+
+/* Measured throughput of the FP32 pipes that bound the mixed-precision formal solve, on
+ * `device`: rates[0] scalar FFMA flops/s (2 per FMA), rates[1] packed FFMA2 flops/s,
+ * rates[2] ex2.approx results/s, rates[3] rcp.approx results/s (independent chains over a
+ * grid of 4 CTAs per SM, best of three timed launches). Allocates 16 bytes; synchronises. */
+int mg_measure_pipe_rates(int32_t device, double *rates);
 
 #ifdef __cplusplus
 }

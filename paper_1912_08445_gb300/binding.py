@@ -27,7 +27,8 @@ class mg_options(C.Structure):
                 ("max_iter", C.c_int32), ("ng_period", C.c_int32), ("dshift_frac", C.c_double),
                 ("chi_min", C.c_double), ("dtau_min", C.c_double), ("T_cmb", C.c_double),
                 ("line_cut", C.c_double), ("max_steps", C.c_int64), ("profile", C.c_int32),
-                ("spectrum", C.c_int32), ("pad", C.c_int32), ("tau_fp64", C.c_double)]
+                ("spectrum", C.c_int32), ("pad", C.c_int32), ("tau_fp64", C.c_double),
+                ("alo_band", C.c_int32), ("pad2", C.c_int32)]
 
 
 class mg_train_opts(C.Structure):
@@ -47,7 +48,7 @@ class mg_ray_stats(C.Structure):
 
 class mg_ali_report(C.Structure):
     _fields_ = [("iterations", C.c_int32), ("ng_steps", C.c_int32), ("converged", C.c_int32),
-                ("pad", C.c_int32), ("last_change", C.c_double), ("n_fallback", C.c_int64),
+                ("alo_band", C.c_int32), ("last_change", C.c_double), ("n_fallback", C.c_int64),
                 ("seconds", C.c_double)]
 
 
@@ -92,8 +93,14 @@ _SIGS = {
     "mg_kernel_times": (C.c_int, [_P, C.c_int32, _P, _P, _P, _P]),
     "mg_reset_kernel_times": (C.c_int, [_P]),
     "mg_work_counts": (C.c_int, [_P, _P, _P]),
+    "mg_executed_work": (C.c_int, [_P, _P]),
+    "mg_measure_pipe_rates": (C.c_int, [C.c_int32, _P]),
     "mg_autotune": (C.c_int, [_P, C.c_int32, _P, _P, _P]),
     "mg_status_counts": (C.c_int, [_P, _P, _P]),
+    "mg_band_status": (C.c_int, [_P, _P, _P]),
+    "mg_set_scattering": (C.c_int, [_P, _P, C.c_double, C.c_int32]),
+    "mg_scattering_status": (C.c_int, [_P, _P, _P]),
+    "mg_get_band_terms": (C.c_int, [_P, _P, _P, _P]),
     "mg_promoted_cells": (C.c_int, [_P, _P]),
     "mg_mlp_create": (C.c_int, [_P, C.c_int32, C.c_uint64, C.c_int32]),
     "mg_mlp_destroy": (C.c_int, [_P]),
@@ -171,6 +178,16 @@ def default_options(**kw):
             raise KeyError(k)
         setattr(o, k, v)
     return o
+
+
+def measure_pipe_rates(device=0):
+    """Measured FP32 pipe throughput on a device: dict with ffma, ffma2 (flops/s), ex2,
+    rcp (results/s)."""
+    r = np.zeros(4)
+    rc = load().mg_measure_pipe_rates(int(device), _ptr(r))
+    if rc != MG_OK:
+        raise MagritteError(rc, "mg_measure_pipe_rates failed")
+    return dict(ffma=float(r[0]), ffma2=float(r[1]), ex2=float(r[2]), rcp=float(r[3]))
 
 
 class Context:
@@ -358,6 +375,33 @@ class Context:
         self._chk(self.lib.mg_status_counts(self.h, C.byref(f), C.byref(n)), "mg_status_counts")
         return f.value, n.value
 
+    def set_scattering(self, chi_sca, tol=1e-8, max_iter=100):
+        """Isotropic coherent scattering of opacity chi_sca [n] (None switches it off)."""
+        x = None if chi_sca is None else _c(chi_sca, np.float64)
+        self._chk(self.lib.mg_set_scattering(self.h, _ptr(x), float(tol), int(max_iter)), "mg_set_scattering")
+
+    def scattering_status(self):
+        """(passes, final relative change) of the last formal solve's scattering iteration."""
+        it = C.c_int32(0); ch = C.c_double(0)
+        self._chk(self.lib.mg_scattering_status(self.h, C.byref(it), C.byref(ch)), "mg_scattering_status")
+        return it.value, ch.value
+
+    def band_status(self):
+        """(bandwidth in use, GMRES iterations since populations were set)."""
+        b = C.c_int32(0); it = C.c_int64(0)
+        self._chk(self.lib.mg_band_status(self.h, C.byref(b), C.byref(it)), "mg_band_status")
+        return b.value, it.value
+
+    def get_band_terms(self):
+        """J_eff of bandwidths 1..B [B][n][n_lines] and coupling terms M [n][n_lines][R][B]
+        of the last formal solve."""
+        B = C.c_int32(0)
+        self._chk(self.lib.mg_get_band_terms(self.h, C.byref(B), None, None), "mg_get_band_terms")
+        R = self.get_directions()[0].shape[0]
+        Jb = np.empty((B.value, self.n, self.n_lines)); M = np.empty((self.n, self.n_lines, R, B.value))
+        self._chk(self.lib.mg_get_band_terms(self.h, C.byref(B), _ptr(Jb), _ptr(M)), "mg_get_band_terms")
+        return Jb, M
+
     def features(self):
         out = np.empty((self.n, 4), np.float32)
         self._chk(self.lib.mg_features(self.h, _ptr(out)), "mg_features")
@@ -384,6 +428,12 @@ class Context:
         s = C.c_int64(0); u = C.c_int64(0)
         self._chk(self.lib.mg_work_counts(self.h, C.byref(s), C.byref(u)), "mg_work_counts")
         return s.value, u.value
+
+    def executed_work(self):
+        """Point-bin updates the warp kernel executed since reset_kernel_times (profiling)."""
+        u = C.c_int64(0)
+        self._chk(self.lib.mg_executed_work(self.h, C.byref(u)), "mg_executed_work")
+        return u.value
 
     # ---- convenience: load a synthetic model
     def load_model(self, m, nside=None, dirs=None, n_q=None):

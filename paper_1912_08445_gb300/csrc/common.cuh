@@ -132,7 +132,9 @@ struct mg_ctx {
 
     // ---- scalars
     unsigned long long *d_scal = nullptr;   // [0] max change bits, [1] fallbacks, [2] non-finite,
-                                            // [3] Ng flags, [4] negative line opacities
+                                            // [3] Ng flags, [4] negative line opacities, [5] band
+                                            // solve: singular blocks, [6] image negative opacities,
+                                            // [7] executed point-bin updates (profiling)
     int64_t last_fallback = 0, last_neg_opacity = 0;
     unsigned long long *h_scal = nullptr;   // pinned
     int32_t *d_err = nullptr;               // kernel error word
@@ -150,6 +152,28 @@ struct mg_ctx {
 
     // ---- launch variant of the mixed formal solve (-1: default for the model)
     int mixed_variant = -1;
+
+    // ---- band-diagonal ALO (band.cu): bandwidth in use, that of the last formal solve,
+    //      its J_eff of bandwidths 1..B [B][n][L] and coupling terms [n][L][R][B], the
+    //      band points' cells and weights [n][R][opt.alo_band], and the solver's buffers
+    int band_cur = 0, band_solved = 0;
+    bool band_geo_ready = false;
+    int64_t band_cap_n = 0;
+    int band_cap_lev = 0, band_cap_L = 0, band_cap_R = 0;
+    int64_t band_gmres_iters = 0;
+    double *d_Jeffb = nullptr, *d_Mb = nullptr;
+    int2 *d_bcells = nullptr;
+    double *d_bw = nullptr, *d_blu = nullptr, *d_bs = nullptr, *d_bz = nullptr, *d_bx = nullptr, *d_bw2 = nullptr;
+    double *d_bV = nullptr, *d_bpart = nullptr, *d_bh = nullptr;
+    int32_t *d_bpiv = nullptr;
+
+    // ---- isotropic coherent scattering (FP64): opacity [n], the previous and the new mean
+    //      intensity per bin [n][L][Q], the iteration's tolerance, cap and last outcome
+    bool sca_on = false;
+    double *d_chisca = nullptr, *d_Jsca = nullptr, *d_Jsca_new = nullptr;
+    unsigned long long *d_scaw = nullptr;
+    double sca_tol = 1e-8, sca_change = 0.0;
+    int32_t sca_max_iter = 100, sca_iters = 0;
 
     // ---- allocation-free update: set-up done at mg_set_species (stateq_noalloc.cu)
     bool na_ready = false;
@@ -203,6 +227,8 @@ int mg_launch_line_data64(mg_ctx *ctx, float *linef, unsigned long long *neg);
 int mg_launch_image(mg_ctx *ctx, int ray, int line, int n_ch, const double *d_u, const mg::Overlap *d_ov,
                     int n_ov, double *d_I, double *d_xy);
 int mg_launch_feautrier(mg_ctx *ctx);
+int mg_launch_max_rel_change(mg_ctx *ctx, int64_t m, const double *a_new, const double *a_old,
+                             unsigned long long *word);
 int mg_launch_feautrier_fp64_list(mg_ctx *ctx, const int32_t *olist, const int32_t *ocount);
 int mg_autotune_mixed(mg_ctx *ctx, int reps, int *best, double *best_ms, int *n_tried);
 int mg_launch_lte(mg_ctx *ctx);
@@ -213,6 +239,11 @@ int mg_launch_push_history(mg_ctx *ctx);
 int mg_launch_stateq_into(mg_ctx *ctx, const double *pops_old, double *pops_new, const int32_t *active);
 int mg_ensure_solve_state(mg_ctx *ctx);   // state buffers, overlaps and collision rates ready
 void mg_noalloc_prepare(mg_ctx *ctx);     // set-up of mg_update_populations_noalloc
+int mg_band_alloc(mg_ctx *ctx);
+int mg_band_geometry(mg_ctx *ctx);
+int mg_band_update(mg_ctx *ctx, double *max_change, int64_t *n_fallback, int *band_used);
+void mg_band_free(mg_ctx *ctx);
+void mg_band_restart(mg_ctx *ctx);        // populations set: bandwidth back to opt.alo_band
 // batch helpers (solve_mixed.cu)
 size_t mg_mixargs_size();
 int mg_fill_mixargs(mg_ctx *ctx, void *out);

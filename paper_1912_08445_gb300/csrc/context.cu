@@ -56,6 +56,7 @@ extern "C" void mg_default_options(mg_options *o) {
     o->profile = 0;
     o->spectrum = 0;
     o->tau_fp64 = 0.0;
+    o->alo_band = 0;
 }
 
 extern "C" int mg_create(mg_ctx **out, const mg_options *opt) {
@@ -68,7 +69,8 @@ extern "C" int mg_create(mg_ctx **out, const mg_options *opt) {
     if ((o.precision != MG_FP64 && o.precision != MG_MIXED) || !(o.tol > 0) || o.max_iter < 1 ||
         o.ng_period < 0 || !(o.dshift_frac > 0) || !(o.chi_min > 0) || !(o.dtau_min > 0) ||
         !(o.T_cmb > 0) || !(o.line_cut > 0) || o.max_steps < 1 || !(o.tau_fp64 >= 0) ||
-        (o.tau_fp64 > 0 && o.tau_fp64 <= 1)) {
+        (o.tau_fp64 > 0 && o.tau_fp64 <= 1) || o.alo_band < 0 || o.alo_band > 2 ||
+        (o.alo_band > 0 && o.precision != MG_FP64)) {
         delete ctx;
         return MG_ERR_ARG;
     }
@@ -85,6 +87,7 @@ extern "C" int mg_create(mg_ctx **out, const mg_options *opt) {
         return MG_ERR_CUDA;
     }
     ctx->stream = ctx->own_stream;
+    ctx->band_cur = o.alo_band;
     cudaMemset(ctx->d_scal, 0, 8 * sizeof(unsigned long long));
     *out = ctx;
     return MG_OK;
@@ -94,6 +97,7 @@ static void free_rays(mg_ctx *ctx) {
     mg_free(ctx->d_ray_off); mg_free(ctx->d_cells); mg_free(ctx->d_xcum); mg_free(ctx->d_ds);
     mg_free(ctx->d_vpar); mg_free(ctx->d_dsf); mg_free(ctx->d_vparf);
     ctx->traced = false;
+    ctx->band_geo_ready = false;
 }
 
 static void drop_state(mg_ctx *ctx) {
@@ -104,6 +108,11 @@ static void drop_state(mg_ctx *ctx) {
     // image buffers are sized by the point and line counts
     mg_free(ctx->d_img); mg_free(ctx->d_imgxy); mg_free(ctx->d_imgov); mg_free(ctx->d_imglf);
     ctx->img_cap = 0;
+    mg_band_free(ctx);
+    ctx->band_solved = 0;
+    // scattering buffers are sized by the point, line and bin counts: set them again
+    mg_free(ctx->d_chisca); mg_free(ctx->d_Jsca); mg_free(ctx->d_Jsca_new); mg_free(ctx->d_scaw);
+    ctx->sca_on = false;
 }
 
 extern "C" int mg_destroy(mg_ctx *ctx) {
@@ -123,6 +132,8 @@ extern "C" int mg_destroy(mg_ctx *ctx) {
     mg_free(ctx->d_Jeff); mg_free(ctx->d_Lc); mg_free(ctx->d_Jnu); mg_free(ctx->d_scal);
     mg_free(ctx->d_err);
     mg_free(ctx->d_uch); mg_free(ctx->d_img); mg_free(ctx->d_imgxy); mg_free(ctx->d_imgov); mg_free(ctx->d_imglf);
+    mg_band_free(ctx);
+    mg_free(ctx->d_chisca); mg_free(ctx->d_Jsca); mg_free(ctx->d_Jsca_new); mg_free(ctx->d_scaw);
     if (ctx->h_scal) cudaFreeHost(ctx->h_scal);
     if (ctx->ev0) cudaEventDestroy(ctx->ev0);
     if (ctx->ev1) cudaEventDestroy(ctx->ev1);
@@ -572,6 +583,12 @@ extern "C" int mg_get_ray(const mg_ctx *cctx, int64_t point, int32_t ray, int32_
 }
 
 // ------------------------------------------------------------------ populations
+// New populations start a new iteration: the bandwidth in use returns to the option's.
+void mg_band_restart(mg_ctx *ctx) {
+    ctx->band_cur = ctx->opt.alo_band;
+    ctx->band_gmres_iters = 0;
+}
+
 static int ensure_state(mg_ctx *ctx) {
     int64_t n = ctx->n;
     int L = ctx->n_lines, lev = ctx->n_lev;
@@ -612,6 +629,7 @@ extern "C" int mg_init_populations(mg_ctx *ctx, int32_t mode) {
     if (mode != MG_INIT_LTE) return mg_fail(ctx, MG_ERR_ARG, "mg_init_populations: unknown mode");
     if ((rc = ensure_state(ctx))) return rc;
     if ((rc = mg_launch_lte(ctx))) return rc;
+    mg_band_restart(ctx);
     ctx->have_pops = true;
     ctx->have_rad = false;
     return MG_OK;
@@ -624,6 +642,7 @@ extern "C" int mg_set_populations(mg_ctx *ctx, const double *pops) {
     cudaSetDevice(ctx->device);
     if ((rc = ensure_state(ctx))) return rc;
     MG_CUDA(cudaMemcpyAsync(ctx->d_pops, pops, 8 * ctx->n * ctx->n_lev, cudaMemcpyHostToDevice, ctx->stream));
+    mg_band_restart(ctx);
     ctx->have_pops = true;
     ctx->have_rad = false;
     return MG_OK;
@@ -636,6 +655,7 @@ extern "C" int mg_set_populations_dev(mg_ctx *ctx, const double *d_pops) {
     cudaSetDevice(ctx->device);
     if ((rc = ensure_state(ctx))) return rc;
     MG_CUDA(cudaMemcpyAsync(ctx->d_pops, d_pops, 8 * ctx->n * ctx->n_lev, cudaMemcpyDeviceToDevice, ctx->stream));
+    mg_band_restart(ctx);
     ctx->have_pops = true;
     ctx->have_rad = false;
     return MG_OK;
@@ -677,9 +697,74 @@ extern "C" int mg_formal_solve(mg_ctx *ctx) {
     if (ctx->h_ovl_off.size() != (size_t)ctx->n_lines + 1)
         if ((rc = upload_overlaps(ctx))) return rc;
     MG_CUDA(cudaMemsetAsync(ctx->d_scal + 4, 0, sizeof(unsigned long long), ctx->stream));
+    if (ctx->band_cur > 0 && (rc = mg_band_alloc(ctx))) return rc;
     if ((rc = mg_launch_line_data(ctx))) return rc;
-    if ((rc = mg_launch_feautrier(ctx))) return rc;
+    if (ctx->sca_on) {
+        // scattering (Sec. 3.3): the right-hand side from the previous iteration's mean
+        // intensity, until the per-bin mean intensity changes by less than sca_tol
+        const int64_t m = ctx->n * ctx->n_lines * ctx->Q;
+        double ch = INFINITY;
+        int it = 0;
+        while (it < ctx->sca_max_iter) {
+            if ((rc = mg_launch_feautrier(ctx))) return rc;
+            if ((rc = mg_launch_max_rel_change(ctx, m, ctx->d_Jsca_new, ctx->d_Jsca, ctx->d_scaw))) return rc;
+            std::swap(ctx->d_Jsca, ctx->d_Jsca_new);
+            it++;
+            unsigned long long bits = 0;
+            MG_CUDA(cudaMemcpyAsync(&bits, ctx->d_scaw, 8, cudaMemcpyDeviceToHost, ctx->stream));
+            MG_CUDA(cudaStreamSynchronize(ctx->stream));
+            std::memcpy(&ch, &bits, 8);
+            if (ch < ctx->sca_tol) break;
+        }
+        ctx->sca_iters = it;
+        ctx->sca_change = ch;
+        if (ctx->opt.spectrum && ctx->d_Jnu)
+            MG_CUDA(cudaMemcpyAsync(ctx->d_Jnu, ctx->d_Jsca, 8 * (size_t)m, cudaMemcpyDeviceToDevice, ctx->stream));
+    } else if ((rc = mg_launch_feautrier(ctx))) {
+        return rc;
+    }
+    ctx->band_solved = ctx->opt.precision == MG_FP64 ? ctx->band_cur : 0;
     ctx->have_rad = true;
+    return MG_OK;
+}
+
+extern "C" int mg_set_scattering(mg_ctx *ctx, const double *chi_sca, double tol, int32_t max_iter) {
+    if (!ctx) return MG_ERR_ARG;
+    cudaSetDevice(ctx->device);
+    if (!chi_sca) {
+        ctx->sca_on = false;
+        ctx->have_rad = false;
+        return MG_OK;
+    }
+    if (ctx->opt.precision != MG_FP64)
+        return mg_fail(ctx, MG_ERR_STATE, "mg_set_scattering: scattering is built for FP64 contexts");
+    if (!ctx->have_mesh || !ctx->have_species || !ctx->have_quad)
+        return mg_fail(ctx, MG_ERR_STATE, "mg_set_scattering: set the mesh, species and quadrature first");
+    if (!(tol > 0) || max_iter < 1) return mg_fail(ctx, MG_ERR_ARG, "mg_set_scattering: tol > 0 and max_iter >= 1");
+    for (int64_t i = 0; i < ctx->n; i++)
+        if (!(chi_sca[i] >= 0.0) || !std::isfinite(chi_sca[i]))
+            return mg_fail(ctx, MG_ERR_ARG, "mg_set_scattering: chi_sca must be finite and >= 0");
+    const size_t m = (size_t)ctx->n * ctx->n_lines * ctx->Q;
+    int rc;
+    if ((rc = mg_alloc(ctx, &ctx->d_chisca, ctx->n)) || (rc = mg_alloc(ctx, &ctx->d_Jsca, m)) ||
+        (rc = mg_alloc(ctx, &ctx->d_Jsca_new, m)) || (rc = mg_alloc(ctx, &ctx->d_scaw, 1)))
+        return rc;
+    MG_CUDA(cudaMemcpyAsync(ctx->d_chisca, chi_sca, 8 * (size_t)ctx->n, cudaMemcpyHostToDevice, ctx->stream));
+    MG_CUDA(cudaMemsetAsync(ctx->d_Jsca, 0, 8 * m, ctx->stream));   // no scattered light to start from
+    MG_CUDA(cudaStreamSynchronize(ctx->stream));
+    ctx->sca_tol = tol;
+    ctx->sca_max_iter = max_iter;
+    ctx->sca_iters = 0;
+    ctx->sca_change = 0.0;
+    ctx->sca_on = true;
+    ctx->have_rad = false;
+    return MG_OK;
+}
+
+extern "C" int mg_scattering_status(const mg_ctx *ctx, int32_t *iterations, double *last_change) {
+    if (!ctx) return MG_ERR_ARG;
+    if (iterations) *iterations = ctx->sca_iters;
+    if (last_change) *last_change = ctx->sca_change;
     return MG_OK;
 }
 
@@ -716,6 +801,7 @@ extern "C" int mg_set_radiation(mg_ctx *ctx, const double *J, const double *L, c
     MG_CUDA(cudaMemcpyAsync(ctx->d_Lc, oml.data(), 8 * m, cudaMemcpyHostToDevice, ctx->stream));
     MG_CUDA(cudaMemsetAsync(ctx->d_scal + 4, 0, sizeof(unsigned long long), ctx->stream));
     MG_CUDA(cudaStreamSynchronize(ctx->stream));
+    ctx->band_solved = 0;   // no band terms: the next update uses the diagonal ALO
     ctx->have_rad = true;
     return MG_OK;
 }
@@ -824,6 +910,23 @@ extern "C" int mg_update_populations(mg_ctx *ctx, double *max_rel_change) {
         if ((rc = mg_launch_collision_rates(ctx))) return rc;
         ctx->coll_ready = true;
     }
+    if (ctx->band_cur > 0 && ctx->band_solved > 0) {
+        // band ALO: one coupled system over all cells, with bandwidth reduction
+        if ((rc = mg_band_geometry(ctx))) return rc;
+        double ch = 0.0;
+        int64_t nf = 0;
+        int bu = 0;
+        if ((rc = mg_band_update(ctx, &ch, &nf, &bu)) < 0) return rc;
+        MG_CUDA(cudaMemcpyAsync(ctx->h_scal + 4, ctx->d_scal + 4, sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                                ctx->stream));
+        MG_CUDA(cudaStreamSynchronize(ctx->stream));
+        if (max_rel_change) *max_rel_change = ch;
+        ctx->have_rad = false;
+        ctx->last_fallback = nf;
+        ctx->last_neg_opacity = (int64_t)ctx->h_scal[4];
+        if (nf) return MG_WARN_NEG_POP_FALLBACK;
+        return ctx->h_scal[4] ? MG_WARN_NEG_OPACITY : MG_OK;
+    }
     if ((rc = mg_launch_stateq(ctx))) return rc;
     MG_CUDA(cudaMemcpyAsync(ctx->h_scal, ctx->d_scal, 5 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, ctx->stream));
     MG_CUDA(cudaStreamSynchronize(ctx->stream));
@@ -850,6 +953,28 @@ extern "C" int mg_promoted_cells(const mg_ctx *cctx, int64_t *count) {
     return MG_OK;
 }
 
+extern "C" int mg_band_status(const mg_ctx *ctx, int32_t *band_in_use, int64_t *gmres_iters) {
+    if (!ctx) return MG_ERR_ARG;
+    if (band_in_use) *band_in_use = ctx->band_cur;
+    if (gmres_iters) *gmres_iters = ctx->band_gmres_iters;
+    return MG_OK;
+}
+
+extern "C" int mg_get_band_terms(const mg_ctx *cctx, int32_t *band, double *Jeffb, double *M) {
+    mg_ctx *ctx = const_cast<mg_ctx *>(cctx);
+    if (!ctx || !band) return MG_ERR_ARG;
+    if (!ctx->have_rad || ctx->band_solved < 1)
+        return mg_fail(ctx, MG_ERR_STATE, "mg_get_band_terms: the last formal solve had no band terms");
+    cudaSetDevice(ctx->device);
+    const int B = ctx->band_solved;
+    *band = B;
+    const size_t nl = (size_t)ctx->n * ctx->n_lines;
+    if (Jeffb) MG_CUDA(cudaMemcpyAsync(Jeffb, ctx->d_Jeffb, 8 * nl * B, cudaMemcpyDeviceToHost, ctx->stream));
+    if (M) MG_CUDA(cudaMemcpyAsync(M, ctx->d_Mb, 8 * nl * ctx->R * B, cudaMemcpyDeviceToHost, ctx->stream));
+    MG_CUDA(cudaStreamSynchronize(ctx->stream));
+    return MG_OK;
+}
+
 extern "C" int mg_status_counts(const mg_ctx *ctx, int64_t *fallback_cells, int64_t *negative_opacity) {
     if (!ctx) return MG_ERR_ARG;
     if (fallback_cells) *fallback_cells = ctx->last_fallback;
@@ -865,7 +990,8 @@ extern "C" int mg_iterate(mg_ctx *ctx, mg_ali_report *rep) {
     cudaSetDevice(ctx->device);
     auto t0 = std::chrono::steady_clock::now();
     mg_ali_report r{};
-    int nh = 0;
+    int nh = 0, grow = 0;
+    double last = 0.0;
     for (int it = 0; it < ctx->opt.max_iter; it++) {
         if ((rc = mg_formal_solve(ctx)) < 0) return rc;
         double ch = 0;
@@ -874,6 +1000,14 @@ extern "C" int mg_iterate(mg_ctx *ctx, mg_ali_report *rep) {
         r.n_fallback += ctx->last_fallback;
         r.iterations = it + 1;
         r.last_change = ch;
+        // band ALO: a change that has grown three iterations in a row (a diverging
+        // iteration) reduces the bandwidth in use by one
+        grow = (it > 0 && ch > last) ? grow + 1 : 0;
+        last = ch;
+        if (grow >= 3 && ctx->band_cur > 0) {
+            ctx->band_cur--;
+            grow = 0;
+        }
         if (ch < ctx->opt.tol) { r.converged = 1; break; }
         if (ctx->opt.ng_period > 0) {
             if ((rc = mg_launch_push_history(ctx))) return rc;
@@ -888,6 +1022,7 @@ extern "C" int mg_iterate(mg_ctx *ctx, mg_ali_report *rep) {
     }
     MG_CUDA(cudaStreamSynchronize(ctx->stream));
     r.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    r.alo_band = ctx->band_cur;
     if (rep) *rep = r;
     return r.converged ? MG_OK : mg_fail(ctx, MG_ERR_NOT_CONVERGED, "ALI did not reach the tolerance");
 }
@@ -949,6 +1084,20 @@ extern "C" int mg_kernel_times(const mg_ctx *ctx, int32_t cap, const char **name
 extern "C" int mg_reset_kernel_times(mg_ctx *ctx) {
     if (!ctx) return MG_ERR_ARG;
     for (auto &t : ctx->timers) { t.ms = 0.0; t.launches = 0; }
+    cudaSetDevice(ctx->device);
+    MG_CUDA(cudaMemsetAsync(ctx->d_scal + 7, 0, sizeof(unsigned long long), ctx->stream));
+    MG_CUDA(cudaStreamSynchronize(ctx->stream));
+    return MG_OK;
+}
+
+extern "C" int mg_executed_work(const mg_ctx *cctx, int64_t *updates) {
+    mg_ctx *ctx = const_cast<mg_ctx *>(cctx);
+    if (!ctx || !updates) return MG_ERR_ARG;
+    cudaSetDevice(ctx->device);
+    unsigned long long v = 0;
+    MG_CUDA(cudaMemcpyAsync(&v, ctx->d_scal + 7, sizeof(v), cudaMemcpyDeviceToHost, ctx->stream));
+    MG_CUDA(cudaStreamSynchronize(ctx->stream));
+    *updates = (int64_t)v;
     return MG_OK;
 }
 

@@ -766,6 +766,7 @@ extern "C" int mg_init_populations_mlp(mg_ctx *ctx, mg_mlp *p) {
     }
     cudaFree(dF);
     cudaFree(dL);
+    mg_band_restart(ctx);
     ctx->have_pops = true;
     ctx->have_rad = false;
     return rc;

@@ -48,6 +48,10 @@ struct SolveArgs {
     const int32_t *olist;    // optional list of origins (FP64 promotion), count in *ocount
     const int32_t *ocount;
     int32_t groups;          // FP64 kernel: warps that solve different ray pairs of a point (1: the whole CTA per pair)
+    double *Jeffb;           // band ALO: [B][n][L] J_eff of bandwidths 1..B
+    double *Mb;              // band ALO: [n][L][R][B] coupling coefficients of the band points
+    const double *chi_sca;   // scattering: [n] opacity, m^-1
+    const double *Jsca;      // scattering: [n][L][Q] previous mean intensity per bin
 };
 
 __device__ __forceinline__ double planck_d(double nu, double T) {
@@ -90,17 +94,41 @@ __device__ void stage_half64(const SolveArgs &a, int64_t o, int r, int base, int
     }
 }
 
-// Opacity, emissivity and line l's own share at pair point k for bin (l, q).
+// Opacity, emissivity and line l's own share at pair point k for bin (l, q), and line l's
+// own profile phi_l there.
 struct Pt64 {
-    double chi, eta, chil, etal;
+    double chi, eta, chil, etal, phil;
 };
 
+// Mean intensity of cell c in the bins of line l at offset r (in widths) from the line
+// centre: linear interpolation between the Gauss-Hermite roots (ascending), the outermost
+// values beyond them (binary search for the bracketing roots).
+__device__ __forceinline__ double spectrum_at(const SolveArgs &a, int64_t c, int l, double r) {
+    const double *Jc = a.Jsca + ((size_t)c * a.L + l) * a.Q;
+    const double *x = a.roots;
+    const int Q = a.Q;
+    if (Q == 1 || r <= x[0]) return Jc[0];
+    if (r >= x[Q - 1]) return Jc[Q - 1];
+    int lo = 0, hi = Q - 1;   // x[lo] <= r < x[hi]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (x[mid] <= r) lo = mid;
+        else hi = mid;
+    }
+    const double t = (r - x[lo]) / (x[lo + 1] - x[lo]);
+    return Jc[lo] + t * (Jc[lo + 1] - Jc[lo]);
+}
+
 // k1 = 1 + a_q/c: the comoving shift a_q (1 - v/c) - v is a_q - v k1 (no division).
+// SCAT: isotropic coherent scattering adds chi_sca to the opacity and chi_sca J to the
+// emissivity (Sec. 3.3, eq. 'GFE' with Psi+ = chi_sca J and Psi- = 0), both interpolated
+// between the point's cells, J read at the point's comoving offset from the line centre.
+template <bool SCAT = false>
 __device__ __forceinline__ Pt64 point64(const SolveArgs &a, int l, double aq, double k1, int k, const PairSmem64 &S) {
     constexpr double kCsp = kC / kSqrtPi;
     const double v = S.v[k], ibk = S.ib[k], w = S.w[k];
     const double *pa = a.line + (int64_t)S.ca[k] * 2 * a.L, *pb = a.line + (int64_t)S.cb[k] * 2 * a.L;
-    Pt64 p{0.0, 0.0, 0.0, 0.0};
+    Pt64 p{0.0, 0.0, 0.0, 0.0, 0.0};
     const int o0 = a.ovl_off[l], o1 = a.ovl_off[l + 1];
     const double base = aq - v * k1;
     for (int i = o0; i < o1; i++) {
@@ -111,7 +139,15 @@ __device__ __forceinline__ Pt64 point64(const SolveArgs &a, int l, double aq, do
         const double ch = ((1.0 - w) * pa[2 * ov.l2 + 1] + w * pb[2 * ov.l2 + 1]) * phi;
         p.eta += et;
         p.chi += ch;
-        if (i == o0) { p.etal = et; p.chil = ch; }
+        if (i == o0) { p.etal = et; p.chil = ch; p.phil = phi; }
+    }
+    if constexpr (SCAT) {
+        const int64_t ca = S.ca[k], cb = S.cb[k];
+        const double r = base * ibk;
+        const double xs = (1.0 - w) * a.chi_sca[ca] + w * a.chi_sca[cb];
+        const double Jk = (1.0 - w) * spectrum_at(a, ca, l, r) + w * spectrum_at(a, cb, l, r);
+        p.chi += xs;
+        p.eta += xs * Jk;
     }
     return p;
 }
@@ -130,34 +166,66 @@ __device__ __forceinline__ Pt64 point64(const SolveArgs &a, int l, double aq, do
 //   u - Lambda* S_o = sigma (psi_b + psi_f)/D,    1 - Lambda* = sigma (Phi_b iota_b + Phi_f iota_f)/D,
 // all sums of non-negative terms. An empty half contributes Phi iota = 1, psi = I_o and
 // dtau = 0 (the origin row is then the boundary row).
+//
+// Band-diagonal ALO (Sec. 3.4, eq. 'ALO'; B = bandwidth): with m the point next to the
+// origin and m-1 the one before it, psi_m = g_1 S_m + g_2 S_{m-1} + r_2, where
+//   g_1 = t_m iota_m, g_2 = t_{m-1} iota_{m-1} iota_m   (d psi_m / d S at those points),
+//   r_1 = psi_{m-1} iota_m, r_2 = psi_{m-2} iota_{m-1} iota_m;
+// so the entries of row ko of the inverse are Lambda*_{ko,k_j} = sigma g_j / D, and the
+// effective intensity of bandwidth b keeps only the other lines' share of S at the band
+// points: sigma (g_1 S_oth,m [+ g_2 S_oth,m-1] + r_b)/D, again a sum of non-negative terms.
+// Missing points have g = 0 (and r_2 = r_1).
 struct Side64 {
     double phi_iota, psi, dtau;
+    double g[2], r[2], h[2], so[2];   // band weights, reduced psi, phi_l/chi and S_other at m, m-1
 };
 
+// Per-row history of the sweep for the band terms.
+struct Row64 {
+    double t, iota, psi_in, h, so;
+};
+
+template <int B, bool SCAT>
 __device__ __forceinline__ Side64 sweep64(const SolveArgs &a, int l, double aq, double k1, double nu_o, int kstart,
                                           int kend, int step, const PairSmem64 &S, Pt64 &po) {
     // kstart: far end, kend: origin; step = +1 (backward half) or -1 (forward half)
-    Pt64 p = point64(a, l, aq, k1, kstart, S);
+    Pt64 p = point64<SCAT>(a, l, aq, k1, kstart, S);
     double chi_prev = fmax(p.chi, a.chi_min);
     double S_prev = p.eta / chi_prev;
+    double h_prev = 0.0, so_prev = 0.0;
+    if constexpr (B > 0) {
+        h_prev = p.phil / chi_prev;
+        so_prev = (p.eta - p.etal) / chi_prev;
+    }
     const double I = planck_d(nu_o * (1.0 - S.v[kstart] / kC), a.T_cmb);
     double Phi = 0.0, iota = 0.0, psi = 0.0, dt_prev = 0.0;
+    Row64 r1{0, 0, 0, 0, 0}, r2{0, 0, 0, 0, 0};
     int row = 0;
     for (int k = kstart + step;; k += step) {
-        Pt64 q = point64(a, l, aq, k1, k, S);
+        Pt64 q = point64<SCAT>(a, l, aq, k1, k, S);
         const double chi = fmax(q.chi, a.chi_min);
         const double Sk = q.eta / chi;
         const double dsk = S.ds[step > 0 ? k - 1 : k];
         const double dt = fmax(0.5 * (chi_prev + chi) * dsk, a.dtau_min);
+        double t, psi_in;
         if (row == 0) {
+            t = 0.5 * dt;
+            psi_in = I;
             Phi = 0.5 * dt + 1.0;
             iota = 1.0 / (1.0 + dt * Phi);
             psi = (0.5 * dt * S_prev + I) * iota;
         } else {
-            const double t = 0.5 * (dt_prev + dt);
+            t = 0.5 * (dt_prev + dt);
+            psi_in = psi;
             Phi = t + Phi * iota;
             iota = 1.0 / (1.0 + dt * Phi);
             psi = (t * S_prev + psi) * iota;
+        }
+        if constexpr (B > 0) {
+            r2 = r1;
+            r1 = Row64{t, iota, psi_in, h_prev, so_prev};
+            h_prev = q.phil / chi;
+            so_prev = (q.eta - q.etal) / chi;
         }
         row++;
         dt_prev = dt;
@@ -169,11 +237,28 @@ __device__ __forceinline__ Side64 sweep64(const SolveArgs &a, int l, double aq, 
             break;
         }
     }
-    return Side64{Phi * iota, psi, dt_prev};
+    Side64 s{Phi * iota, psi, dt_prev, {0.0, 0.0}, {psi, psi}, {0.0, 0.0}, {0.0, 0.0}};
+    if constexpr (B > 0) {
+        s.g[0] = r1.t * r1.iota;
+        s.r[0] = r1.psi_in * r1.iota;
+        s.h[0] = r1.h;
+        s.so[0] = r1.so;
+        s.r[1] = s.r[0];
+        if (row >= 2) {
+            s.g[1] = r2.t * r2.iota * r1.iota;
+            s.r[1] = r2.psi_in * r2.iota * r1.iota;
+            s.h[1] = r2.h;
+            s.so[1] = r2.so;
+        }
+    }
+    return s;
 }
 
+// NA accumulators per bin: sum u, L, Jeff, 1 - L, then Jeff of bandwidths 1..B.
+template <int B, bool SCAT>
 __global__ void k_feautrier64(SolveArgs a) {
     extern __shared__ double smem[];
+    constexpr int NA = 4 + B;
     const int L = a.L, Q = a.Q, F = L * Q;
     const int kmax = a.kmax;
     // G groups of TG threads; with G > 1 each group is one warp and solves the pairs
@@ -188,17 +273,20 @@ __global__ void k_feautrier64(SolveArgs a) {
     S.v = S.ds + kmax;
     S.ib = S.v + kmax;
     S.w = S.ib + kmax;
-    double *acc_all = smem + (size_t)G * 4 * kmax;   // [G][F][4]
-    double *acc = acc_all + (size_t)g * 4 * F;
-    S.ca = reinterpret_cast<int32_t *>(acc_all + (size_t)G * 4 * F) + (size_t)g * 2 * kmax;
+    double *acc_all = smem + (size_t)G * 4 * kmax;   // [G][F][NA]
+    double *acc = acc_all + (size_t)g * NA * F;
+    // band ALO: per pair, [G][F][2][B] coupling terms of the band points before the sum over bins
+    double *mac = acc_all + (size_t)G * NA * F + (size_t)g * 2 * B * F;
+    S.ca = reinterpret_cast<int32_t *>(acc_all + (size_t)G * (NA + 2 * B) * F) + (size_t)g * 2 * kmax;
     S.cb = S.ca + kmax;
     int64_t o = blockIdx.x;
     if (a.olist) {
         if ((int)blockIdx.x >= *a.ocount) return;
         o = a.olist[blockIdx.x];
     }
-    for (int f = t; f < 4 * F; f += TG) acc[f] = 0.0;
+    for (int f = t; f < NA * F; f += TG) acc[f] = 0.0;
     const double bo = a.b[o];
+    const double invP = 1.0 / a.P;
     for (int p = g; p < a.P; p += G) {
         const int rf = a.pf[p], rb = a.pb[p];
         const int64_t ofb = a.ray_off[o * a.R + rb], ofl = a.ray_off[o * a.R + rf];
@@ -228,20 +316,24 @@ __global__ void k_feautrier64(SolveArgs a) {
             const double k1 = 1.0 + aq / kC;
             const double nu_o = a.lc[l].nu * k1;
             Side64 sb, sf;
-            Pt64 po{0, 0, 0, 0};
-            double u, lam, uml, oml;
+            Pt64 po{0, 0, 0, 0, 0};
+            double u, lam, uml, oml, jb[2] = {0.0, 0.0};
             if (K == 1) {
                 const double I = planck_d(nu_o, a.T_cmb);
                 u = I; lam = 0.0; uml = I; oml = 1.0;
-                po = point64(a, l, aq, k1, Kb, S);
+                jb[0] = jb[1] = I;
+                po = point64<SCAT>(a, l, aq, k1, Kb, S);
                 po.chi = fmax(po.chi, a.chi_min);
+                if (B > 0)
+                    for (int j = 0; j < 2 * B; j++) mac[f * 2 * B + j] = 0.0;
             } else {
-                if (Kb > 0) sb = sweep64(a, l, aq, k1, nu_o, 0, Kb, +1, S, po);
-                if (Kf > 0) sf = sweep64(a, l, aq, k1, nu_o, K - 1, Kb, -1, S, po);
+                if (Kb > 0) sb = sweep64<B, SCAT>(a, l, aq, k1, nu_o, 0, Kb, +1, S, po);
+                if (Kf > 0) sf = sweep64<B, SCAT>(a, l, aq, k1, nu_o, K - 1, Kb, -1, S, po);
                 if (Kb == 0 || Kf == 0) {
                     const double Io = planck_d(nu_o, a.T_cmb);
-                    if (Kb == 0) sb = Side64{1.0, Io, 0.0};
-                    if (Kf == 0) sf = Side64{1.0, Io, 0.0};
+                    const Side64 empty{1.0, Io, 0.0, {0.0, 0.0}, {Io, Io}, {0.0, 0.0}, {0.0, 0.0}};
+                    if (Kb == 0) sb = empty;
+                    if (Kf == 0) sf = empty;
                 }
                 const double So = po.eta / po.chi;
                 const double sig = 2.0 / (sb.dtau + sf.dtau);
@@ -252,32 +344,58 @@ __global__ void k_feautrier64(SolveArgs a) {
                 lam = iD;
                 uml = sig * (sb.psi + sf.psi) * iD;
                 oml = sig * pi2 * iD;
+                if constexpr (B > 0) {
+                    const double rb1 = sb.g[0] * sb.so[0] + sb.r[0], rf1 = sf.g[0] * sf.so[0] + sf.r[0];
+                    jb[0] = sig * (rb1 + rf1) * iD;
+                    if constexpr (B > 1)
+                        jb[1] = sig * (sb.g[0] * sb.so[0] + sb.g[1] * sb.so[1] + sb.r[1] +
+                                       sf.g[0] * sf.so[0] + sf.g[1] * sf.so[1] + sf.r[1]) * iD;
+                    const double sD = sig * iD;
+                    for (int j = 0; j < B; j++) {
+                        mac[f * 2 * B + j] = sD * sb.g[j] * sb.h[j];
+                        mac[f * 2 * B + B + j] = sD * sf.g[j] * sf.h[j];
+                    }
+                }
             }
             const double ichi = 1.0 / po.chi;
-            acc[4 * f + 0] += u;
-            acc[4 * f + 1] += lam * po.chil * ichi;
-            acc[4 * f + 2] += uml + lam * (po.eta - po.etal) * ichi;
-            acc[4 * f + 3] += oml + lam * (po.chi - po.chil) * ichi;
+            const double oth = lam * (po.eta - po.etal) * ichi;
+            acc[NA * f + 0] += u;
+            acc[NA * f + 1] += lam * po.chil * ichi;
+            acc[NA * f + 2] += uml + oth;
+            acc[NA * f + 3] += oml + lam * (po.chi - po.chil) * ichi;
+            for (int j = 0; j < B; j++) acc[NA * f + 4 + j] += jb[j] + oth;
+        }
+        if constexpr (B > 0) {
+            // coupling coefficients of this pair's band points: weighted sums over each
+            // line's bins (fixed order), times chi_int,l(o)/P
+            if (G > 1) __syncwarp(); else __syncthreads();
+            for (int tk = t; tk < 2 * B * L; tk += TG) {
+                const int l = tk / (2 * B), sj = tk - l * 2 * B;
+                double s = 0.0;
+                for (int q = 0; q < Q; q++) s += a.weights[q] * mac[(l * Q + q) * 2 * B + sj];
+                const int side = sj / B, j = sj - side * B;
+                const int r = side ? rf : rb;
+                a.Mb[(((size_t)o * L + l) * a.R + r) * B + j] = s * invP * a.line[(o * L + l) * 2 + 1];
+            }
         }
     }
     __syncthreads();
-    const double invP = 1.0 / a.P;
-    for (int tt = threadIdx.x; tt < 4 * L; tt += blockDim.x) {
-        const int l = tt >> 2, k = tt & 3;
+    for (int tt = threadIdx.x; tt < NA * L; tt += blockDim.x) {
+        const int l = tt / NA, k = tt - l * NA;
         double s = 0.0;
         for (int q = 0; q < Q; q++) {
-            double v = acc_all[4 * (l * Q + q) + k];
-            for (int gg = 1; gg < G; gg++) v += acc_all[(size_t)gg * 4 * F + 4 * (l * Q + q) + k];
+            double v = acc_all[NA * (l * Q + q) + k];
+            for (int gg = 1; gg < G; gg++) v += acc_all[(size_t)gg * NA * F + NA * (l * Q + q) + k];
             s += a.weights[q] * v;
         }
         s *= invP;
-        double *dst = k == 0 ? a.J : (k == 1 ? a.Lout : (k == 2 ? a.Jeff : a.Lc));
+        double *dst = k == 0 ? a.J : (k == 1 ? a.Lout : (k == 2 ? a.Jeff : (k == 3 ? a.Lc : a.Jeffb + (size_t)(k - 4) * a.n * L)));
         dst[o * L + l] = s;
     }
     if (a.Jnu)
         for (int f = threadIdx.x; f < F; f += blockDim.x) {
-            double v = acc_all[4 * f];
-            for (int gg = 1; gg < G; gg++) v += acc_all[(size_t)gg * 4 * F + 4 * f];
+            double v = acc_all[NA * f];
+            for (int gg = 1; gg < G; gg++) v += acc_all[(size_t)gg * NA * F + NA * f];
             a.Jnu[o * F + f] = v * invP;
         }
 }
@@ -555,6 +673,33 @@ __global__ void k_image32(ImageArgs a) {
 
 }  // namespace
 
+namespace {
+// Largest |a_new - a_old| / a_new over m values into *word (as the bits of a double, which
+// order like the values for non-negative doubles); NaN counts as infinity.
+__global__ void k_vec_max_rel_change(int64_t m, const double *a_new, const double *a_old, unsigned long long *word) {
+    double mx = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+        double d = fabs(a_new[i] - a_old[i]) / a_new[i];
+        if (!(d <= INFINITY)) d = INFINITY;
+        mx = fmax(mx, d);
+    }
+    unsigned long long bits = __double_as_longlong(mx);
+    for (int d = 16; d; d >>= 1) {
+        const unsigned long long o = __shfl_down_sync(0xffffffffu, bits, d);
+        bits = o > bits ? o : bits;
+    }
+    if ((threadIdx.x & 31) == 0) atomicMax(word, bits);
+}
+}  // namespace
+
+int mg_launch_max_rel_change(mg_ctx *ctx, int64_t m, const double *a_new, const double *a_old,
+                             unsigned long long *word) {
+    MG_CUDA(cudaMemsetAsync(word, 0, sizeof(unsigned long long), ctx->stream));
+    k_vec_max_rel_change<<<4 * 152, 256, 0, ctx->stream>>>(m, a_new, a_old, word);
+    MG_CUDA(cudaGetLastError());
+    return MG_OK;
+}
+
 int mg_launch_line_data(mg_ctx *ctx) {
     if (ctx->opt.precision == MG_MIXED) return mg_launch_line_data_mixed(ctx);
     const int64_t m = ctx->n * ctx->n_lines;
@@ -610,9 +755,13 @@ static int launch_fp64(mg_ctx *ctx, const int32_t *olist, const int32_t *ocount,
     a.err = ctx->d_err;
     a.olist = olist;
     a.ocount = ocount;
+    const int B = olist ? 0 : ctx->band_cur;   // the band ALO is built for FP64 contexts
+    a.Jeffb = ctx->d_Jeffb;
+    a.Mb = ctx->d_Mb;
     const int F = a.L * a.Q;
     auto smem_for = [&](int G) {
-        return (size_t)G * (sizeof(double) * ((size_t)a.kmax * 4 + 4 * (size_t)F) + sizeof(int32_t) * 2 * (size_t)a.kmax);
+        return (size_t)G * (sizeof(double) * ((size_t)a.kmax * 4 + (4 + 3 * (size_t)B) * F) +
+                            sizeof(int32_t) * 2 * (size_t)a.kmax);
     };
     size_t smem = smem_for(1);
     if (smem > 227 * 1024)
@@ -627,13 +776,21 @@ static int launch_fp64(mg_ctx *ctx, const int32_t *olist, const int32_t *ocount,
         a.groups = (a.P + rounds - 1) / rounds;
     }
     smem = smem_for(a.groups);
-    MG_CUDA(cudaFuncSetAttribute(k_feautrier64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const bool sca = !olist && ctx->sca_on;
+    void (*kern)(SolveArgs) = sca ? (B == 0 ? k_feautrier64<0, true> : (B == 1 ? k_feautrier64<1, true> : k_feautrier64<2, true>))
+                                  : (B == 0 ? k_feautrier64<0, false> : (B == 1 ? k_feautrier64<1, false> : k_feautrier64<2, false>));
+    if (sca) {
+        a.chi_sca = ctx->d_chisca;
+        a.Jsca = ctx->d_Jsca;
+        a.Jnu = ctx->d_Jsca_new;
+    }
+    MG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int threads = a.groups > 1 ? 32 * a.groups : ((F + 31) / 32) * 32;
     if (threads > 256) threads = 256;
     if (!olist) MG_CUDA(cudaMemsetAsync(ctx->d_err, 0, 4, ctx->stream));
     {
         MgTimed t(ctx, olist ? "feautrier_fp64_promoted" : "feautrier_fp64");
-        k_feautrier64<<<grid, threads, smem, ctx->stream>>>(a);
+        kern<<<grid, threads, smem, ctx->stream>>>(a);
     }
     MG_CUDA(cudaGetLastError());
     return MG_OK;

@@ -84,6 +84,7 @@ struct MixArgs {
     int32_t kmax;
     int32_t overlap;             // some line overlaps another
     int32_t *err;
+    unsigned long long *work;    // optional: point-bin updates the warp kernel executed
 };
 
 __device__ __forceinline__ float planck_f(const MixArgs &a, float nu_g) {
@@ -602,7 +603,7 @@ __device__ __forceinline__ void sweep_half(const MixArgs &a, const SweepK &k, in
                                            int rnext, float nu_g, const float4 Ao, const float4 Do, RingPt *rg,
                                            float4 *rl, ElemWin<G> &w, int &bf, bool &pre, BinState<NB> &st,
                                            float (&pi)[NB], float (&ps)[NB], float (&dt)[NB], float aq_lo,
-                                           float aq_hi) {
+                                           float aq_hi, int &npts) {
     const int lane = threadIdx.x & 31;
     const int64_t off = a.ray_off[o * a.R + r];
     const int len = (int)(a.ray_off[o * a.R + r + 1] - off);
@@ -681,6 +682,7 @@ __device__ __forceinline__ void sweep_half(const MixArgs &a, const SweepK &k, in
             const float4 A = rg[0].a;
             const float vfar = -A.z / (A.x - A.z * (float)(1.0 / kC));   // v = (v pz)/pz
             first_point<NB>(k, st, A, my[0], nu_g, vfar);
+            npts++;
             const float4 B = rg[0].b;
             qp = make_float2(B.x, B.y);
             far1 = false;
@@ -712,6 +714,7 @@ __device__ __forceinline__ void sweep_half(const MixArgs &a, const SweepK &k, in
             unsigned proc = ~(farmask & f1 & f2) & all;
             if (j) proc &= ~1u;   // point 0 of the first chunk is the far end, done above
             const bool dense_chunk = (proc | (j ? 1u : 0u)) == all;
+            npts += dense_chunk ? cnt - j : __popc(proc);
 #pragma unroll 1
             for (int seg = 0; seg < 2; seg++) {
                 if (dense_chunk) {   // nothing to skip in this chunk: the unrolled sweep
@@ -744,6 +747,7 @@ __device__ __forceinline__ void sweep_half(const MixArgs &a, const SweepK &k, in
                 far1 = farmask & 1u;
             }
         } else {
+            npts += cnt - j;
 #pragma unroll 1
             for (int seg = 0; seg < 2; seg++) {
                 if (floor_needed) dense(std::true_type{}, seg ? cnt : mid);
@@ -760,6 +764,7 @@ __device__ __forceinline__ void sweep_half(const MixArgs &a, const SweepK &k, in
     } while (xnext >= 0);
     if (pre) bf ^= 1;   // the next half-ray's first window sits in the other buffer
     step_point<NB>(k, st, Ao, Do, qp);   // the origin
+    npts++;
     bin_results<NB>(st, pi, ps, dt);
 }
 
@@ -814,6 +819,7 @@ __device__ __forceinline__ void solve_item(const MixArgs &a, int64_t o, int l0, 
     }
     int bf = 0;
     bool pre = false;
+    int npts = 0;   // points swept (warp-uniform), for the executed-work count
     for (int p = 0; p < a.P; p++) {
         const int rb = a.pb[p], rf = a.pf[p];
         const int rn = p + 1 < a.P ? a.pb[p + 1] : -1;
@@ -821,7 +827,7 @@ __device__ __forceinline__ void solve_item(const MixArgs &a, int64_t o, int l0, 
 #pragma unroll 1
         for (int h = 0; h < 2; h++) {   // backward half, then forward half (one code copy)
             sweep_half<G, NB, SKIP>(a, k, o, l0, grp, h ? rf : rb, h ? rn : rf, nu_g, Ao, Do, rg, rl, w, bf, pre,
-                                    st, pif, psf, dtf, aq_lo, aq_hi);
+                                    st, pif, psf, dtf, aq_lo, aq_hi, npts);
             if (h == 0) {
 #pragma unroll
                 for (int i = 0; i < NB; i++) {
@@ -861,6 +867,10 @@ __device__ __forceinline__ void solve_item(const MixArgs &a, int64_t o, int l0, 
         }
     }
     cp_async_wait_all();
+    if (a.work && lane == 0) {
+        const int lines = min(G, a.L - l0);
+        atomicAdd(a.work, (unsigned long long)npts * (unsigned long long)(lines * Q));
+    }
     // weighted sums over each line's bins: fixed shuffle tree in FP64 within the lane group
     const double invP = 1.0 / a.P;
     double s[4] = {0.0, 0.0, 0.0, 0.0};
@@ -995,6 +1005,7 @@ static void fill_args(mg_ctx *ctx, MixArgs &a) {
     a.Jnu = ctx->opt.spectrum ? ctx->d_Jnu : nullptr;
     a.kmax = (int32_t)ctx->max_pair_len;
     a.err = ctx->d_err;
+    a.work = ctx->opt.profile ? ctx->d_scal + 7 : nullptr;   // executed updates, profiling runs only
     bool overlap = false;
     for (int l = 0; l < L; l++) overlap |= (ctx->h_ovl_off[l + 1] - ctx->h_ovl_off[l]) > 1;
     a.overlap = overlap;

@@ -230,6 +230,9 @@ extern "C" int mg_update_populations_noalloc(mg_ctx *ctx, const double *d_pops_o
     if (!d_pops_old || !d_pops_new) return mg_fail(ctx, MG_ERR_ARG, "mg_update_populations_noalloc: null buffer");
     if (!ctx->have_rad || !ctx->d_Lc)
         return mg_fail(ctx, MG_ERR_STATE, "mg_update_populations_noalloc: run mg_formal_solve first");
+    if (ctx->band_cur > 0)
+        return mg_fail(ctx, MG_ERR_STATE,
+                       "mg_update_populations_noalloc: needs the diagonal ALO (the band ALO's solver allocates)");
     if (ctx->n > kNaMaxCells)
         return mg_fail(ctx, MG_ERR_CAPACITY,
                        "mg_update_populations_noalloc: at most 2097152 cells per call (static scratch of 512 KiB)");
