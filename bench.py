@@ -1,20 +1,31 @@
 """Benchmark of the ALI hot path on synthetic inputs shaped like the paper's models.
 
-A step is one accelerated Lambda iteration on the 3D clumpy cloud (50k points, 48 HEALPix
-rays = 24 ray pairs, 5-level rotor with 4 lines x 31 Gauss-Hermite bins): line data ->
+Default line (the headline): the Keplerian disc -- 200k points in a flared disc, 192
+HEALPix rays (96 ray pairs), a 20-level linear rotor with 19 lines x 63 Gauss-Hermite
+bins -- dense enough that the line-centre optical depth of the low lines reaches ~1e4, in
+mixed precision: the FP32 formal solve with the cancellation-free elimination, FP64
+statistical equilibrium. A step is one accelerated Lambda iteration: line data ->
 Feautrier formal solve of every (point, ray pair, bin) -> statistical equilibrium ->
 convergence measure. The rays are traced once before the timed region (the mesh is
 static across iterations, Sec. 3.2).
+fp64_elimination: the same construction at 10k points, one step with the cells of
+optical depth above 1e2 (diagonal ALO weight >= 0.99) solved again in FP64, against the
+FP32 step: promoted share, time, and how far the FP32 results were from the FP64 ones.
 
 metric: point-ray-pair-frequency Feautrier solves per second (whole job).
 value : device-resident inputs, CUDA events around K steps on the library's stream.
 e2e   : the same steps through the C ABI with host buffers: populations copied in from
         pinned memory and read back every step.
+ali   : the second half of the metric, in the same run: ALI time to converge (max relative
+        population change < 1e-6) on the 3D clumpy cloud (50k points, 48 rays, 5-level
+        rotor, 4 lines x 31 bins): plain FP64 from LTE, mixed from LTE, and mixed from
+        the populations of a network trained in the run on converged clouds of the same
+        species (held-out seeds), each with Ng off and on.
 Multi-GPU (torchrun): every rank solves its own independently seeded model; no
 collective on the data path (weak scaling); max time over ranks.
 
 --impl reference times the FP64 CPU oracle on host cores on a bounded sample of the
-same workload (the reference arm: there is no other implementation to run).
+disc (the reference arm: there is no other implementation to run).
 """
 from __future__ import annotations
 
@@ -32,11 +43,19 @@ sys.path.insert(0, ROOT)
 
 import numpy as np  # noqa: E402
 
-WORKLOAD = dict(workload="3D clumpy cloud, 50k points, k=16 symmetric NN, 48 rays (HEALPix nside=2), "
-                         "5-level linear rotor, 4 lines x 31 Gauss-Hermite bins, radial outflow to 10 km/s",
-                n_points=50_000, n_rays=48, n_lines=4, n_bins=31)
+DISC_N_H2_IN = 2.5e16   # n_H2 at the inner radius (m^-3): line-centre optical depths ~1e4
+DISC_TAU_FP64 = 100.0
+WORKLOAD = dict(workload="Keplerian disc, 200k points (flared, n ~ r^-1 exp(-z^2/2H^2), H/r = 0.1, T ~ r^-0.5, "
+                         "Keplerian velocity around 1 M_sun), 192 rays (HEALPix nside=4), 20-level linear rotor, "
+                         "19 lines x 63 Gauss-Hermite bins, line-centre optical depths up to ~1e4, mixed precision",
+                n_points=200_000, n_rays=192, n_lines=19, n_bins=63, n_h2_in=DISC_N_H2_IN)
+CLUMPY = dict(workload="3D clumpy cloud, 50k points, k=16 symmetric NN, 48 rays (HEALPix nside=2), "
+                       "5-level linear rotor, 4 lines x 31 Gauss-Hermite bins, radial outflow to 10 km/s",
+              n_points=50_000, n_rays=48, n_lines=4, n_bins=31)
 METRIC = "point-ray-pair-frequency Feautrier solves/s"
 UNIT = "solves/s"
+FLOPS_PER_UPDATE = 16.0   # FMA-pipe flops of one point-bin update of the FP32 sweep (FMA = 2)
+MUFU_PER_UPDATE = (1, 1)  # ex2, rcp per point-bin update
 
 
 def dist_env():
@@ -119,14 +138,19 @@ def whole_job_rate(units_per_rank, steps, world_size, ms_max):
 
 def build_model(seed):
     import synthetic as syn
-    return syn.model_clumpy_3d(n=WORKLOAD["n_points"], seed=seed)
+    return syn.model_disc(n=WORKLOAD["n_points"], seed=seed, n_h2_in=DISC_N_H2_IN)
 
 
-def recorded_traffic(kernel_variant):
+def build_clumpy(seed):
+    import synthetic as syn
+    return syn.model_clumpy_3d(n=CLUMPY["n_points"], seed=seed)
+
+
+def recorded_traffic(kernel_variant, record="feautrier_warp_disc200k.json"):
     """DRAM bytes per launch of the formal-solve kernel from the committed ncu record,
     used only while the kernel's source is unchanged since the capture (else None)."""
     import hashlib
-    rec_p = os.path.join(ROOT, "profiles", "feautrier_warp_clumpy50k.json")
+    rec_p = os.path.join(ROOT, "profiles", record)
     if not os.path.exists(rec_p):
         return None
     rec = json.load(open(rec_p))
@@ -147,7 +171,7 @@ def peaks():
 
 
 # ------------------------------------------------------------------ oracle (CPU) timing
-def time_oracle(model, target_s=15.0, seed=0):
+def time_oracle(model, target_s=15.0, seed=0, k0=4):
     """Times the FP64 oracle's formal solve on a bounded sample of origin points, grown
     until it takes about target_s seconds; returns solves/s, threads and the sample."""
     from oracle import Oracle
@@ -157,7 +181,7 @@ def time_oracle(model, target_s=15.0, seed=0):
     rng = np.random.default_rng(seed)
     P = o.dirs.shape[0] // 2
     F = model.species.n_lines * o.Q
-    k = 16
+    k = k0
     while True:
         origins = np.sort(rng.choice(model.n, k, replace=False))
         t0 = time.perf_counter()
@@ -170,24 +194,94 @@ def time_oracle(model, target_s=15.0, seed=0):
     return solves / dt, threads, f"{k} of {model.n} origin points ({solves} solves, {dt:.1f} s)"
 
 
-def time_oracle_one_thread(model, target_s=5.0, seed=1):
-    """The same oracle timing on one host thread (a smaller sample)."""
-    from oracle import Oracle
-    o = Oracle(model, nthreads=1)
-    pops = o.lte()
-    rng = np.random.default_rng(seed)
-    P = o.dirs.shape[0] // 2
-    F = model.species.n_lines * o.Q
-    k = 2
-    while True:
-        origins = np.sort(rng.choice(model.n, k, replace=False))
+# ------------------------------------------------------------------ ALI time to converge
+def train_clumpy_network(species, n_models=100, n_points=3000, seed0=1000):
+    """Network for learned initial populations of the clumpy cloud's species: converged
+    populations of seeded cloud and disc models with that species (seeds from seed0,
+    held out from the evaluated model) -> trained in the library's BF16 kernels."""
+    from paper_1912_08445_gb300 import learned
+    t0 = time.perf_counter()
+    models = learned.corpus_models(n_models, seed0, n_points=n_points, species=species)
+    X, Y, reps = learned.build_corpus(models, ng_period=4)
+    corpus_s = time.perf_counter() - t0
+    net, trep = learned.train_network(X, Y, species.n_lev, epochs=30, batch=4096, lr=2e-3)
+    return net, {"corpus_models": n_models, "corpus_points_each": n_points, "corpus_rows": int(X.shape[0]),
+                 "corpus_seconds": round(corpus_s, 2), "train_seconds": round(trep["seconds"], 2),
+                 "loss_first_last": [round(trep["first_loss"], 4), round(trep["last_loss"], 4)]}
+
+
+def ali_time_to_converge(model, net, stream, tol=1e-6, max_iter=300):
+    """ALI from LTE (FP64 and mixed) and from the network (mixed) to a max relative change
+    below tol, Ng off and on; the rays are traced beforehand (untimed). The timed region
+    covers the initial populations (the network's inference included) and the whole
+    iteration loop, with a device synchronisation on both sides."""
+    import torch
+    import paper_1912_08445_gb300 as mg
+    tune = mg.Context(precision=mg.MG_MIXED)
+    tune.set_stream(stream.cuda_stream)
+    tune.load_model(model)
+    tune.trace_rays()
+    tune.init_populations()
+    variant = tune.autotune(reps=1)[0]
+    tune.close()
+    runs = {}
+    for ng in (0, 4):
+        for name, prec, start in (("fp64_lte", mg.MG_FP64, "lte"), ("mixed_lte", mg.MG_MIXED, "lte"),
+                                  ("mixed_network", mg.MG_MIXED, "network")):
+            ctx = mg.Context(precision=prec, tol=tol, max_iter=max_iter, ng_period=ng)
+            ctx.set_stream(stream.cuda_stream)
+            ctx.load_model(model)
+            ctx.trace_rays()
+            if prec == mg.MG_MIXED:
+                ctx.set_variant(variant)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            if start == "lte":
+                ctx.init_populations()
+            else:
+                ctx.init_populations_mlp(net)
+            rep, rc = ctx.iterate(allow_not_converged=True)
+            torch.cuda.synchronize()
+            runs[f"{name}_ng{ng}"] = {"seconds": round(time.perf_counter() - t0, 5), "iterations": rep["iterations"],
+                                      "converged": bool(rep["converged"])}
+            ctx.close()
+    return runs, variant
+
+
+def fp64_elimination(stream, variant, n_points=10_000):
+    """The disc's construction at n_points: one ALI step in FP32 and one with the cells of
+    optical depth above 1e2 (diagonal ALO weight >= 1 - 1/100) solved again in FP64, from
+    the same LTE start; the promoted share, both times, and the largest relative
+    differences of J and of the populations after the step."""
+    import torch
+    import paper_1912_08445_gb300 as mg
+    import synthetic as syn
+    m = syn.model_disc(n=n_points, seed=0, n_h2_in=DISC_N_H2_IN)
+    out = {"n_points": n_points, "tau_fp64": DISC_TAU_FP64}
+    res = {}
+    for tau in (0.0, DISC_TAU_FP64):
+        c = mg.Context(precision=mg.MG_MIXED, tau_fp64=tau)
+        c.set_stream(stream.cuda_stream)
+        c.load_model(m)
+        c.trace_rays()
+        c.init_populations()
+        c.set_variant(variant)
+        c.formal_solve()          # warm-up (kernel loading)
+        c.init_populations()
+        torch.cuda.synchronize()
         t0 = time.perf_counter()
-        o.formal_solve(pops, origins)
-        dt = time.perf_counter() - t0
-        if dt > target_s / 4 or k >= model.n:
-            break
-        k = min(model.n, int(k * max(2.0, target_s / 4 / max(dt, 1e-3))))
-    return k * P * F / dt, f"{k} origin points, 1 thread, {dt:.1f} s"
+        c.formal_solve()
+        J = c.get_radiation()[0]
+        c.update_populations()
+        torch.cuda.synchronize()
+        res[tau] = (time.perf_counter() - t0, J, c.get_populations(), c.promoted_cells() if tau > 0 else 0)
+        c.close()
+    (t32, J32, p32, _), (t64, J64, p64, prom) = res[0.0], res[DISC_TAU_FP64]
+    rel = lambda a, b: float(np.max(2 * np.abs(a - b) / (np.abs(a) + np.abs(b))))
+    out.update(promoted_cells=int(prom), promoted_share=round(prom / n_points, 4), step_s_fp32=round(t32, 4),
+               step_s_with_fp64=round(t64, 3), slowdown=round(t64 / t32, 1), J_max_rel_diff=rel(J32, J64),
+               populations_max_rel_diff=rel(p32, p64))
+    return out
 
 
 # ------------------------------------------------------------------ GPU arm
@@ -195,22 +289,40 @@ def run_gpu(args):
     import torch
     import torch.distributed as dist
     import paper_1912_08445_gb300 as mg
+    import synthetic as syn
 
     ws, rank, local = dist_env()
     if ws > 1:
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(local)
     stream = torch.cuda.Stream()
-    model = build_model(seed=rank)
-    prec = mg.MG_MIXED if args.precision == "mixed" else mg.MG_FP64
-    ctx = mg.Context(device=local, precision=prec, profile=0)
-    ctx.set_stream(stream.cuda_stream)
-    ctx.load_model(model)
-    st, _ = ctx.trace_rays()
-    ctx.init_populations()
-    tuned = ctx.autotune(reps=2) if prec == mg.MG_MIXED else (-1, None, 0)
-    solves, updates = ctx.work_counts()
+    clumpy_mode = args.workload == "clumpy"
+    spec = CLUMPY if clumpy_mode else WORKLOAD
+    tau_fp64 = 0.0
+    model = build_clumpy(seed=rank) if clumpy_mode else build_model(seed=rank)
     n, lev = model.n, model.species.n_lev
+    # launch variant: autotuned on the model itself (clumpy cloud) or on a 20k-point disc
+    # of the same construction (a full-size disc trial costs a formal solve per variant)
+    small = model if clumpy_mode else syn.model_disc(n=20_000, seed=rank, n_h2_in=DISC_N_H2_IN)
+    tune = mg.Context(precision=mg.MG_MIXED)
+    tune.set_stream(stream.cuda_stream)
+    tune.load_model(small)
+    tune.trace_rays()
+    tune.init_populations()
+    variant, _, n_tried = tune.autotune(reps=2)
+    tune.close()
+
+    def make_ctx(profile):
+        c = mg.Context(device=local, precision=mg.MG_MIXED, profile=profile, tau_fp64=tau_fp64)
+        c.set_stream(stream.cuda_stream)
+        c.load_model(model)
+        st_, _ = c.trace_rays()
+        c.init_populations()
+        c.set_variant(variant)
+        return c, st_
+
+    ctx, st = make_ctx(0)
+    solves, updates = ctx.work_counts()
 
     def step():
         ctx.formal_solve()
@@ -233,85 +345,106 @@ def run_gpu(args):
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1)
         clk = clocks.stop()
-
-        # per-kernel times of the dominant kernel (events on the same stream)
+        promoted = ctx.promoted_cells()
+        ctx.formal_solve()   # (untimed) radiation field of the final populations
+        max_L = float(np.max(ctx.get_radiation()[1]))
+        feats = ctx.features()
         ctx.close()
-        ctx = mg.Context(device=local, precision=prec, profile=1)
-        ctx.set_stream(stream.cuda_stream)
-        ctx.load_model(model)
-        ctx.trace_rays()
-        ctx.init_populations()
-        ctx.set_variant(tuned[0])
+
+        # per-kernel times and executed work (events on the same stream, profiling context)
+        ctx, _ = make_ctx(1)
         step()
         ctx.reset_kernel_times()
-        for _ in range(max(2, min(args.steps, 5))):
+        kreps = max(2, min(args.steps, 3))
+        for _ in range(kreps):
             step()
         kt = ctx.kernel_times()
+        executed = ctx.executed_work() / kreps
 
         # end to end through the C ABI with pinned host buffers
+        e2e_steps = max(2, min(args.steps, 5))
         h_in = torch.empty((n, lev), dtype=torch.float64, pin_memory=True).numpy()
         h_out = torch.empty((n, lev), dtype=torch.float64, pin_memory=True).numpy()
         h_in[:] = ctx.get_populations()
-        for _ in range(2):
-            ctx.set_populations(h_in); step(); ctx.get_populations(out=h_out)
+        ctx.set_populations(h_in); step(); ctx.get_populations(out=h_out)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        for _ in range(args.steps):
+        for _ in range(e2e_steps):
             ctx.set_populations(h_in)
             step()
             ctx.get_populations(out=h_out)
         torch.cuda.synchronize()
-        e2e_s = time.perf_counter() - t0
+        e2e_ms = (time.perf_counter() - t0) * 1e3 / e2e_steps * args.steps
+        ctx.close()
 
-    ms_max, e2e_ms_max = reduce_max([ms, e2e_s * 1e3], device=f"cuda:{local}")
+    ms_max, e2e_ms_max = reduce_max([ms, e2e_ms], device=f"cuda:{local}")
     if ws > 1:
         dist.barrier()
 
     if rank == 0:
         pk, pk_kind = peaks()
-        kname = "feautrier_mixed" if prec == mg.MG_MIXED else "feautrier_fp64"
-        k_ms, k_n = kt.get(kname, (float("nan"), 1))
+        rates = mg.measure_pipe_rates(local)
+        k_ms, k_n = kt.get("feautrier_mixed", (float("nan"), 1))
         k_avg = k_ms / max(k_n, 1)
-        # algorithmic work of one formal-solve launch: cell-frequency updates x flops per
-        # update (FP32: 16 FMA-pipe flops + 2 MUFU ops; FP64: 18 flops, exp and divide
-        # counted as one each)
-        flops_per_update = 18.0
-        if prec == mg.MG_MIXED:
-            peak = 152 * 128 * 2 * 2.07e9 / 1e12
-            peak_note = "FP32 FMA lanes x 2 x 2.07 GHz (derived)"
-        else:
-            peak = 1.25
-            peak_note = "nominal FP64 1.25 TFLOP/s (GB300)"
-        achieved = updates * flops_per_update / (k_avg * 1e-3) / 1e12
-        traffic = recorded_traffic(tuned[0]) if prec == mg.MG_MIXED else None
-        roof = {"bound": "alu", "achieved": round(achieved, 4), "peak": peak, "unit": "TFLOP/s",
-                "frac": round(achieved / peak, 4), "traffic": traffic, "kernel": kname,
-                "kernel_ms": round(k_avg, 3), "peak_source": peak_note,
-                "cell_freq_updates_per_launch": updates,
-                "hbm_algorithmic_GBps": round(st["n_elements"] * 16 / (k_avg * 1e-3) / 1e9, 2),
-                "hbm_algorithmic_frac_of_measured": round(st["n_elements"] * 16 / (k_avg * 1e-3) / 1e9 / pk["hbm_gbs"], 5)}
+        upd_s = executed / (k_avg * 1e-3)
+        fma_peak = max(rates["ffma"], rates["ffma2"])
+        achieved = FLOPS_PER_UPDATE * upd_s
+        mufu_time = upd_s * (MUFU_PER_UPDATE[0] / rates["ex2"] + MUFU_PER_UPDATE[1] / rates["rcp"])
+        hbm_bytes = st["n_elements"] * 16
+        traffic = recorded_traffic(variant, "feautrier_warp_clumpy50k.json" if clumpy_mode else
+                                   "feautrier_warp_disc200k.json")
+        roof = {"bound": "alu", "achieved": round(achieved / 1e12, 3), "peak": round(fma_peak / 1e12, 3),
+                "unit": "TFLOP/s", "frac": round(achieved / fma_peak, 4), "traffic": traffic,
+                "kernel": "k_feautrier_warp (feautrier_mixed)", "kernel_ms": round(k_avg, 3),
+                "peak_source": "measured in this run: max of scalar FFMA and packed FFMA2 flops/s "
+                               "(mg_measure_pipe_rates)",
+                "work": f"{FLOPS_PER_UPDATE:g} FMA-pipe flops per executed point-bin update (counted by the "
+                        "kernel: far-wing points it skips are not work)",
+                "executed_updates_per_launch": int(executed), "nominal_updates_per_launch": int(updates),
+                "mufu_frac": round(mufu_time, 4),
+                "mufu_note": "one ex2 and one rcp per update against the measured ex2 and rcp rates",
+                "pipe_rates": {k: float(f"{v:.4g}") for k, v in rates.items()},
+                "hbm_algorithmic_GBps": round(hbm_bytes / (k_avg * 1e-3) / 1e9, 2),
+                "hbm_algorithmic_frac": round(hbm_bytes / (k_avg * 1e-3) / 1e9 / pk["hbm_gbs"], 5),
+                "other_kernels_ms": {k: round(v[0] / max(v[1], 1), 3) for k, v in kt.items() if k != "feautrier_mixed"}}
+        # the second half of the metric: ALI time to converge on the clumpy cloud
+        ali = None
+        if args.ali_in_bench and not clumpy_mode:
+            clumpy = build_clumpy(seed=0)
+            net, train = train_clumpy_network(clumpy.species)
+            runs, cvar = ali_time_to_converge(clumpy, net, stream)
+            ali = {"metric": "ALI time to converge (max relative population change < 1e-6)", "unit": "s",
+                   "higher_is_better": False, "config": dict(CLUMPY, launch_variant=cvar),
+                   "runs": runs, "network": train,
+                   "speedup_mixed_network_vs_fp64": {
+                       f"ng{ng}": round(runs[f"fp64_lte_ng{ng}"]["seconds"] / runs[f"mixed_network_ng{ng}"]["seconds"], 1)
+                       for ng in (0, 4)}}
+        fp64e = None if (clumpy_mode or not args.fp64e) else fp64_elimination(stream, variant)
         cpu_v, cores, sample = time_oracle(model) if args.cpu_baseline else (None, None, None)
-        cpu_1 = time_oracle_one_thread(model) if args.cpu_baseline else None
         value = whole_job_rate(solves, args.steps, ws, ms_max)
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32+f64" if prec == mg.MG_MIXED else "f64", "data": "synthetic",
-            "config": dict(WORKLOAD, precision=args.precision, l2="inputs larger than L2 (ray store "
+            "dtype": "f32+f64", "data": "synthetic",
+            "config": dict(spec, precision="mixed (FP32 formal solve, cancellation-free elimination; FP64 "
+                           "statistical equilibrium)",
+                           l2="inputs larger than L2 (ray store "
                            f"{st['n_elements'] * 24 / 1e9:.2f} GB read per step)",
                            parallelism=f"replicas x{ws}", solves_per_step=solves,
                            cell_freq_updates_per_step=updates, mean_pair_len=round(st["mean_pair_len"], 1),
-                           launch_variant=tuned[0], variants_tried=tuned[2]),
+                           launch_variant=variant, variants_tried=n_tried, promoted_cells=promoted,
+                           max_L=round(max_L, 5), max_tau_sobolev_line0=float(f"{10 ** float(np.max(feats[:, 3])):.3g}"),
+                           tau_sobolev_line0_p99=float(f"{10 ** float(np.quantile(feats[:, 3], 0.99)):.3g}")),
             "e2e": {"value": whole_job_rate(solves, args.steps, ws, e2e_ms_max), "unit": UNIT,
                     "h2d_bytes_per_step": n * lev * 8, "d2h_bytes_per_step": n * lev * 8},
             "gpu_launches": 3 * args.steps,
             "clocks": clk,
             "roofline": roof,
+            "ali": ali,
+            "fp64_elimination": fp64e,
             "cpu_baseline": None if cpu_v is None else {"value": cpu_v, "unit": UNIT, "cores": cores,
-                                                        "kind": "oracle", "sample": sample,
-                                                        "single_thread": {"value": cpu_1[0], "unit": UNIT,
-                                                                          "sample": cpu_1[1]}},
+                                                        "kind": "oracle", "sample": sample},
             "peaks_source": pk_kind,
         }
         print(json.dumps(line))
@@ -321,32 +454,37 @@ def run_gpu(args):
 
 # ------------------------------------------------------------------ reference arm
 def run_reference(args):
+    """The oracle (FP64, all host threads) on the default workload: every step is the
+    formal solve of a bounded sample of origin points (16 of the disc's 200k, a few
+    seconds), whose rate is the line's value."""
     ws, rank, local = dist_env()
     if rank != 0:
         return
-    model = build_model(seed=0)
+    clumpy_mode = args.workload == "clumpy"
+    model = build_clumpy(seed=0) if clumpy_mode else build_model(seed=0)
     from oracle import Oracle
     threads = os.cpu_count() or 1
     o = Oracle(model, nthreads=threads)
     pops = o.lte()
     P = o.dirs.shape[0] // 2
     F = model.species.n_lines * o.Q
-    k = 256
+    k = 256 if clumpy_mode else 16
     rng = np.random.default_rng(0)
     origins = np.sort(rng.choice(model.n, k, replace=False))
     for _ in range(args.warmup):
-        o.formal_solve(pops, origins[:32])
+        o.formal_solve(pops, origins[:2])
     t0 = time.perf_counter()
     for _ in range(args.steps):
         J, L, E = o.formal_solve(pops, origins)
     dt = time.perf_counter() - t0
     solves = k * P * F * args.steps
     v = solves / dt
+    spec = CLUMPY if clumpy_mode else WORKLOAD
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": dict(WORKLOAD, precision="fp64"),
+        "config": dict(spec, precision="fp64"),
         "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
                          "sample": f"{k} of {model.n} origin points per step ({k * P * F} solves)"},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -360,10 +498,10 @@ def run_ali(args):
     beforehand (not timed); the timed region is the whole iteration loop."""
     import torch
     import paper_1912_08445_gb300 as mg
-    model = build_model(seed=0)
+    model = build_clumpy(seed=0)
     stream = torch.cuda.Stream()
     out = {"metric": "ALI time to converge (max relative population change < 1e-6)", "unit": "s",
-           "higher_is_better": False, "data": "synthetic", "config": dict(WORKLOAD), "runs": []}
+           "higher_is_better": False, "data": "synthetic", "config": dict(CLUMPY), "runs": []}
     for prec_name in args.ali_precisions.split(","):
         prec = mg.MG_MIXED if prec_name == "mixed" else mg.MG_FP64
         for ng in (0, 4):
@@ -459,14 +597,18 @@ def run_disc(args):
     import torch
     import paper_1912_08445_gb300 as mg
     import synthetic as syn
-    m = syn.model_disc(n=args.disc_points, seed=0)
+    m = syn.model_disc(n=args.disc_points, seed=0, n_h2_in=DISC_N_H2_IN)
     ctx = mg.Context(precision=mg.MG_MIXED, profile=1, tau_fp64=args.tau_fp64)
     ctx.load_model(m)
     t0 = time.perf_counter()
     st, _ = ctx.trace_rays()
     trace_s = time.perf_counter() - t0
     ctx.init_populations()
-    v, tms, nt = ctx.autotune(reps=1)
+    if args.variant >= 0:
+        v = args.variant
+        ctx.set_variant(v)
+    else:
+        v, tms, nt = ctx.autotune(reps=1)
     solves, updates = ctx.work_counts()
     ctx.reset_kernel_times()
     torch.cuda.synchronize()
@@ -485,6 +627,47 @@ def run_disc(args):
                       "tau_fp64": args.tau_fp64, "promoted_cells": ctx.promoted_cells() if args.tau_fp64 > 0 else 0,
                       "max_L": max_L,
                       "trace_s": trace_s, "ray_stats": st, "kernel_ms": {k: v2[0] / max(v2[1], 1) for k, v2 in kt.items()}}))
+
+
+def run_kernels(args):
+    """Every kernel family once on stated cases, for profiling (each launch also timed
+    with CUDA events): the ray tracer, line data, warp formal solve and statistical
+    equilibrium on the 3D clumpy cloud (50k points, mixed); the FP64 formal solve, the
+    band-ALO kernels (bandwidth 1) and the scattering iteration on a 2000-point cloud."""
+    import torch
+    import paper_1912_08445_gb300 as mg
+    import synthetic as syn
+    out = {"cases": {}}
+    big = build_clumpy(seed=0)
+    c = mg.Context(precision=mg.MG_MIXED, profile=1)
+    c.load_model(big)
+    c.trace_rays()
+    c.init_populations()
+    c.formal_solve()
+    c.update_populations()
+    torch.cuda.synchronize()
+    out["cases"]["clumpy50k_mixed"] = {k: round(v[0] / max(v[1], 1), 4) for k, v in c.kernel_times().items()}
+    c.close()
+    small = syn.model_clumpy_3d(n=2000, seed=1)
+    for name, opts, sca in (("clumpy2k_fp64", {}, False), ("clumpy2k_fp64_band1", {"alo_band": 1}, False),
+                            ("clumpy2k_fp64_scattering", {}, True)):
+        c = mg.Context(precision=mg.MG_FP64, profile=1, **opts)
+        c.load_model(small)
+        c.trace_rays()
+        c.init_populations()
+        if sca:
+            c.set_scattering(3e-14 * small.n_coll / small.n_coll.max(), tol=1e-10, max_iter=50)
+        c.formal_solve()
+        c.update_populations()
+        torch.cuda.synchronize()
+        rec = {k: round(v[0] / max(v[1], 1), 4) for k, v in c.kernel_times().items()}
+        if opts:
+            rec["gmres_iterations"] = c.band_status()[1]
+        if sca:
+            rec["scattering_passes"] = c.scattering_status()[0]
+        out["cases"][name] = rec
+        c.close()
+    print(json.dumps(out))
 
 
 def run_image(args):
@@ -629,13 +812,17 @@ def run_learned(args):
     from paper_1912_08445_gb300 import learned
     sp = syn.species_rotor(20, np.random.default_rng(77))
     t0 = time.perf_counter()
-    train = learned.corpus_models(args.corpus, 1000, n_points=args.corpus_points, species=sp)
+    train = learned.corpus_models(args.corpus, 1000, n_points=args.corpus_points, species=sp,
+                                  abundance_range=(1e-7, 1e-4))
     X, Y, reps = learned.build_corpus(train, ng_period=4)
     corpus_s = time.perf_counter() - t0
     net, trep = learned.train_network(X, Y, 20, epochs=args.epochs, batch=4096, lr=2e-3)
-    held = learned.corpus_models(10, 5000, n_points=args.corpus_points, species=sp)
+    held = learned.corpus_models(10, 5000, n_points=args.corpus_points, species=sp, abundance_range=(1e-7, 1e-4))
+    slow = learned.slow_discs((5101, 5102), n_points=args.corpus_points, species=sp)
+    for m in slow:
+        m.name = "disc_slow"
     rows = []
-    for m in held:
+    for m in held + slow:
         for ng in (0, 4):
             rec = {"n": m.n, "shape": m.name, "ng_period": ng}
             for name, prec, start in (("fp64_lte", mg.MG_FP64, "lte"), ("mixed_lte", mg.MG_MIXED, "lte"),
@@ -656,14 +843,18 @@ def run_learned(args):
                 ctx.close()
             rows.append(rec)
     summ = {}
-    for ng in (0, 4):
-        sel = [r for r in rows if r["ng_period"] == ng]
+    for ng, group in ((0, "held_out"), (4, "held_out"), (0, "slow_discs"), (4, "slow_discs")):
+        sel = [r for r in rows if r["ng_period"] == ng and (r["shape"] == "disc_slow") == (group == "slow_discs")]
+        key = "" if group == "held_out" else "slow_"
         for name in ("fp64_lte", "mixed_lte", "mixed_mlp"):
-            summ[f"{name}_ng{ng}"] = {"mean_seconds": float(np.mean([r[name]["seconds"] for r in sel])),
-                                      "mean_iterations": float(np.mean([r[name]["iterations"] for r in sel])),
-                                      "all_converged": all(r[name]["converged"] for r in sel)}
+            summ[f"{key}{name}_ng{ng}"] = {"mean_seconds": float(np.mean([r[name]["seconds"] for r in sel])),
+                                           "mean_iterations": float(np.mean([r[name]["iterations"] for r in sel])),
+                                           "all_converged": all(r[name]["converged"] for r in sel)}
+        summ[f"{key}iteration_gain_ng{ng}"] = [round(1 - r["mixed_mlp"]["iterations"] / r["mixed_lte"]["iterations"], 3)
+                                               for r in sel]
     print(json.dumps({"metric": "ALI time to converge (1e-6), held-out seeds", "unit": "s", "higher_is_better": False,
-                      "workload": f"20-level rotor, cloud/disc models of {args.corpus_points} points, 48 rays, 19 lines x 31 bins",
+                      "workload": f"20-level rotor, cloud/disc models of {args.corpus_points} points, 48 rays, 19 lines x 31 bins; "
+                                  "held-out seeds, plus slow discs (X = 1e-4, n_H2(r_in) 1e12-1e13 m^-3)",
                       "corpus_models": len(train), "corpus_rows": int(X.shape[0]), "corpus_seconds": corpus_s,
                       "training": trep, "summary": summ, "runs": rows}))
 
@@ -671,13 +862,18 @@ def run_learned(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=60)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--no-ali", dest="ali_in_bench", action="store_false",
+                    help="leave out the ALI time-to-converge half of the default line")
+    ap.add_argument("--no-fp64e", dest="fp64e", action="store_false",
+                    help="leave out the FP64-elimination record of the default line")
+    ap.add_argument("--variant", type=int, default=-1, help="disc workload: launch variant (-1: autotune)")
     ap.add_argument("--ali", action="store_true", help="measure ALI time to converge instead")
-    ap.add_argument("--workload", default="clumpy", choices=["clumpy", "batch", "disc", "learned", "image", "sphere1d"])
+    ap.add_argument("--workload", default="default",
+                    choices=["default", "clumpy", "batch", "disc", "learned", "image", "sphere1d", "kernels"])
     ap.add_argument("--corpus", type=int, default=200)
     ap.add_argument("--corpus-points", type=int, default=3000)
     ap.add_argument("--epochs", type=int, default=30)
@@ -698,6 +894,8 @@ def main():
         run_image(args)
     elif args.workload == "sphere1d":
         run_sphere1d(args)
+    elif args.workload == "kernels":
+        run_kernels(args)
     elif args.ali:
         run_ali(args)
     elif args.impl == "reference":

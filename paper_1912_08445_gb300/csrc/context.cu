@@ -916,7 +916,10 @@ extern "C" int mg_update_populations(mg_ctx *ctx, double *max_rel_change) {
         double ch = 0.0;
         int64_t nf = 0;
         int bu = 0;
-        if ((rc = mg_band_update(ctx, &ch, &nf, &bu)) < 0) return rc;
+        {
+            MgTimed t(ctx, "band_solve");   // block set-up, GMRES and finish, host steps included
+            if ((rc = mg_band_update(ctx, &ch, &nf, &bu)) < 0) return rc;
+        }
         MG_CUDA(cudaMemcpyAsync(ctx->h_scal + 4, ctx->d_scal + 4, sizeof(unsigned long long), cudaMemcpyDeviceToHost,
                                 ctx->stream));
         MG_CUDA(cudaStreamSynchronize(ctx->stream));

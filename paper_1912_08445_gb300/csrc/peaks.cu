@@ -1,8 +1,9 @@
 // Throughput of the FP32 pipes that bound the mixed-precision formal solve, measured on
 // the device (the roofline denominators of the FP32 sweep): scalar FFMA, packed FFMA2,
 // and the MUFU operations ex2.approx and rcp.approx. Each kernel runs independent
-// dependency chains (8 per thread, enough to cover the pipe latencies) over a grid of
-// 4 CTAs of 256 threads per SM, timed with CUDA events after a warm-up launch.
+// dependency chains (8 per thread) over a grid of 8 CTAs of 256 threads per SM (full
+// occupancy, enough operations in flight to cover the pipe latencies), timed with CUDA
+// events after a warm-up launch.
 #include <cstring>
 #include "common.cuh"
 
@@ -63,14 +64,16 @@ __global__ void __launch_bounds__(256) k_ex2(float *out) {
     if (s == 1.2345f) out[0] = s;
 }
 
-// rcp chains: x <- rcp(x) alternates between two finite values.
+// rcp chains: x <- rcp(x + 1) converges to the golden ratio's inverse; the add keeps
+// the compiler from folding rcp(rcp(x)) into x (the add runs on the FMA pipe, which has
+// eight times the MUFU rate).
 __global__ void __launch_bounds__(256) k_rcp(float *out) {
     float x[kChains];
 #pragma unroll
     for (int c = 0; c < kChains; c++) x[c] = 1.5f + threadIdx.x * 1e-6f + c * 0.01f;
     for (int i = 0; i < kIters; i++)
 #pragma unroll
-        for (int c = 0; c < kChains; c++) x[c] = rcp_approx(x[c]);
+        for (int c = 0; c < kChains; c++) x[c] = rcp_approx(x[c] + 1.0f);
     float s = 0.f;
 #pragma unroll
     for (int c = 0; c < kChains; c++) s += x[c];
@@ -93,7 +96,7 @@ extern "C" int mg_measure_pipe_rates(int32_t device, double *rates) {
     if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) { cudaFree(d); return MG_ERR_CUDA; }
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    const unsigned grid = 4u * (unsigned)sms, threads = 256;
+    const unsigned grid = 8u * (unsigned)sms, threads = 256;
     const double work = (double)grid * threads * kChains * kIters;
     double res[4] = {0, 0, 0, 0};
     for (int k = 0; k < 4; k++) {

@@ -963,6 +963,9 @@ const WarpVariant kWarpVariants[] = {
     MG_VARIANT(2, 2, 6, false), MG_VARIANT(1, 2, 4, false), MG_VARIANT(1, 2, 6, false), MG_VARIANT(1, 4, 3, false),
     MG_VARIANT(1, 4, 4, false), MG_VARIANT(2, 4, 3, false), MG_VARIANT(2, 4, 4, false), MG_VARIANT(4, 4, 3, false),
     MG_VARIANT(4, 4, 4, false),
+    // two lines x four bins per lane at 5 and 6 blocks per SM (95 and 80 registers, a few
+    // spilled words) for more warps in flight on lines with 33-64 bins
+    MG_VARIANT(2, 4, 5, false), MG_VARIANT(2, 4, 6, false),
 };
 #undef MG_VARIANT
 constexpr int kNumWarpVariants = sizeof(kWarpVariants) / sizeof(kWarpVariants[0]);
@@ -1049,7 +1052,8 @@ static int launch_mixed(mg_ctx *ctx, int variant) {
 // Default launch variant for a model: two lines per warp with two bins per lane when the
 // lines have <= 32 bins, otherwise one line per warp with as many bins per lane as needed.
 static int default_variant(int L, int Q) {
-    const int order[] = {4, 3, 2, 0, 1, 6, 5, 8, 7, 12, 11, 10, 9, 17, 16, 15, 13, 14, 19, 18, 21, 20, 25, 24, 23, 22};
+    const int order[] = {4, 3, 2, 0, 1, 6, 5, 8, 7, 12, 11, 10, 9, 17, 16, 15, 13, 14, 19, 18, 21, 20, 25, 24, 23, 22,
+                         26, 27};
     for (int v : order)
         if (variant_valid(v, L, Q)) return v;
     return -1;

@@ -43,7 +43,7 @@ def train_network(X, Y, n_lev, epochs=30, batch=4096, lr=2e-3, seed=0, device=0)
     return net, rep
 
 
-def corpus_models(n_models, seed0, n_points=3000, species=None):
+def corpus_models(n_models, seed0, n_points=3000, species=None, abundance_range=(1e-7, 1e-5)):
     """Seeded cloud/disc models of the given species (alternating shapes of the clumpy
     cloud and the Keplerian disc, scaled down), densities and abundances log-uniform."""
     import synthetic as syn
@@ -51,7 +51,7 @@ def corpus_models(n_models, seed0, n_points=3000, species=None):
     for k in range(n_models):
         rng = np.random.default_rng(seed0 + k)
         dens = float(np.exp(rng.uniform(np.log(1e8), np.log(1e11))))
-        X = float(np.exp(rng.uniform(np.log(1e-7), np.log(1e-5))))
+        X = float(np.exp(rng.uniform(np.log(abundance_range[0]), np.log(abundance_range[1]))))
         if k % 2 == 0:
             m = syn.model_clumpy_3d(n=n_points, seed=seed0 + k, n_h2_ref=dens, abundance=X, species=species,
                                     v_max=float(rng.uniform(2e3, 2e4)))
@@ -60,4 +60,18 @@ def corpus_models(n_models, seed0, n_points=3000, species=None):
                                n_h2_in=dens * 100, abundance=X)
             m.species = species
         out.append(m)
+    return out
+
+
+def slow_discs(seeds, n_points=3000, species=None, densities=(1e12, 3e12, 1e13), abundance=1e-4):
+    """Held-out discs in the regime where the ALI from LTE is slow (lines of optical depth
+    ~1-10 with sub-thermal excitation: 19-21 iterations from LTE at 3000 points)."""
+    import synthetic as syn
+    out = []
+    for s in seeds:
+        for d in densities:
+            m = syn.model_disc(n=n_points, seed=s, nside=2, n_q=31, n_lev=species.n_lev, n_h2_in=d,
+                               abundance=abundance)
+            m.species = species
+            out.append(m)
     return out
