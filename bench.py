@@ -54,7 +54,11 @@ CLUMPY = dict(workload="3D clumpy cloud, 50k points, k=16 symmetric NN, 48 rays 
               n_points=50_000, n_rays=48, n_lines=4, n_bins=31)
 METRIC = "point-ray-pair-frequency Feautrier solves/s"
 UNIT = "solves/s"
-FLOPS_PER_UPDATE = 16.0   # FMA-pipe flops of one point-bin update of the FP32 sweep (FMA = 2)
+# One point-bin update of the FP32 sweep: 11 FP32 operations on the FMA pipe (FMA, MUL or
+# ADD, one each: profile argument, square, line opacity, floored source, dtau, t, Phi,
+# 1 + dtau Phi, psi), of which 4 are FMAs (15 flops with FMA = 2); one ex2 and one rcp.
+FMA_OPS_PER_UPDATE = 11.0
+FLOPS_PER_UPDATE = 15.0
 MUFU_PER_UPDATE = (1, 1)  # ex2, rcp per point-bin update
 
 
@@ -387,19 +391,25 @@ def run_gpu(args):
         k_ms, k_n = kt.get("feautrier_mixed", (float("nan"), 1))
         k_avg = k_ms / max(k_n, 1)
         upd_s = executed / (k_avg * 1e-3)
-        fma_peak = max(rates["ffma"], rates["ffma2"])
-        achieved = FLOPS_PER_UPDATE * upd_s
+        fma_peak = max(rates["ffma"], rates["ffma2"])       # flops/s, FMA = 2
+        op_peak = fma_peak / 2.0                            # FP32 operations/s on the FMA pipe
+        achieved = FMA_OPS_PER_UPDATE * upd_s
         mufu_time = upd_s * (MUFU_PER_UPDATE[0] / rates["ex2"] + MUFU_PER_UPDATE[1] / rates["rcp"])
         hbm_bytes = st["n_elements"] * 16
         traffic = recorded_traffic(variant, "feautrier_warp_clumpy50k.json" if clumpy_mode else
                                    "feautrier_warp_disc200k.json")
-        roof = {"bound": "alu", "achieved": round(achieved / 1e12, 3), "peak": round(fma_peak / 1e12, 3),
-                "unit": "TFLOP/s", "frac": round(achieved / fma_peak, 4), "traffic": traffic,
+        roof = {"bound": "alu", "achieved": round(achieved / 1e12, 3), "peak": round(op_peak / 1e12, 3),
+                "unit": "T FP32 ops/s (FMA pipe)", "frac": round(achieved / op_peak, 4), "traffic": traffic,
                 "kernel": "k_feautrier_warp (feautrier_mixed)", "kernel_ms": round(k_avg, 3),
-                "peak_source": "measured in this run: max of scalar FFMA and packed FFMA2 flops/s "
-                               "(mg_measure_pipe_rates)",
-                "work": f"{FLOPS_PER_UPDATE:g} FMA-pipe flops per executed point-bin update (counted by the "
-                        "kernel: far-wing points it skips are not work)",
+                "peak_source": "measured in this run: the FMA pipe's FP32 operation rate, max of scalar FFMA "
+                               "and packed FFMA2 (mg_measure_pipe_rates; flops/s / 2)",
+                "work": f"{FMA_OPS_PER_UPDATE:g} FP32 operations on the FMA pipe (FMA, MUL, ADD one each) per "
+                        "executed point-bin update (counted by the kernel: far-wing points it skips are not work)",
+                "flops": {"achieved_tflops": round(FLOPS_PER_UPDATE * upd_s / 1e12, 3),
+                          "peak_tflops": round(fma_peak / 1e12, 3),
+                          "frac": round(FLOPS_PER_UPDATE * upd_s / fma_peak, 4),
+                          "note": f"{FLOPS_PER_UPDATE:g} flops per update with FMA = 2; the MULs and ADDs of the "
+                                  "recursion take the FMA pipe like FMAs, so this fraction cannot reach 1"},
                 "executed_updates_per_launch": int(executed), "nominal_updates_per_launch": int(updates),
                 "mufu_frac": round(mufu_time, 4),
                 "mufu_note": "one ex2 and one rcp per update against the measured ex2 and rcp rates",
@@ -429,8 +439,8 @@ def run_gpu(args):
             "dtype": "f32+f64", "data": "synthetic",
             "config": dict(spec, precision="mixed (FP32 formal solve, cancellation-free elimination; FP64 "
                            "statistical equilibrium)",
-                           l2="inputs larger than L2 (ray store "
-                           f"{st['n_elements'] * 24 / 1e9:.2f} GB read per step)",
+                           l2="inputs larger than L2 (FP32 ray store "
+                           f"{st['n_elements'] * 16 / 1e9:.2f} GB read per step)",
                            parallelism=f"replicas x{ws}", solves_per_step=solves,
                            cell_freq_updates_per_step=updates, mean_pair_len=round(st["mean_pair_len"], 1),
                            launch_variant=variant, variants_tried=n_tried, promoted_cells=promoted,
@@ -579,6 +589,22 @@ def run_batch(args):
     reps, rc = b.iterate(allow_not_converged=True)
     ali_s = time.perf_counter() - t0
     its = [r["iterations"] for r in reps]
+    # the same batched ALI with each model's Ng steps (every 4th iteration)
+    ctxs_ng = []
+    for m in models:
+        c = mg.Context(precision=mg.MG_MIXED, tol=1e-6, max_iter=100, ng_period=4)
+        c.load_model(m)
+        c.trace_rays()
+        c.init_populations()
+        ctxs_ng.append(c)
+    b_ng = mg.Batch(ctxs_ng)
+    b_ng.set_variant(v, srt)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    reps_ng, rc_ng = b_ng.iterate(allow_not_converged=True)
+    ali_ng_s = time.perf_counter() - t0
+    its_ng = [r["iterations"] for r in reps_ng]
+    b_ng.close()
     print(json.dumps({
         "metric": METRIC, "unit": UNIT, "workload": f"{len(models)} clumpy clouds, "
         f"{min(m.n for m in models)}-{max(m.n for m in models)} points, 48 rays, 4 lines x 31 bins",
@@ -586,7 +612,9 @@ def run_batch(args):
         "cell_freq_updates": updates, "batched_value": solves / batched, "batched_ms": batched * 1e3,
         "looped_value": solves / looped, "looped_ms": looped * 1e3, "variant": v, "queue_sorted": srt,
         "ali_seconds": ali_s, "ali_iterations_min_max": [min(its), max(its)],
-        "ali_converged": int(sum(r["converged"] for r in reps)), "generation_s": gen_s}))
+        "ali_converged": int(sum(r["converged"] for r in reps)),
+        "ali_ng_seconds": ali_ng_s, "ali_ng_iterations_min_max": [min(its_ng), max(its_ng)],
+        "ali_ng_converged": int(sum(r["converged"] for r in reps_ng)), "generation_s": gen_s}))
 
 
 def run_disc(args):
@@ -825,6 +853,7 @@ def run_learned(args):
     for m in held + slow:
         for ng in (0, 4):
             rec = {"n": m.n, "shape": m.name, "ng_period": ng}
+            starts, final = {}, None
             for name, prec, start in (("fp64_lte", mg.MG_FP64, "lte"), ("mixed_lte", mg.MG_MIXED, "lte"),
                                       ("mixed_mlp", mg.MG_MIXED, "mlp")):
                 ctx = mg.Context(precision=prec, tol=1e-6, max_iter=400, ng_period=ng)
@@ -840,7 +869,18 @@ def run_learned(args):
                 torch.cuda.synchronize()
                 rec[name] = {"seconds": time.perf_counter() - t1, "iterations": rep["iterations"],
                              "converged": bool(rep["converged"])}
+                if prec == mg.MG_MIXED:   # (untimed) the start and the fixed point it reached
+                    final = ctx.get_populations()
+                    if start == "lte":
+                        ctx.init_populations()
+                    else:
+                        ctx.init_populations_mlp(net)
+                    starts[start] = ctx.get_populations()
                 ctx.close()
+            # distance of each start from the fixed point (levels above 1e-6 of the species)
+            big = final >= 1e-6 * final.sum(axis=1, keepdims=True)
+            for start, p0 in starts.items():
+                rec[f"start_error_{start}"] = float(np.max(np.abs(p0[big] - final[big]) / final[big]))
             rows.append(rec)
     summ = {}
     for ng, group in ((0, "held_out"), (4, "held_out"), (0, "slow_discs"), (4, "slow_discs")):
@@ -852,6 +892,16 @@ def run_learned(args):
                                            "all_converged": all(r[name]["converged"] for r in sel)}
         summ[f"{key}iteration_gain_ng{ng}"] = [round(1 - r["mixed_mlp"]["iterations"] / r["mixed_lte"]["iterations"], 3)
                                                for r in sel]
+        # the iterations a start saves if the error falls by a constant factor rho per
+        # iteration: log(e_lte / e_mlp) / log(1 / rho), rho from the LTE run to 1e-6
+        pred = []
+        for r in sel:
+            e_l, e_m, it = r["start_error_lte"], r["start_error_mlp"], r["mixed_lte"]["iterations"]
+            rho = (1e-6 / e_l) ** (1.0 / it) if e_l > 1e-6 and it > 0 else float("nan")
+            pred.append(round(float(np.log(e_l / e_m) / np.log(1.0 / rho)), 2) if 0 < rho < 1 else None)
+        summ[f"{key}start_error_lte_ng{ng}"] = [float(f"{r['start_error_lte']:.3g}") for r in sel]
+        summ[f"{key}start_error_mlp_ng{ng}"] = [float(f"{r['start_error_mlp']:.3g}") for r in sel]
+        summ[f"{key}predicted_iterations_saved_ng{ng}"] = pred
     print(json.dumps({"metric": "ALI time to converge (1e-6), held-out seeds", "unit": "s", "higher_is_better": False,
                       "workload": f"20-level rotor, cloud/disc models of {args.corpus_points} points, 48 rays, 19 lines x 31 bins; "
                                   "held-out seeds, plus slow discs (X = 1e-4, n_H2(r_in) 1e12-1e13 m^-3)",

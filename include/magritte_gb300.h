@@ -338,7 +338,9 @@ int mg_set_variant(mg_ctx *ctx, int32_t variant);
  * The contexts must be traced and populated, on the same device, in MG_MIXED precision,
  * with the same number of lines and bins and no overlapping lines. The batch keeps the
  * context pointers but does not own the contexts: destroy the batch first. While a batch
- * call runs, the contexts use the batch's stream. The batch ALI runs without Ng steps. */
+ * call runs, the contexts use the batch's stream. In the batch ALI each model takes its
+ * own Ng steps (opt.ng_period of its context; 0 = off) between the graph launches, as in
+ * mg_iterate. */
 typedef struct mg_batch mg_batch;
 int mg_batch_create(mg_batch **out, int32_t n_models, mg_ctx *const *models);
 int mg_batch_destroy(mg_batch *batch);

@@ -299,23 +299,39 @@ extern "C" int mg_batch_iterate(mg_batch *b, mg_ali_report *reps) {
     }
     const int max_iter = b->models[0]->opt.max_iter;
     int n_active = b->n_models;
+    std::vector<int> nh(b->n_models, 0);   // iterates in each model's Ng history
     for (int it = 0; it < max_iter && n_active > 0; it++) {
         B_CUDA(cudaGraphLaunch(b->exec, b->stream));
         B_CUDA(cudaStreamSynchronize(b->stream));
         bool changed = false;
         for (int m = 0; m < b->n_models; m++) {
             if (!b->h_active[m]) continue;
+            mg_ctx *c = b->models[m];
             double ch;
             std::memcpy(&ch, &b->h_scal_all[3 * m], 8);
             r[m].iterations++;
             r[m].last_change = ch;
             r[m].n_fallback += (int64_t)b->h_scal_all[3 * m + 1];
             if (b->h_scal_all[3 * m + 2]) return bfail(b, MG_ERR_NUMERIC, "batch: non-finite populations");
-            if (ch < b->models[m]->opt.tol) {
+            if (ch < c->opt.tol) {
                 r[m].converged = 1;
                 b->h_active[m] = 0;
                 n_active--;
                 changed = true;
+                continue;
+            }
+            // Ng acceleration of this model, as in mg_iterate (outside the graph: the
+            // history ring rotates and the step's acceptance is read on the host)
+            if (c->opt.ng_period > 0) {
+                int rc = mg_launch_push_history(c);
+                if (rc) return bfail(b, rc, "batch: Ng history");
+                if (nh[m] < 4) nh[m]++;
+                if (nh[m] == 4 && (it + 1) % c->opt.ng_period == 0) {
+                    int acc = 0;
+                    if ((rc = mg_launch_ng(c, &acc))) return bfail(b, rc, "batch: Ng step");
+                    r[m].ng_steps += acc;
+                    nh[m] = 0;
+                }
             }
         }
         if (changed)

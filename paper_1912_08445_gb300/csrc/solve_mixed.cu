@@ -78,7 +78,8 @@ struct MixArgs {
     const int32_t *ovl_off;
     const Overlap *ovl;
     float chi_min, dtau_min, inv_chi_min;
-    float q_nofloor;             // q = ds/(2 sqrt 2) from which 2 chi_min q >= dtau_min in FP32
+    float q_nofloor;             // q' = chi_min ds/(2 sqrt 2) from which 2 q' >= dtau_min in FP32
+    float qscale;                // chi_min/(2 sqrt 2): q' of an interval per unit length
     float planck_a, planck_b;    // B'(nu) = a nu_G^3 / expm1(b nu_G): a = 2h 1e27/c^2/I0, b = h 1e9/(k T_cmb)
     double *J, *Lout, *Jeff, *Lc, *Jnu;
     int32_t kmax;
@@ -330,7 +331,10 @@ __global__ void __launch_bounds__(256) k_feautrier_mixed(MixArgs a) {
 // needed, and the pair sums are kept per lane in a fixed order. The boundary row is the
 // interior update started from the virtual state (Phi iota = 1, psi = I, dtau = 0).
 // The opacity floor: chi = max(chi_l, chi_min) and S_eff = S min(chi_l/chi_min, 1),
-// which is eta/chi with chi floored.
+// which is eta/chi with chi floored. The warp kernel carries opacities in units of
+// chi_min (and the interval factor q times chi_min, so that dtau is unchanged): the floor
+// is then max(chi', 1) and the source's min(chi', 1), with no multiplication by
+// 1/chi_min per bin.
 //
 // The ray elements behind the ring come from an element window in shared memory (one
 // element per lane). A window serves refills until its points are used up; meanwhile
@@ -406,7 +410,7 @@ __device__ __forceinline__ void win_gathers(const MixArgs &a, int l0, ElemWin<G>
 
 // Scalars of the sweep, held in registers (not re-read from the argument block).
 struct SweepK {
-    float chi_min, inv_chi_min, dtau_min, planck_a, planck_b;
+    float dtau_min, planck_a, planck_b;
 };
 
 // B_nu / I0 at nu_g GHz; e^x - 1 from one ex2 (x = h nu / k T_cmb is O(1) at line
@@ -419,10 +423,12 @@ __device__ __forceinline__ float planck_k(const SweepK &k, float nu_g) {
 // pair reads them as the operand pairs of packed FP32x2 arithmetic:
 //   a = (g_z, g_z, -g_y, -g_y) with g_y = sqrt(log2 e) v/b and g_z = sqrt(log2 e)(1 - v/c)/b,
 //       so that the profile argument of bin a_q is x' = a_q g_z - g_y;
-//   b = (q, q, far, 0) with q = ds/(2 sqrt 2) to the next point towards the origin (the
-//       half-width interval factor that yields delta = dtau/sqrt 2).
-// The line data of a point are (X, X, S, S) per line: chi_l = X 2^(-x'^2) and the floored
-// source is S_eff = S min(chi_l/chi_min, 1), which is eta/chi with chi = max(chi_l, chi_min)
+//   b = (q', q', far, 0) with q' = chi_min ds/(2 sqrt 2) to the next point towards the
+//       origin (the half-width interval factor that yields delta = dtau/sqrt 2 from
+//       opacities in units of chi_min).
+// The line data of a point are (X', X', S, S) per line, X' = X/chi_min: the line opacity
+// in units of chi_min is chi' = X' 2^(-x'^2), the floored opacity max(chi', 1), and the
+// floored source S_eff = S min(chi', 1), which is eta/chi with chi = max(chi_l, chi_min)
 // (exactly S where the line is not floored; finite for any finite S).
 struct RingPt {
     float4 a, b;
@@ -447,8 +453,9 @@ __device__ __forceinline__ void stage_ring_point(const MixArgs &a, const ElemWin
     const float2 w1 = make_float2(wt, wt), w0 = make_float2(1.0f - wt, 1.0f - wt);
     const float2 vbi = __ffma2_rn(w1, w.vb[bf][i], __fmul2_rn(w0, w.vb[bf][i + 1]));
     const float v = vbi.x;
-    const float qds = kInvSqrt8 * w.ds[bf][i] * rn;
+    const float qds = a.qscale * w.ds[bf][i] * rn;
     const float ib = rcpf(vbi.y);
+    const float ibc = ib * a.inv_chi_min;
     const float pz = kSqrtLog2e * ib;
     const float gy = v * pz, gz = (1.0f - v * (float)(1.0 / kC)) * pz;
     const float xlo = aq_lo * gz - gy, xhi = aq_hi * gz - gy;
@@ -458,14 +465,14 @@ __device__ __forceinline__ void stage_ring_point(const MixArgs &a, const ElemWin
 #pragma unroll
     for (int k = 0; k < G; k++) {
         const float2 e = __ffma2_rn(w1, w.ln[bf][k][i], __fmul2_rn(w0, w.ln[bf][k][i + 1]));   // (eta, chi)
-        const float X = fmaxf(e.y, 0.0f) * ib;
+        const float X = fmaxf(e.y, 0.0f) * ibc;
         // (a line whose opacity is below the smallest normal float has no source here)
         const float S = e.y >= 1.17549435e-38f ? e.x * rcpf(e.y) : 0.0f;
         ln[k * kRing] = make_float4(X, X, S, S);   // line k's slot of this point
         Xmax = fmaxf(Xmax, X);
     }
     pt.a = make_float4(gz, gz, -gy, -gy);
-    pt.b = make_float4(qds, qds, Xmax * wing < a.chi_min ? 1.0f : 0.0f, 0.0f);
+    pt.b = make_float4(qds, qds, Xmax * wing < 1.0f ? 1.0f : 0.0f, 0.0f);
 }
 
 // Per-bin sweep state in the variables delta = dtau/sqrt 2, Phi^ = sqrt 2 Phi and
@@ -502,15 +509,13 @@ __device__ __forceinline__ void first_point(const SweepK &k, BinState<NB> &st, c
                                             const float nu_g, const float v) {
     const float2 gz = make_float2(A.x, A.y), ngy = make_float2(A.z, A.w);
     const float2 X = make_float2(D.x, D.y), S = make_float2(D.z, D.w);
-    const float2 icm = make_float2(k.inv_chi_min, k.inv_chi_min);
     const float dop = 1.0f - v * (float)(1.0 / kC);
 #pragma unroll
     for (int p = 0; p < BinState<NB>::NP; p++) {
         const float2 x = __ffma2_rn(st.aq2[p], gz, ngy);
         const float2 chil = __fmul2_rn(X, ex2f2(__fmul2_rn(x, x)));
-        st.chi_p2[p] = make_float2(fmaxf(chil.x, k.chi_min), fmaxf(chil.y, k.chi_min));
-        const float2 t = __fmul2_rn(chil, icm);
-        st.S_p2[p] = __fmul2_rn(S, make_float2(fminf(t.x, 1.0f), fminf(t.y, 1.0f)));
+        st.chi_p2[p] = make_float2(fmaxf(chil.x, 1.0f), fmaxf(chil.y, 1.0f));
+        st.S_p2[p] = __fmul2_rn(S, make_float2(fminf(chil.x, 1.0f), fminf(chil.y, 1.0f)));
         st.Phi2[p] = make_float2(kSqrt2, kSqrt2);
         st.iota2[p] = make_float2(1.0f, 1.0f);
         st.d_p2[p] = make_float2(0.0f, 0.0f);
@@ -520,8 +525,8 @@ __device__ __forceinline__ void first_point(const SweepK &k, BinState<NB> &st, c
     if constexpr (BinState<NB>::ODD) {
         const float x = fmaf(st.aq1, gz.x, ngy.x);
         const float chil = X.x * ex2f(-x * x);
-        st.chi_p1 = fmaxf(chil, k.chi_min);
-        st.S_p1 = S.x * fminf(chil * k.inv_chi_min, 1.0f);
+        st.chi_p1 = fmaxf(chil, 1.0f);
+        st.S_p1 = S.x * fminf(chil, 1.0f);
         st.Phi1 = kSqrt2;
         st.iota1 = 1.0f;
         st.d_p1 = 0.0f;
@@ -531,20 +536,18 @@ __device__ __forceinline__ void first_point(const SweepK &k, BinState<NB> &st, c
 
 // Update with the interval (previous point, this point); qp = (q, q) of that interval,
 // A and D the point's ring entries. FLOOR = false drops the dtau floor where the caller
-// knows that it cannot bind (q >= q_nofloor): the result is the same bit for bit.
+// knows that it cannot bind (q' >= q_nofloor): the result is the same bit for bit.
 template <int NB, bool FLOOR = true>
 __device__ __forceinline__ void step_point(const SweepK &k, BinState<NB> &st, const float4 A, const float4 D,
                                            const float2 qp) {
     const float2 gz = make_float2(A.x, A.y), ngy = make_float2(A.z, A.w);
     const float2 X = make_float2(D.x, D.y), S = make_float2(D.z, D.w);
-    const float2 icm = make_float2(k.inv_chi_min, k.inv_chi_min);
 #pragma unroll
     for (int p = 0; p < BinState<NB>::NP; p++) {
         const float2 x = __ffma2_rn(st.aq2[p], gz, ngy);
         const float2 chil = __fmul2_rn(X, ex2f2(__fmul2_rn(x, x)));
-        const float2 chi = make_float2(fmaxf(chil.x, k.chi_min), fmaxf(chil.y, k.chi_min));
-        const float2 t = __fmul2_rn(chil, icm);
-        const float2 Sx = __fmul2_rn(S, make_float2(fminf(t.x, 1.0f), fminf(t.y, 1.0f)));
+        const float2 chi = make_float2(fmaxf(chil.x, 1.0f), fmaxf(chil.y, 1.0f));
+        const float2 Sx = __fmul2_rn(S, make_float2(fminf(chil.x, 1.0f), fminf(chil.y, 1.0f)));
         const float2 d0 = __fmul2_rn(__fadd2_rn(st.chi_p2[p], chi), qp);
         const float2 dl = FLOOR ? make_float2(fmaxf(d0.x, k.dtau_min), fmaxf(d0.y, k.dtau_min)) : d0;
         const float2 sm = __fadd2_rn(st.d_p2[p], dl);
@@ -559,8 +562,8 @@ __device__ __forceinline__ void step_point(const SweepK &k, BinState<NB> &st, co
     if constexpr (BinState<NB>::ODD) {
         const float x = fmaf(st.aq1, gz.x, ngy.x);
         const float chil = X.x * ex2f(-x * x);
-        const float chi = fmaxf(chil, k.chi_min);
-        const float Sx = S.x * fminf(chil * k.inv_chi_min, 1.0f);
+        const float chi = fmaxf(chil, 1.0f);
+        const float Sx = S.x * fminf(chil, 1.0f);
         const float d0 = (st.chi_p1 + chi) * qp.x;
         const float dl = FLOOR ? fmaxf(d0, k.dtau_min) : d0;
         const float sm = st.d_p1 + dl;
@@ -692,7 +695,7 @@ __device__ __forceinline__ void sweep_half(const MixArgs &a, const SweepK &k, in
         }
         // The chunk is swept in two segments, points [0, 16) and [16, cnt), with the
         // gathers of the next window issued between them (one copy of each loop body).
-        // A chunk whose intervals all have q >= q_nofloor sweeps without the dtau floor.
+        // A chunk whose intervals all have q' >= q_nofloor sweeps without the dtau floor.
         const int mid = cnt < 16 ? cnt : 16;
         const bool floor_needed = __any_sync(0xffffffffu, my_tiny) || qp.x < a.q_nofloor;
         auto dense = [&](auto floor_tag, int jend) {
@@ -793,12 +796,12 @@ __device__ __forceinline__ void solve_item(const MixArgs &a, int64_t o, int l0, 
     const float2 dl = reinterpret_cast<const float2 *>(a.line)[o * a.L + lc];
     // ring entries of the origin (v = 0 there): a = (g_z, g_z, -0, -0), line = (X, X, S, S)
     const float gzo = kSqrtLog2e * ibo;
-    const float Xo = fmaxf(dl.y, 0.0f) * ibo;
+    const float Xo = fmaxf(dl.y, 0.0f) * (ibo * a.inv_chi_min);   // in units of chi_min
     const float So = dl.y > 0.0f ? dl.x / dl.y : 0.0f;
     const float4 Ao = make_float4(gzo, gzo, -0.0f, -0.0f);
     const float4 Do = make_float4(Xo, Xo, So, So);
     const float nu_g = a.nu_ghz[lc];
-    const SweepK k{a.chi_min, a.inv_chi_min, a.dtau_min, a.planck_a, a.planck_b};
+    const SweepK k{a.dtau_min, a.planck_a, a.planck_b};
     BinState<NB> st;
 #pragma unroll
     for (int i = 0; i < NB; i++) {
@@ -843,8 +846,8 @@ __device__ __forceinline__ void solve_item(const MixArgs &a, int64_t o, int l0, 
             // the origin's line opacity, floored opacity and floored source in this bin
             const float xo = st.aq(i) * gzo;
             const float chilo = Xo * ex2f(-xo * xo);
-            const float chio = fmaxf(chilo, k.chi_min);
-            const float Sov = So * fminf(chilo * k.inv_chi_min, 1.0f);
+            const float chio = fmaxf(chilo, 1.0f);
+            const float Sov = So * fminf(chilo, 1.0f);
             float u, lam, uml, oml;
             if (dtb == 0.0f && dtf[i] == 0.0f) {   // isolated origin: both halves empty
                 u = psb * (float)(1.0 / 1.4142135623730951); lam = 0.0f; uml = u; oml = 1.0f;
@@ -999,9 +1002,11 @@ static void fill_args(mg_ctx *ctx, MixArgs &a) {
     a.roots = ctx->d_roots; a.weights = ctx->d_weights; a.ovl_off = ctx->d_ovl_off; a.ovl = ctx->d_ovl;
     a.chi_min = (float)ctx->opt.chi_min; a.dtau_min = (float)ctx->opt.dtau_min;
     a.inv_chi_min = (float)(1.0 / ctx->opt.chi_min);
-    // Every floored opacity is >= chi_min, so an interval with q >= q_nofloor has
-    // dtau/sqrt 2 = (chi_prev + chi) q >= dtau_min: the floor cannot bind there.
-    a.q_nofloor = std::nextafter((float)(ctx->opt.dtau_min / (2.0 * ctx->opt.chi_min)) * 1.000001f, INFINITY);
+    // Every floored opacity is >= 1 in units of chi_min, so an interval with
+    // q' >= q_nofloor has dtau/sqrt 2 = (chi'_prev + chi') q' >= dtau_min: the floor
+    // cannot bind there.
+    a.q_nofloor = std::nextafter((float)(ctx->opt.dtau_min / 2.0) * 1.000001f, INFINITY);
+    a.qscale = (float)(ctx->opt.chi_min * (double)kInvSqrt8);
     a.planck_a = (float)(2.0 * kH * 1e27 / (kC * kC) / (double)kI0);
     a.planck_b = (float)(kH * 1e9 / (kKB * ctx->opt.T_cmb));
     a.J = ctx->d_J; a.Lout = ctx->d_L; a.Jeff = ctx->d_Jeff; a.Lc = ctx->d_Lc;

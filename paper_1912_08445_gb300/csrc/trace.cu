@@ -2,6 +2,7 @@
 // This translation unit is compiled with --fmad=false: every floating-point decision of
 // the walk (projections, distances, velocity steps) is reproducible bit for bit.
 #include <cmath>
+#include <algorithm>
 #include "common.cuh"
 
 using namespace mg;
@@ -463,10 +464,18 @@ int mg_launch_trace(mg_ctx *ctx) {
         k_posf<<<(unsigned)((ctx->n + 255) / 256), 256, 0, ctx->stream>>>(ctx->n, ctx->d_pos, sc.posf);
     }
     a.posf = sc.posf;
-    // record up to cap_tmp cells per half-ray in the count pass (at most 32 GiB of scratch)
+    // Record up to cap_tmp cells per half-ray in the count pass, in scratch of at most
+    // 32 GiB and a quarter of the free device memory (freed after tracing; half-rays with
+    // more cells, or all of them without scratch, are walked again by the fill pass).
     int32_t *&d_tmp = sc.tmp;
     int32_t cap_tmp = 128;
-    while (cap_tmp > 0 && (double)nr * cap_tmp * 4.0 > 32.0 * (1 << 30)) cap_tmp /= 2;
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+        cudaGetLastError();
+        free_b = 0;
+    }
+    const double budget = std::min(32.0 * (1 << 30), 0.25 * (double)free_b);
+    while (cap_tmp > 0 && (double)nr * cap_tmp * 4.0 > budget) cap_tmp /= 2;
     if (ctx->geometry == MG_GEOM_3D && cap_tmp > 0 && cudaMalloc(&d_tmp, (size_t)nr * cap_tmp * 4) != cudaSuccess) {
         cudaGetLastError();
         d_tmp = nullptr;

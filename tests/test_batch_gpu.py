@@ -49,19 +49,22 @@ def test_batch_formal_solve_matches_single_models():
     b.close()
 
 
-def test_batch_ali_matches_single_model_ali():
+@pytest.mark.parametrize("ng", [0, 4])
+def test_batch_ali_matches_single_model_ali(ng):
+    """The batched ALI takes the same iterations (and, with Ng, the same Ng steps) as
+    each model's own mg_iterate and reaches the same populations."""
     import paper_1912_08445_gb300 as mg
     ms = _models(k=5, seed=12)
     singles, batched = [], []
     for m in ms:
-        c = gpu_context(m, precision=1, tol=1e-6, max_iter=100, ng_period=0)
+        c = gpu_context(m, precision=1, tol=1e-6, max_iter=100, ng_period=ng)
         c.trace_rays()
         c.init_populations()
         rep, rc = c.iterate()
         singles.append((rep, c.get_populations()))
     ctxs = []
     for m in ms:
-        c = gpu_context(m, precision=1, tol=1e-6, max_iter=100, ng_period=0)
+        c = gpu_context(m, precision=1, tol=1e-6, max_iter=100, ng_period=ng)
         c.trace_rays()
         c.init_populations()
         ctxs.append(c)
@@ -70,6 +73,7 @@ def test_batch_ali_matches_single_model_ali():
     assert rc == 0
     for (rep, pops), r2, c in zip(singles, reps, ctxs):
         assert r2["converged"] and r2["iterations"] == rep["iterations"]
+        assert r2["ng_steps"] == rep["ng_steps"]
         assert np.max(rel_err(c.get_populations(), pops)) < 1e-12
     b.close()
 
