@@ -161,9 +161,10 @@ def recorded_traffic(kernel_variant, record="feautrier_warp_disc200k.json"):
     src = os.path.join(ROOT, rec["source"])
     if not os.path.exists(src) or hashlib.sha256(open(src, "rb").read()).hexdigest() != rec["source_sha256"]:
         return None
-    if kernel_variant != rec.get("variant"):      # the record belongs to one launch variant
+    cap = rec.get("captures", {}).get(str(kernel_variant))   # one capture per launch variant
+    if cap is None:
         return None
-    return rec["dram_bytes_read_per_launch"] + rec["dram_bytes_write_per_launch"]
+    return cap["dram_bytes_read_per_launch"] + cap["dram_bytes_write_per_launch"]
 
 
 def peaks():
