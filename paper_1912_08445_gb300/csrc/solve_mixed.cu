@@ -344,7 +344,7 @@ __global__ void __launch_bounds__(256) k_feautrier_mixed(MixArgs a) {
 // normally complete when it is needed. The last window of a half-ray prefetches the
 // first window of the next half-ray.
 constexpr int kRing = 32;
-constexpr int kWarps2 = 4;
+constexpr int kWarps2 = 4;   // warps per block of most launch variants
 constexpr int kWin = 32;   // elements top, top-1, ..., top-31 of a half-ray
 
 // Element window of one warp, double-buffered: one slot per lane. Element e of the
@@ -897,15 +897,15 @@ __device__ __forceinline__ void solve_item(const MixArgs &a, int64_t o, int l0, 
     }
 }
 
-template <int G, int NB, int MINB, bool SKIP>
-__global__ void __launch_bounds__(32 * kWarps2, MINB) k_feautrier_warp(MixArgs a) {
-    __shared__ RingPt rgs[kWarps2][kRing];
-    __shared__ float4 rls[kWarps2][G * kRing];
-    __shared__ ElemWin<G> ews[kWarps2];
-    __shared__ PairSmem<NB> pss[kWarps2];
+template <int G, int NB, int MINB, bool SKIP, int W>
+__global__ void __launch_bounds__(32 * W, MINB) k_feautrier_warp(MixArgs a) {
+    __shared__ RingPt rgs[W][kRing];
+    __shared__ float4 rls[W][G * kRing];
+    __shared__ ElemWin<G> ews[W];
+    __shared__ PairSmem<NB> pss[W];
     const int warp = threadIdx.x >> 5;
     const int ngroups = (a.L + G - 1) / G;
-    const int64_t item = (int64_t)blockIdx.x * kWarps2 + warp;
+    const int64_t item = (int64_t)blockIdx.x * W + warp;
     if (item >= a.n * ngroups) return;
     const int64_t o = item / ngroups;
     const int l0 = (int)(item - o * ngroups) * G;
@@ -920,15 +920,15 @@ struct BatchItem {
     int32_t local;   // origin * L + first line of the warp's line group
 };
 
-template <int G, int NB, int MINB, bool SKIP>
-__global__ void __launch_bounds__(32 * kWarps2, MINB)
+template <int G, int NB, int MINB, bool SKIP, int W>
+__global__ void __launch_bounds__(32 * W, MINB)
 k_feautrier_batch(const MixArgs *__restrict__ models, const BatchItem *__restrict__ items, int64_t n_items,
                   unsigned long long *counter, const int32_t *__restrict__ active) {
-    __shared__ RingPt rgs[kWarps2][kRing];
-    __shared__ float4 rls[kWarps2][G * kRing];
-    __shared__ ElemWin<G> ews[kWarps2];
-    __shared__ PairSmem<NB> pss[kWarps2];
-    __shared__ MixArgs sa[kWarps2];
+    __shared__ RingPt rgs[W][kRing];
+    __shared__ float4 rls[W][G * kRing];
+    __shared__ ElemWin<G> ews[W];
+    __shared__ PairSmem<NB> pss[W];
+    __shared__ MixArgs sa[W];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (;;) {
         unsigned long long idx = 0;
@@ -947,14 +947,18 @@ k_feautrier_batch(const MixArgs *__restrict__ models, const BatchItem *__restric
     }
 }
 
-// Launch variants of the warp kernel: (lines per warp, bins per lane, min blocks per SM).
+// Launch variants of the warp kernel: (lines per warp, bins per lane, min blocks per SM,
+// far-wing skipping, warps per block).
 struct WarpVariant {
     int G, NB, MINB;
     bool skip;
+    int W;
     void (*fn)(MixArgs);
     void (*batch)(const MixArgs *, const BatchItem *, int64_t, unsigned long long *, const int32_t *);
 };
-#define MG_VARIANT(G, NB, M, S) {G, NB, M, S, k_feautrier_warp<G, NB, M, S>, k_feautrier_batch<G, NB, M, S>}
+#define MG_VARIANT_W(G, NB, M, S, W) \
+    {G, NB, M, S, W, k_feautrier_warp<G, NB, M, S, W>, k_feautrier_batch<G, NB, M, S, W>}
+#define MG_VARIANT(G, NB, M, S) MG_VARIANT_W(G, NB, M, S, kWarps2)
 const WarpVariant kWarpVariants[] = {
     // with far-wing skipping
     MG_VARIANT(1, 1, 8, true), MG_VARIANT(1, 1, 10, true), MG_VARIANT(2, 2, 4, true), MG_VARIANT(2, 2, 5, true),
@@ -969,8 +973,14 @@ const WarpVariant kWarpVariants[] = {
     // two lines x four bins per lane at 5 and 6 blocks per SM (95 and 80 registers, a few
     // spilled words) for more warps in flight on lines with 33-64 bins
     MG_VARIANT(2, 4, 5, false), MG_VARIANT(2, 4, 6, false),
+    // eight bins per lane (four independent bin pairs per lane) at four lines per warp,
+    // for lines with 33-64 bins; three warps per block keep the static shared memory
+    // below 48 KB
+    MG_VARIANT_W(4, 8, 3, false, 3), MG_VARIANT_W(4, 8, 4, false, 3), MG_VARIANT_W(4, 8, 3, true, 3),
+    MG_VARIANT_W(4, 8, 4, true, 3),
 };
 #undef MG_VARIANT
+#undef MG_VARIANT_W
 constexpr int kNumWarpVariants = sizeof(kWarpVariants) / sizeof(kWarpVariants[0]);
 
 bool variant_valid(int v, int L, int Q) {
@@ -1042,9 +1052,9 @@ static int launch_mixed(mg_ctx *ctx, int variant) {
     } else if (variant >= 0 && variant < kNumWarpVariants) {
         const WarpVariant &wv = kWarpVariants[variant];
         const int64_t items = ctx->n * ((L + wv.G - 1) / wv.G);
-        const unsigned grid = (unsigned)((items + kWarps2 - 1) / kWarps2);
+        const unsigned grid = (unsigned)((items + wv.W - 1) / wv.W);
         MgTimed t(ctx, "feautrier_mixed");
-        wv.fn<<<grid, 32 * kWarps2, 0, ctx->stream>>>(a);
+        wv.fn<<<grid, 32 * wv.W, 0, ctx->stream>>>(a);
     } else {
         MG_CUDA(cudaFuncSetAttribute(k_feautrier_mixed<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         MgTimed t(ctx, "feautrier_mixed");
@@ -1058,7 +1068,7 @@ static int launch_mixed(mg_ctx *ctx, int variant) {
 // lines have <= 32 bins, otherwise one line per warp with as many bins per lane as needed.
 static int default_variant(int L, int Q) {
     const int order[] = {4, 3, 2, 0, 1, 6, 5, 8, 7, 12, 11, 10, 9, 17, 16, 15, 13, 14, 19, 18, 21, 20, 25, 24, 23, 22,
-                         26, 27};
+                         26, 27, 28, 29, 30, 31};
     for (int v : order)
         if (variant_valid(v, L, Q)) return v;
     return -1;
@@ -1127,7 +1137,7 @@ int mg_variant_default(int L, int Q) { return default_variant(L, Q); }
 int mg_batch_launch(int v, int grid, const void *d_args, const void *d_items, int64_t n_items,
                     unsigned long long *counter, const int32_t *active, cudaStream_t stream) {
     if (v < 0 || v >= kNumWarpVariants) return MG_ERR_ARG;
-    kWarpVariants[v].batch<<<grid, 32 * kWarps2, 0, stream>>>(static_cast<const MixArgs *>(d_args),
+    kWarpVariants[v].batch<<<grid, 32 * kWarpVariants[v].W, 0, stream>>>(static_cast<const MixArgs *>(d_args),
                                                                static_cast<const BatchItem *>(d_items), n_items,
                                                                counter, active);
     return cudaGetLastError() == cudaSuccess ? MG_OK : MG_ERR_CUDA;
