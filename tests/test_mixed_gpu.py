@@ -76,8 +76,8 @@ def test_formal_solve_mixed_clumpy_50k_sampled():
 def test_formal_solve_mixed_disc_200k_sampled():
     """The disc workload at full size (200k points, 192 rays, 20-level rotor, 19 lines x
     63 bins), every valid launch variant: sampled origins against the oracle."""
-    _full_size_variants(syn.model_disc(n=200_000, seed=0), [5, 6, 9, 10, 18, 19, 22, 23, 26, 27, 28, 29, 30, 31],
-                        8, 7)
+    _full_size_variants(syn.model_disc(n=200_000, seed=0),
+                        [5, 6, 9, 10, 18, 19, 22, 23, 26, 27, 28, 29, 30, 31], 8, 7)
 
 
 @pytest.mark.parametrize("name", ["sphere1d", "sphere1d_thick"])
