@@ -47,7 +47,7 @@ DISC_N_H2_IN = 2.5e16   # n_H2 at the inner radius (m^-3): line-centre optical d
 DISC_TAU_FP64 = 100.0
 WORKLOAD = dict(workload="Keplerian disc, 200k points (flared, n ~ r^-1 exp(-z^2/2H^2), H/r = 0.1, T ~ r^-0.5, "
                          "Keplerian velocity around 1 M_sun), 192 rays (HEALPix nside=4), 20-level linear rotor, "
-                         "19 lines x 63 Gauss-Hermite bins, line-centre optical depths up to ~1e4, mixed precision",
+                         "19 lines x 63 Gauss-Hermite bins, line-centre optical depths up to ~1e4",
                 n_points=200_000, n_rays=192, n_lines=19, n_bins=63, n_h2_in=DISC_N_H2_IN)
 CLUMPY = dict(workload="3D clumpy cloud, 50k points, k=16 symmetric NN, 48 rays (HEALPix nside=2), "
                        "5-level linear rotor, 4 lines x 31 Gauss-Hermite bins, radial outflow to 10 km/s",
@@ -101,9 +101,21 @@ class Clocks:
         except Exception:
             self.proc.kill()
         self.f.close()
+        with open(self.path) as f:
+            out = self.parse(f) or out
+        try:
+            os.remove(self.path)
+        except OSError:
+            pass
+        return out
+
+    @staticmethod
+    def parse(lines):
+        """Median SM clock, maximum clock and the throttle reasons seen in nvidia-smi CSV
+        lines of the query above (None without a valid sample)."""
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in open(self.path):
+        for line in lines:
             p = [x.strip() for x in line.split(",")]
             if len(p) < 9:
                 continue
@@ -114,14 +126,10 @@ class Clocks:
             for nm, v in zip(names, p[5:9]):
                 if v.lower().startswith("active"):
                     reasons.add(nm)
-        if sm:
-            out = {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
-                   "samples": len(sm)}
-        try:
-            os.remove(self.path)
-        except OSError:
-            pass
-        return out
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
 
 
 def reduce_max(values, device="cpu"):
@@ -150,15 +158,15 @@ def build_clumpy(seed):
     return syn.model_clumpy_3d(n=CLUMPY["n_points"], seed=seed)
 
 
-def recorded_traffic(kernel_variant, record="feautrier_warp_disc200k.json"):
+def recorded_traffic(kernel_variant, record="feautrier_warp_disc200k.json", root=ROOT):
     """DRAM bytes per launch of the formal-solve kernel from the committed ncu record,
     used only while the kernel's source is unchanged since the capture (else None)."""
     import hashlib
-    rec_p = os.path.join(ROOT, "profiles", record)
+    rec_p = os.path.join(root, "profiles", record)
     if not os.path.exists(rec_p):
         return None
     rec = json.load(open(rec_p))
-    src = os.path.join(ROOT, rec["source"])
+    src = os.path.join(root, rec["source"])
     if not os.path.exists(src) or hashlib.sha256(open(src, "rb").read()).hexdigest() != rec["source_sha256"]:
         return None
     cap = rec.get("captures", {}).get(str(kernel_variant))   # one capture per launch variant
