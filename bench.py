@@ -911,11 +911,35 @@ def run_learned(args):
         summ[f"{key}start_error_lte_ng{ng}"] = [float(f"{r['start_error_lte']:.3g}") for r in sel]
         summ[f"{key}start_error_mlp_ng{ng}"] = [float(f"{r['start_error_mlp']:.3g}") for r in sel]
         summ[f"{key}predicted_iterations_saved_ng{ng}"] = pred
+    # the band-diagonal ALO (FP64 contexts) on the slow discs, Ng off: the method's own
+    # means of cutting these iterations, beside the network's start
+    band_rows = []
+    for m in slow:
+        rec = {"n": m.n, "shape": m.name}
+        for band in (1, 2):
+            ctx = mg.Context(precision=mg.MG_FP64, tol=1e-6, max_iter=400, ng_period=0, alo_band=band)
+            ctx.load_model(m)
+            ctx.trace_rays()
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            ctx.init_populations()
+            rep, rc = ctx.iterate(allow_not_converged=True)
+            torch.cuda.synchronize()
+            rec[f"fp64_band{band}"] = {"seconds": time.perf_counter() - t1, "iterations": rep["iterations"],
+                                       "converged": bool(rep["converged"]), "band_in_use": rep["alo_band"]}
+            ctx.close()
+        band_rows.append(rec)
+    for band in (1, 2):
+        summ[f"slow_fp64_band{band}_ng0"] = {
+            "mean_seconds": float(np.mean([r[f"fp64_band{band}"]["seconds"] for r in band_rows])),
+            "mean_iterations": float(np.mean([r[f"fp64_band{band}"]["iterations"] for r in band_rows])),
+            "all_converged": all(r[f"fp64_band{band}"]["converged"] for r in band_rows),
+            "band_in_use": [r[f"fp64_band{band}"]["band_in_use"] for r in band_rows]}
     print(json.dumps({"metric": "ALI time to converge (1e-6), held-out seeds", "unit": "s", "higher_is_better": False,
                       "workload": f"20-level rotor, cloud/disc models of {args.corpus_points} points, 48 rays, 19 lines x 31 bins; "
                                   "held-out seeds, plus slow discs (X = 1e-4, n_H2(r_in) 1e12-1e13 m^-3)",
                       "corpus_models": len(train), "corpus_rows": int(X.shape[0]), "corpus_seconds": corpus_s,
-                      "training": trep, "summary": summ, "runs": rows}))
+                      "training": trep, "summary": summ, "runs": rows, "band_runs": band_rows}))
 
 
 def main():

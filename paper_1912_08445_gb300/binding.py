@@ -507,6 +507,16 @@ class Batch:
         return s.value, u.value
 
 
+MLP_IN = 4   # network inputs per cell (mg_features)
+
+
+def _rows(X, width, what):
+    X = _c(X, np.float32)
+    if X.ndim != 2 or X.shape[1] != width:
+        raise ValueError(f"{what}: expected rows of {width} values, got shape {X.shape}")
+    return X
+
+
 class MLP:
     """Owns one mg_mlp (learned initial populations)."""
 
@@ -564,22 +574,24 @@ class MLP:
         c = C.c_int64(0)
         self.lib.mg_mlp_param_count(self.h, C.byref(c))
         self.n_params = c.value
-        self.n_out = (self.n_params - (4 * 128 + 128 + 2 * (128 * 128 + 128))) // 129
+        self.n_out = (self.n_params - (MLP_IN * 128 + 128 + 2 * (128 * 128 + 128))) // 129
         return self
 
     def set_normalisation(self, mean, std):
         m, s = _c(mean, np.float32), _c(std, np.float32)
+        if m.size != MLP_IN or s.size != MLP_IN:
+            raise ValueError(f"set_normalisation: expected {MLP_IN} means and standard deviations")
         self.mean, self.std = m, s
         self._chk(self.lib.mg_mlp_set_normalisation(self.h, _ptr(m), _ptr(s)), "mg_mlp_set_normalisation")
 
     def forward(self, X):
-        X = _c(X, np.float32)
+        X = _rows(X, MLP_IN, "forward")
         out = np.empty((X.shape[0], self.n_out), np.float32)
         self._chk(self.lib.mg_mlp_forward(self.h, X.shape[0], _ptr(X), _ptr(out)), "mg_mlp_forward")
         return out
 
     def loss_grad(self, X, Y):
-        X, Y = _c(X, np.float32), _c(Y, np.float32)
+        X, Y = _rows(X, MLP_IN, "loss_grad"), _rows(Y, self.n_out, "loss_grad")
         loss = C.c_double(0)
         g = np.empty(self.n_params, np.float32)
         self._chk(self.lib.mg_mlp_loss_grad(self.h, X.shape[0], _ptr(X), _ptr(Y), C.byref(loss), _ptr(g)),
@@ -587,7 +599,7 @@ class MLP:
         return loss.value, g
 
     def train(self, X, Y, epochs=10, batch=4096, lr=1e-3, seed=0):
-        X, Y = _c(X, np.float32), _c(Y, np.float32)
+        X, Y = _rows(X, MLP_IN, "train"), _rows(Y, self.n_out, "train")
         o = mg_train_opts(epochs=epochs, batch=batch, lr=lr, seed=seed)
         r = mg_train_report()
         self._chk(self.lib.mg_mlp_train(self.h, X.shape[0], _ptr(X), _ptr(Y), C.byref(o), C.byref(r)), "mg_mlp_train")
