@@ -189,3 +189,43 @@ def test_mixed_fixed_point_clumpy_50k():
         assert rep["converged"]
     p64, p32 = c64.get_populations(), c32.get_populations()
     assert np.max(rel_err(p32, p64)) < TOL_MIX
+
+
+def test_executed_work_counter():
+    """The warp kernel's own count of point-bin updates (profiling contexts): without
+    skipping it is the nominal count plus the origin, swept once per non-empty half
+    (nominal <= executed <= nominal + n P L Q); with far-wing skipping it is smaller and
+    positive; two launches count twice; a context without profiling counts nothing."""
+    m = syn.model_clumpy_3d(n=1500, seed=6)
+    counts = {}
+    for v in (25, 12):   # (4 lines x 4 bins, 4 blocks) without and with skipping
+        ctx = gpu_context(m, precision=1, profile=1)
+        ctx.trace_rays()
+        ctx.init_populations()
+        ctx.set_variant(v)
+        solves, nominal = ctx.work_counts()
+        ctx.reset_kernel_times()
+        ctx.formal_solve()
+        one = ctx.executed_work()
+        ctx.formal_solve()
+        assert ctx.executed_work() == 2 * one
+        counts[v] = one
+    P = ctx.get_directions()[0].shape[0] // 2
+    L, Q = m.species.n_lines, 31
+    assert nominal <= counts[25] <= nominal + m.n * P * L * Q
+    assert 0 < counts[12] < counts[25]
+    quiet = gpu_context(m, precision=1)
+    quiet.trace_rays()
+    quiet.init_populations()
+    quiet.formal_solve()
+    assert quiet.executed_work() == 0
+
+
+def test_measured_pipe_rates_are_plausible():
+    """The roofline's denominators: FP32 FMA-pipe rates near 128 lanes x 2 flops per SM
+    and clock, packed FFMA2 not below scalar FFMA, ex2 faster than rcp."""
+    import paper_1912_08445_gb300 as mg
+    r = mg.measure_pipe_rates(0)
+    assert 2e13 < r["ffma"] < 2e14 and 2e13 < r["ffma2"] < 2e14
+    assert r["ffma2"] >= 0.9 * r["ffma"]
+    assert 1e12 < r["rcp"] < r["ex2"] < 1e14
