@@ -21,6 +21,8 @@
  *   - Functions ending in _dev take device pointers (on the context's device) and read
  *     or write them in stream order on the context's stream; they never free them.
  *   - A context is not thread safe; distinct contexts are independent.
+ *   - A call on a context makes the context's device the calling thread's current CUDA
+ *     device and leaves it so (mg_measure_pipe_rates restores the previous one).
  *   - Array layouts are C order (row major); "[n][3]" means 3 doubles per point.
  */
 #ifndef MAGRITTE_GB300_H

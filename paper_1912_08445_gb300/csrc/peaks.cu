@@ -84,8 +84,25 @@ __global__ void __launch_bounds__(256) k_rcp(float *out) {
 
 /* Measured pipe rates (see the header): rates[0] FFMA flops/s (2 per FMA), rates[1]
  * FFMA2 flops/s (4 per packed FMA), rates[2] ex2 results/s, rates[3] rcp results/s. */
+namespace {
+// Restores the calling thread's current device on every return path.
+struct DeviceRestore {
+    int prev = -1;
+    DeviceRestore() {
+        if (cudaGetDevice(&prev) != cudaSuccess) {
+            cudaGetLastError();
+            prev = -1;
+        }
+    }
+    ~DeviceRestore() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+}  // namespace
+
 extern "C" int mg_measure_pipe_rates(int32_t device, double *rates) {
     if (!rates) return MG_ERR_ARG;
+    DeviceRestore keep;
     if (cudaSetDevice(device) != cudaSuccess) return MG_ERR_CUDA;
     int sms = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return MG_ERR_CUDA;
