@@ -323,8 +323,10 @@ typedef struct {
 int mg_iterate(mg_ctx *ctx, mg_ali_report *rep);
 
 /* Autotuner of the mixed-precision formal solve: times every launch variant of the
- * Feautrier kernel that suits the model (lines per warp, bins per lane, blocks per SM;
- * CUDA events, best of reps launches after one warm-up) on the current populations,
+ * Feautrier kernel that suits the model (lines per warp 1/2/4, bins per lane 1/2/4/8,
+ * blocks per SM, warps per block, far-wing skipping on or off; 32 variants, indices 0-31,
+ * those valid for the model's lines and bins tried; CUDA events, best of reps launches
+ * after one warm-up) on the current populations,
  * keeps the fastest for later solves and reports it. Leaves a valid radiation field.
  * Requires precision MG_MIXED, traced rays, quadrature and populations. */
 int mg_autotune(mg_ctx *ctx, int32_t reps, int32_t *variant, double *ms, int32_t *n_tried);
