@@ -658,7 +658,23 @@ def run_disc(args):
     kt = ctx.kernel_times()
     ctx.formal_solve()   # (untimed) the radiation field of the final populations, for max L
     max_L = float(np.max(ctx.get_radiation()[1]))
-    print(json.dumps({"metric": METRIC, "unit": UNIT, "workload": "Keplerian disc, "
+    ali = None
+    if args.disc_ali:   # ALI to 1e-6 from LTE on the same context, Ng every 4th iteration
+        ali = {}
+        for ng in (4, 0):
+            c2 = mg.Context(precision=mg.MG_MIXED, tol=1e-6, max_iter=200, ng_period=ng)
+            c2.load_model(m)
+            c2.trace_rays()
+            c2.set_variant(v)
+            c2.init_populations()
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            rep, rc = c2.iterate(allow_not_converged=True)
+            torch.cuda.synchronize()
+            ali[f"mixed_lte_ng{ng}"] = {"seconds": time.perf_counter() - t1, "iterations": rep["iterations"],
+                                        "converged": bool(rep["converged"])}
+            c2.close()
+    print(json.dumps({"metric": METRIC, "unit": UNIT, "ali_to_1e-6": ali, "workload": "Keplerian disc, "
                       f"{m.n} points, 192 rays, 20 levels, 19 lines x 63 bins", "value": solves / dt,
                       "ms_per_step": dt * 1e3, "cell_freq_updates": updates, "variant": v,
                       "tau_fp64": args.tau_fp64, "promoted_cells": ctx.promoted_cells() if args.tau_fp64 > 0 else 0,
@@ -954,6 +970,7 @@ def main():
     ap.add_argument("--no-fp64e", dest="fp64e", action="store_false",
                     help="leave out the FP64-elimination record of the default line")
     ap.add_argument("--variant", type=int, default=-1, help="disc workload: launch variant (-1: autotune)")
+    ap.add_argument("--disc-ali", action="store_true", help="disc workload: also the ALI to 1e-6 from LTE")
     ap.add_argument("--ali", action="store_true", help="measure ALI time to converge instead")
     ap.add_argument("--workload", default="default",
                     choices=["default", "clumpy", "batch", "disc", "learned", "image", "sphere1d", "kernels"])
