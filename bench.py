@@ -696,10 +696,13 @@ def run_kernels(args):
     c.load_model(big)
     c.trace_rays()
     c.init_populations()
+    if args.variant >= 0:   # the warp kernel's launch variant (else the model's default)
+        c.set_variant(args.variant)
     c.formal_solve()
     c.update_populations()
     torch.cuda.synchronize()
     out["cases"]["clumpy50k_mixed"] = {k: round(v[0] / max(v[1], 1), 4) for k, v in c.kernel_times().items()}
+    out["cases"]["clumpy50k_mixed"]["executed_updates"] = c.executed_work()
     c.close()
     small = syn.model_clumpy_3d(n=2000, seed=1)
     for name, opts, sca in (("clumpy2k_fp64", {}, False), ("clumpy2k_fp64_band1", {"alo_band": 1}, False),
@@ -969,7 +972,8 @@ def main():
                     help="leave out the ALI time-to-converge half of the default line")
     ap.add_argument("--no-fp64e", dest="fp64e", action="store_false",
                     help="leave out the FP64-elimination record of the default line")
-    ap.add_argument("--variant", type=int, default=-1, help="disc workload: launch variant (-1: autotune)")
+    ap.add_argument("--variant", type=int, default=-1,
+                    help="disc and kernels workloads: launch variant of the warp kernel (-1: autotune / default)")
     ap.add_argument("--disc-ali", action="store_true", help="disc workload: also the ALI to 1e-6 from LTE")
     ap.add_argument("--ali", action="store_true", help="measure ALI time to converge instead")
     ap.add_argument("--workload", default="default",
