@@ -46,9 +46,11 @@ def test_formal_solve_mixed_parity(name):
     assert np.max(np.abs(L[sel] - Lo)) < TOL_MIX * max(1e-6, float(np.max(np.abs(Lo))))
 
 
-def _full_size_variants(m, variants, n_origins, seed):
+def _full_size_variants(m, variants, n_origins, seed, jeff_scale_j=False):
     """Every launch variant the autotuner may pick for a full-size workload, each against
-    the oracle on sampled origins; then the autotuned choice itself."""
+    the oracle on sampled origins; then the autotuned choice itself. With jeff_scale_j,
+    J_eff is held to 1e-4 on the scale of J (optically thick cells, where J_eff is a small
+    residual of J)."""
     o = Oracle(m, nthreads=16)
     ctx = gpu_context(m, precision=1)
     ctx.trace_rays()
@@ -60,7 +62,10 @@ def _full_size_variants(m, variants, n_origins, seed):
         ctx.formal_solve()
         J, L, E = ctx.get_radiation()
         assert np.max(rel_err(J[origins], Jo)) < TOL_MIX, v
-        assert np.max(rel_err(E[origins], Eo)) < TOL_MIX, v
+        if jeff_scale_j:
+            assert np.max(np.abs(E[origins] - Eo) / Jo) < TOL_MIX, v
+        else:
+            assert np.max(rel_err(E[origins], Eo)) < TOL_MIX, v
         assert np.max(np.abs(L[origins] - Lo)) < TOL_MIX * float(np.max(np.abs(Lo))), v
     best, _, tried = ctx.autotune(reps=1)
     assert best in variants and tried == len(variants)
@@ -74,10 +79,12 @@ def test_formal_solve_mixed_clumpy_50k_sampled():
 
 
 def test_formal_solve_mixed_disc_200k_sampled():
-    """The disc workload at full size (200k points, 192 rays, 20-level rotor, 19 lines x
-    63 bins), every valid launch variant: sampled origins against the oracle."""
-    _full_size_variants(syn.model_disc(n=200_000, seed=0),
-                        [5, 6, 9, 10, 18, 19, 22, 23, 26, 27, 28, 29, 30, 31], 8, 7)
+    """The disc workload at full size as the bench runs it (200k points, 192 rays,
+    20-level rotor, 19 lines x 63 bins, n_H2 = 2.5e16 m^-3 at the inner radius: Sobolev
+    optical depths up to ~1e4), every valid launch variant: 32 sampled origins against
+    the oracle."""
+    _full_size_variants(syn.model_disc(n=200_000, seed=0, n_h2_in=2.5e16),
+                        [5, 6, 9, 10, 18, 19, 22, 23, 26, 27, 28, 29, 30, 31], 32, 7, jeff_scale_j=True)
 
 
 @pytest.mark.parametrize("name", ["sphere1d", "sphere1d_thick"])
