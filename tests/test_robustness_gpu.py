@@ -92,3 +92,20 @@ def test_checkpoint_resume_matches_uninterrupted_run():
     c3.set_populations(chk)
     c3.iterate(allow_not_converged=True)
     assert np.array_equal(c3.get_populations(), full)
+
+
+def test_half_ray_beyond_max_steps_is_refused():
+    """A half-ray longer than opt.max_steps cells ends the trace with MG_ERR_CAPACITY
+    (nothing is stored); the same model traces with the default limit."""
+    import paper_1912_08445_gb300 as mg
+    m = syn.model_clumpy_3d(n=600, seed=4)
+    ctx = gpu_context(m, max_steps=3)
+    with pytest.raises(mg.MagritteError) as e:
+        ctx.trace_rays()
+    assert e.value.code == mg.binding.MG_ERR_CAPACITY
+    with pytest.raises(mg.MagritteError) as e:
+        ctx.formal_solve()
+    assert e.value.code == mg.binding.MG_ERR_STATE
+    ok = gpu_context(m)
+    st, rc = ok.trace_rays()
+    assert rc >= 0 and st["n_elements"] > 0
