@@ -628,3 +628,46 @@ def test_stateq_twenty_level_rotor_against_60_digit_solve():
         x = np.array([float(v) for v in mpmath.lu_solve(A, mpmath.matrix([0] * (lev - 1) + [ns[c]]))])
         e = np.abs(ref[c] - x) / np.abs(x)
         assert np.all(e[x >= 1e-10 * ns[c]] <= 1e-15) and np.all(e[x >= 1e-20 * ns[c]] <= 1e-12)
+
+
+def _tie_mesh():
+    """Points on integer coordinates, scaled by a power of two so that every projection
+    and squared distance is exact in FP64, with exact ties for the walk along +x from
+    point 0. Points 5 (4, 0, 0) and 6 (-1, 0, 0) are boundary points. Neighbour lists are
+    in reverse index order, so that list order cannot decide a tie."""
+    import synthetic as syn
+    h = 2.0 ** 40
+    pos = np.array([[0, 0, 0], [1, 1, 0], [1, -1, 0], [2, 1, 0], [3, 1, 0], [4, 0, 0], [-1, 0, 0]], float) * h
+    nbrs = {0: [2, 1, 6], 1: [4, 3, 0], 2: [4, 3, 0], 3: [5, 4, 1, 2], 4: [5, 3, 1, 2], 5: [4, 3], 6: [0]}
+    off = np.zeros(len(pos) + 1, np.int64)
+    idx = []
+    for i in range(len(pos)):
+        idx.extend(nbrs[i]); off[i + 1] = len(idx)
+    n = len(pos)
+    sp = syn.species_two_level()
+    m = syn.Model(name="ties", pos=pos, vel=np.zeros((n, 3)), nbr_off=off, nbr_idx=np.array(idx, np.int32),
+                  is_bdy=np.array([0, 0, 0, 0, 0, 1, 1], np.uint8), n_coll=np.full(n, 1e10), T=np.full(n, 20.0),
+                  v_turb=np.full(n, 150.0), n_spec=np.full(n, 1e4), species=sp, n_q=7,
+                  dirs=np.array([[1.0, 0, 0], [-1.0, 0, 0], [0, 1.0, 0], [0, -1.0, 0], [0, 0, 1.0], [0, 0, -1.0]]))
+    return m
+
+
+def test_trace_tie_breaks_exact():
+    """Exact ties (the reading: smaller squared distance to the ray, then smaller
+    projection, then smaller index). Along +x from point 0:
+    - points 1 (1, 1, 0) and 2 (1, -1, 0) tie in projection and distance: point 1, the
+      smaller index, is taken;
+    - from point 1, points 3 (2, 1, 0) and 4 (3, 1, 0) tie in distance: point 3, the
+      smaller projection, is taken;
+    - from point 3, point 5 (4, 0, 0) lies on the ray and ends the walk at the boundary.
+    The oracle and the exhaustive walk in exact arithmetic agree on every half-ray."""
+    m = _tie_mesh()
+    o = Oracle(m)
+    t = o.trace(0, 0)
+    assert t["cells"].tolist() == [1, 3, 5] and not t["dead_end"]
+    for p in range(m.n):
+        for r in range(o.dirs.shape[0]):
+            t = o.trace(p, r)
+            cells, dead = _walk_exact(m, o.dirs, p, r)
+            assert t["cells"].tolist() == cells, (p, r)
+            assert t["dead_end"] == dead, (p, r)

@@ -279,3 +279,19 @@ def test_negative_opacity_is_reported():
     ctx.formal_solve()
     ch, rc = ctx.update_populations()
     assert ctx.status_counts()[1] == 0 and rc == 0
+
+
+def test_trace_tie_breaks_bit_exact():
+    """The constructed mesh of exact ties: every half-ray of the GPU tracer equals the
+    oracle's (smaller distance, then smaller projection, then smaller index)."""
+    from test_oracle_pins import _tie_mesh
+    m = _tie_mesh()
+    o = Oracle(m)
+    ctx = gpu_context(m, oracle_dirs=o.dirs)
+    ctx.trace_rays()
+    for p in range(m.n):
+        for r in range(o.dirs.shape[0]):
+            t = o.trace(p, r)
+            g = ctx.get_ray(p, r)
+            assert g["cells"].tolist() == t["cells"].tolist(), (p, r)
+            assert np.array_equal(g["ds"], t["ds"]), (p, r)
