@@ -121,7 +121,8 @@ static int build_items(mg_batch *b) {
 
 static int launch_solve(mg_batch *b) {
     B_CUDA(cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned long long), b->stream));
-    const int v = b->variant >= 0 ? b->variant : mg_variant_default(b->L, b->Q);
+    int v = b->variant >= 0 ? b->variant : mg_variant_default(b->L, b->Q);
+    for (auto *c : b->models) v = mg_variant_effective(c, v);   // no skipping under a large opacity floor
     const int grid = b->grid > 0 ? b->grid : b->num_sms * mg_variant_minb(v);
     const int G = mg_variant_g(v);
     if (G < 1 || G > mg_batch::kMaxG || !b->d_items_g[G][0] || !b->d_items_g[G][1])

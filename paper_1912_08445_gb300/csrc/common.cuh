@@ -64,6 +64,7 @@ struct mg_ctx {
     int64_t n = 0;
     int32_t geometry = MG_GEOM_3D;
     int64_t n_edges = 0;
+    double extent = 0.0;   // longest path through the model (m): bounding-box diagonal, or the sphere's diameter
     double *d_pos = nullptr, *d_vel = nullptr;
     int64_t *d_nbr_off = nullptr;
     int32_t *d_nbr_idx = nullptr;
@@ -252,5 +253,6 @@ int mg_variant_valid(int v, int L, int Q);
 int mg_variant_minb(int v);
 int mg_variant_g(int v);
 int mg_variant_default(int L, int Q);
+int mg_variant_effective(const mg_ctx *ctx, int v);
 int mg_batch_launch(int v, int grid, const void *d_args, const void *d_items, int64_t n_items,
                     unsigned long long *counter, const int32_t *active, cudaStream_t stream);

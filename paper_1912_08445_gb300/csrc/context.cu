@@ -189,6 +189,19 @@ extern "C" int mg_set_mesh(mg_ctx *ctx, int64_t n, const double *pos, const doub
     for (int64_t i = 0; i < n; i++)
         ctx->vmax = std::max(ctx->vmax, std::sqrt(vel[3 * i] * vel[3 * i] + vel[3 * i + 1] * vel[3 * i + 1] +
                                                   vel[3 * i + 2] * vel[3 * i + 2]));
+    {   // longest path through the model
+        double lo[3] = {pos[0], pos[1], pos[2]}, hi[3] = {pos[0], pos[1], pos[2]}, rmax = 0.0;
+        for (int64_t i = 0; i < n; i++)
+            for (int k = 0; k < 3; k++) {
+                lo[k] = std::min(lo[k], pos[3 * i + k]);
+                hi[k] = std::max(hi[k], pos[3 * i + k]);
+                rmax = std::max(rmax, std::fabs(pos[3 * i + k]));
+            }
+        ctx->extent = geometry == MG_GEOM_SPHERICAL_1D
+                          ? 2.0 * rmax
+                          : std::sqrt((hi[0] - lo[0]) * (hi[0] - lo[0]) + (hi[1] - lo[1]) * (hi[1] - lo[1]) +
+                                      (hi[2] - lo[2]) * (hi[2] - lo[2]));
+    }
     int rc;
     if ((rc = mg_alloc(ctx, &ctx->d_pos, 3 * n)) || (rc = mg_alloc(ctx, &ctx->d_vel, 3 * n)) ||
         (rc = mg_alloc(ctx, &ctx->d_nbr_off, n + 1)) || (rc = mg_alloc(ctx, &ctx->d_nbr_idx, E)) ||

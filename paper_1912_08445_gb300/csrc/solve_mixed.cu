@@ -983,6 +983,26 @@ const WarpVariant kWarpVariants[] = {
 #undef MG_VARIANT_W
 constexpr int kNumWarpVariants = sizeof(kWarpVariants) / sizeof(kWarpVariants[0]);
 
+// Far-wing skipping leaves out the floored intervals of far points. Each changes the
+// sweep by O(chi_min ds), below FP32 resolution only while the floored optical depth of
+// a whole ray, chi_min times the longest path through the model, is; otherwise (a large
+// opacity floor) the variant's non-skipping twin runs instead.
+bool skip_allowed(const mg_ctx *ctx) { return ctx->opt.chi_min * ctx->extent < 1e-7; }
+
+int no_skip_twin(int v) {
+    const WarpVariant &w = kWarpVariants[v];
+    for (int u = 0; u < kNumWarpVariants; u++) {
+        const WarpVariant &x = kWarpVariants[u];
+        if (!x.skip && x.G == w.G && x.NB == w.NB && x.MINB == w.MINB && x.W == w.W) return u;
+    }
+    return v;
+}
+
+int effective_variant(const mg_ctx *ctx, int v) {
+    if (v < 0 || v >= kNumWarpVariants || !kWarpVariants[v].skip || skip_allowed(ctx)) return v;
+    return no_skip_twin(v);
+}
+
 bool variant_valid(int v, int L, int Q) {
     if (v < 0 || v >= kNumWarpVariants) return false;
     const WarpVariant &w = kWarpVariants[v];
@@ -1050,7 +1070,7 @@ static int launch_mixed(mg_ctx *ctx, int variant) {
         MgTimed t(ctx, "feautrier_mixed");
         k_feautrier_mixed<true><<<(unsigned)ctx->n, threads, smem, ctx->stream>>>(a);
     } else if (variant >= 0 && variant < kNumWarpVariants) {
-        const WarpVariant &wv = kWarpVariants[variant];
+        const WarpVariant &wv = kWarpVariants[effective_variant(ctx, variant)];
         const int64_t items = ctx->n * ((L + wv.G - 1) / wv.G);
         const unsigned grid = (unsigned)((items + wv.W - 1) / wv.W);
         MgTimed t(ctx, "feautrier_mixed");
@@ -1092,7 +1112,7 @@ int mg_autotune_mixed(mg_ctx *ctx, int reps, int *best, double *best_ms, int *n_
     const int saved_profile = ctx->opt.profile;
     ctx->opt.profile = 0;
     for (int v = 0; v < kNumWarpVariants; v++) {
-        if (!variant_valid(v, L, Q)) continue;
+        if (!variant_valid(v, L, Q) || effective_variant(ctx, v) != v) continue;
         tried++;
         float vbest = 1e30f;
         for (int r = 0; r < reps + 1; r++) {
@@ -1130,6 +1150,7 @@ int mg_fill_mixargs(mg_ctx *ctx, void *out) {
 
 int mg_variant_count() { return kNumWarpVariants; }
 int mg_variant_valid(int v, int L, int Q) { return variant_valid(v, L, Q) ? 1 : 0; }
+int mg_variant_effective(const mg_ctx *ctx, int v) { return effective_variant(ctx, v); }
 int mg_variant_minb(int v) { return (v >= 0 && v < kNumWarpVariants) ? kWarpVariants[v].MINB : 0; }
 int mg_variant_g(int v) { return (v >= 0 && v < kNumWarpVariants) ? kWarpVariants[v].G : 1; }
 int mg_variant_default(int L, int Q) { return default_variant(L, Q); }

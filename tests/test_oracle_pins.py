@@ -671,3 +671,31 @@ def test_trace_tie_breaks_exact():
             cells, dead = _walk_exact(m, o.dirs, p, r)
             assert t["cells"].tolist() == cells, (p, r)
             assert t["dead_end"] == dead, (p, r)
+
+
+def test_opacity_floor_keeps_the_emission():
+    """Where the line opacity is below the floor chi_min, the floored opacity carries the
+    line's own emissivity (S_eff = eta / chi_min, so S dtau = eta ds): a uniform static
+    slab whose line is negligible against the floor is then a slab of constant opacity
+    chi_min and constant source, whose centre intensity per bin is S_eff (1 - e^-tau) with
+    tau = chi_min a (no boundary radiation: T_cmb -> 0). The ratio of J at two floors is
+    therefore [(1 - e^-tau2) / chi2] / [(1 - e^-tau1) / chi1], independent of the line's
+    normalisation, and the discretisation error falls 4x per halving of the cells. A source
+    taken from the line alone would give (1 - e^-tau2) / (1 - e^-tau1) = 2.49 instead."""
+    import synthetic as syn
+    sp = syn.species_two_level()
+    a = 2e11
+    exact = ((1 - np.exp(-3e-12 * a)) / 3e-12) / ((1 - np.exp(-1e-12 * a)) / 1e-12)
+    errs = []
+    for n_cells in (81, 161, 321):
+        m = syn.model_line_1d(np.linspace(-a, a, n_cells), 0.0, 1e10, 30.0, 150.0, 1e-16, sp, 7)
+        c = n_cells // 2
+        Js = {}
+        for chi in (1e-12, 3e-12):
+            o = Oracle(m, chi_min=chi, T_cmb=0.01)
+            J, L, E = o.formal_solve(o.lte())
+            Js[chi] = J[c, 0]
+        errs.append(abs(Js[3e-12] / Js[1e-12] / exact - 1))
+    assert errs[-1] < 5e-7, errs
+    assert 3.5 < errs[0] / errs[1] < 4.5 and 3.5 < errs[1] / errs[2] < 4.5, errs
+    assert exact < 0.9   # far from the line-only source's 2.49

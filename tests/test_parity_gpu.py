@@ -295,3 +295,25 @@ def test_trace_tie_breaks_bit_exact():
             g = ctx.get_ray(p, r)
             assert g["cells"].tolist() == t["cells"].tolist(), (p, r)
             assert np.array_equal(g["ds"], t["ds"]), (p, r)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_opacity_floor_slab_matches_oracle(precision):
+    """The slab of the oracle's floor pin (a line negligible against chi_min = 1e-12 and
+    3e-12 m^-1, no boundary radiation): the GPU's J, L and J_eff equal the oracle's
+    (1e-10 FP64, 1e-4 mixed), so both carry the line's emission through the floor."""
+    sp = syn.species_two_level()
+    a = 2e11
+    m = syn.model_line_1d(np.linspace(-a, a, 161), 0.0, 1e10, 30.0, 150.0, 1e-16, sp, 7)
+    for chi in (1e-12, 3e-12):
+        o = Oracle(m, chi_min=chi, T_cmb=0.01)
+        ctx = gpu_context(m, oracle_dirs=o.dirs, precision=precision, chi_min=chi, T_cmb=0.01)
+        ctx.trace_rays()
+        ctx.init_populations()
+        ctx.formal_solve()
+        J, L, E = ctx.get_radiation()
+        Jo, Lo, Eo = o.formal_solve(o.lte())
+        tol = TOL64 if precision == 0 else 1e-4
+        assert np.max(rel_err(J, Jo)) < tol
+        assert np.max(rel_err(E, Eo)) < tol
+        assert np.max(np.abs(L - Lo)) < tol * float(np.max(np.abs(Lo)))
