@@ -445,7 +445,8 @@ int mg_executed_work(const mg_ctx *ctx, int64_t *updates);
 /* Measured throughput of the FP32 pipes that bound the mixed-precision formal solve, on
  * `device`: rates[0] scalar FFMA flops/s (2 per FMA), rates[1] packed FFMA2 flops/s,
  * rates[2] ex2.approx results/s, rates[3] rcp.approx results/s (independent chains over a
- * grid of 8 CTAs of 256 threads per SM, best of three timed launches). Allocates 16 bytes; synchronises. */
+ * grid of 8 CTAs of 256 threads per SM, best of three timed launches). Allocates 16 bytes;
+ * synchronises; the calling thread's current device is restored on return. */
 int mg_measure_pipe_rates(int32_t device, double *rates);
 
 #ifdef __cplusplus
